@@ -1,0 +1,253 @@
+"""The VKLB time loop of Sec. 3.5 (Fig. 5), literally, in FP64.
+
+One step, in the flow chart's order:
+  1. Delta t = Delta x / xi                                  (Fig. 5, Sec. 3.2)
+  2. collision  f*_q = f_q - omega (f_q - f_q^eq(U^n))       (Eq. 42)
+  3. streaming  f_q(x + v_q Delta t) = f*_q(x); periodic wrap (Eq. 43, Eq. 37)
+  4. moments    U^{n+1} = sum_q f_q                          (Eq. 3)
+  5. characteristic boundary conditions (1D, non-periodic)   (Eqs. 33-36)
+  6. CFL        xi = max_j |lambda_j| / nu over the grid      (Eq. 29)
+  7. equilibria f^eq(U^{n+1}) for the next step              (Eqs. 22-24 / 41)
+Initialisation: xi from U(x,0), f_q(x,0) = f_q^eq(U(x,0)) (Eq. 2b, Fig. 5).
+
+Lattices: D1Q3 v = (xi, 0, -xi) (Sec. 2.2, Fig. 1); D2Q5 v = (xi,0), (-xi,0),
+(0,0), (0,xi), (0,-xi) (Eq. 38).  Distributions are stored f[q, field, (y,) x].
+
+Readings of the paper taken here (listed in the design notes):
+  R1  alpha normaliser max_j|lambda_j| is per cell and direction.
+  R2  xi is the max over all cells, both directions and all eigenvalues.
+  R3  run_to(T) lands on T with evenly spread steps: every step takes
+      xi_eff = m dx / (T - t), m = ceil((T - t) xi / dx) (the number of
+      CFL-limited steps left), so xi_eff >= xi and the last step ends on T.
+      (Clipping only the last step breaks second order at omega = 2.)
+  R4  MHD-GLM: c_h = ch_factor * max over cells and directions of c_f(U^n),
+      refreshed with xi every step; +-c_h are eigenvalues and enter xi.
+  R9  1D nodes are cell centres x_i = lo + (i + 1/2) dx; nodes 0 and N-1 are the
+      boundary nodes of the characteristic condition.
+  R10 characteristic BC: W = P^-1 U with P frozen at x_b; one-sided difference
+      towards the interior; incoming waves (lambda < 0 on the right, lambda > 0
+      on the left) are dropped; Delta t = dx / xi_n.
+  R11 boundary f = f^eq(U_b^{n+1}) uses xi_{n+1}.
+
+Test infrastructure only.
+
+Parity pins (tests/test_oracle_vklb.py, tests/test_oracle_convergence.py):
+moment constraints (Eqs. 3, 5); Theorems 4.1-4.3 (finite-difference and
+finite-volume forms); exact discrete conservation on periodic grids (Thm 4.3);
+exact shift for advection; exact Riemann solutions (dam break, Sod); second-order
+convergence for smooth problems at omega = 2 (Sec. 5.2); the printed Mach ranges
+of the entropy wave and vortex initial data (Sec. 5.2).
+"""
+import numpy as np
+
+from . import splitting
+from .systems import MHDGLM
+
+D1Q3_M = np.array([1, 0, -1])
+D2Q5_M = np.array([[1, 0], [-1, 0], [0, 0], [0, 1], [0, -1]])
+
+
+def equilibrium_1d(U, Fp, Fm, xi, c):
+    """Weighted upwind set, Eqs. (22)-(24):
+    f1 = c U + F+/xi,  f2 = (1 - 2c) U - (F+ - F-)/xi,  f3 = c U - F-/xi."""
+    f1 = c * U + Fp / xi
+    f2 = (1.0 - 2.0 * c) * U - (Fp - Fm) / xi
+    f3 = c * U - Fm / xi
+    return np.stack([f1, f2, f3])
+
+
+def equilibrium_2d(U, Fp1, Fm1, Fp2, Fm2, xi, c):
+    """2D weighted upwind set, Eq. (41):
+    f1 = c U + F(1,+)/xi, f2 = c U - F(1,-)/xi, f4 = c U + F(2,+)/xi,
+    f5 = c U - F(2,-)/xi,
+    f3 = (1 - 4c) U - (F(1,+) + F(2,+) - F(1,-) - F(2,-))/xi."""
+    f1 = c * U + Fp1 / xi
+    f2 = c * U - Fm1 / xi
+    f4 = c * U + Fp2 / xi
+    f5 = c * U - Fm2 / xi
+    f3 = (1.0 - 4.0 * c) * U - (Fp1 + Fp2 - Fm1 - Fm2) / xi
+    return np.stack([f1, f2, f3, f4, f5])
+
+
+class Sim:
+    """One VKLB simulation on a uniform grid.
+
+    system   : an ``oracle.systems`` object (its dim selects D1Q3 or D2Q5)
+    n        : (nx,) or (nx, ny) cells;  lo, hi: domain corners
+    bc       : "periodic" or "characteristic" (1D only)
+    set_kind : "weighted" (c, k), "centered" (c = 1/Q, F/2), "discontinuous"
+    omega    : relaxation parameter, 0 < omega <= 2 (Sec. 2.3)
+    nu       : CFL number (Eq. 29);  dt > 0 fixes xi = dx / dt instead
+    """
+
+    def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted",
+                 c=0.05, k=2.0, omega=1.0, nu=0.9, dt=None, ch_factor=6.0):
+        self.sys = system
+        self.dim = system.dim
+        self.n = tuple(int(v) for v in n)
+        assert len(self.n) == self.dim
+        lo = np.atleast_1d(np.asarray(lo, float))
+        hi = np.atleast_1d(np.asarray(hi, float))
+        dxs = (hi - lo) / np.asarray(self.n, float)
+        if self.dim == 2 and abs(dxs[0] - dxs[1]) > 1e-12 * dxs[0]:
+            raise ValueError("D2Q5 needs dx == dy (Sec. 3.4)")
+        self.dx = float(dxs[0])
+        self.lo, self.hi = lo, hi
+        if bc not in ("periodic", "characteristic"):
+            raise ValueError(bc)
+        if bc == "characteristic" and self.dim != 1:
+            raise ValueError("characteristic BC is defined in 1D (Sec. 3.3)")
+        self.bc = bc
+        self.set_kind = set_kind
+        if set_kind == "centered":
+            c = 1.0 / 3.0 if self.dim == 1 else 1.0 / 5.0
+        elif set_kind == "discontinuous":
+            c = 0.0
+        self.c, self.k, self.omega, self.nu = float(c), float(k), float(omega), float(nu)
+        if not (0.0 < self.omega <= 2.0):
+            raise ValueError("omega must lie in (0, 2] (Sec. 2.3)")
+        self.fixed_xi = None if dt is None or dt <= 0 else self.dx / float(dt)
+        self.ch_factor = float(ch_factor)
+        self.f = None
+        self.t = 0.0
+        self.steps = 0
+        self.xi = None
+
+    # ----- pieces of one step -------------------------------------------------
+    def _flat(self, U):
+        return U.reshape(U.shape[0], -1)
+
+    def split(self, U, d):
+        Uf = self._flat(U)
+        Fp, Fm = splitting.split(self.sys, Uf, d, self.set_kind, self.k)
+        return Fp.reshape(U.shape), Fm.reshape(U.shape)
+
+    def equilibrium(self, U, xi):
+        if self.dim == 1:
+            Fp, Fm = self.split(U, 0)
+            return equilibrium_1d(U, Fp, Fm, xi, self.c)
+        Fp1, Fm1 = self.split(U, 0)
+        Fp2, Fm2 = self.split(U, 1)
+        return equilibrium_2d(U, Fp1, Fm1, Fp2, Fm2, xi, self.c)
+
+    def refresh_ch(self, U):
+        """R4: c_h = ch_factor * max_{x,d} c_f(U)."""
+        if isinstance(self.sys, MHDGLM):
+            Uf = self._flat(U)
+            cf = max(np.max(self.sys.fast_speed(Uf, d)) for d in range(self.dim))
+            self.sys.ch = self.ch_factor * float(cf)
+
+    def max_lambda(self, U):
+        """R2: global max over cells, directions and eigenvalues."""
+        Uf = self._flat(U)
+        return max(float(np.max(self.sys.max_speed(Uf, d))) for d in range(self.dim))
+
+    def cfl_xi(self, U):
+        """Eq. (29): xi = max_j |lambda_j| / nu (or the fixed dx/dt)."""
+        if self.fixed_xi is not None:
+            return self.fixed_xi
+        return self.max_lambda(U) / self.nu
+
+    def stream(self, fs):
+        """Eq. (43) with periodic wrap (Eq. 37) or, for the characteristic BC, a
+        plain shift whose boundary nodes are overwritten by the BC."""
+        out = np.empty_like(fs)
+        if self.dim == 1:
+            for q, m in enumerate(D1Q3_M):
+                if self.bc == "periodic":
+                    out[q] = np.roll(fs[q], m, axis=-1)
+                else:
+                    out[q] = fs[q]
+                    if m == 1:
+                        out[q][..., 1:] = fs[q][..., :-1]
+                    elif m == -1:
+                        out[q][..., :-1] = fs[q][..., 1:]
+            return out
+        for q, (mx, my) in enumerate(D2Q5_M):
+            out[q] = np.roll(np.roll(fs[q], mx, axis=-1), my, axis=-2)
+        return out
+
+    def char_bc(self, Uold, Unew, xi_n):
+        """Eqs. (33)-(35) with R10: returns the boundary states U_b^{n+1}
+        (left, right) computed from U^n."""
+        res = []
+        for side in (0, 1):
+            if side == 0:
+                ub, dU = Uold[:, 0], Uold[:, 1] - Uold[:, 0]
+            else:
+                ub, dU = Uold[:, -1], Uold[:, -1] - Uold[:, -2]
+            A = splitting.jacobian(self.sys, ub[:, None], 0)[0]
+            lam, P = np.linalg.eig(A)
+            lam = np.real(lam)
+            P = np.real(P)
+            dW = np.linalg.solve(P, dU)          # dx * dW/dx, W = P^-1 U
+            keep = (lam < 0) if side == 0 else (lam > 0)   # outgoing waves only
+            rhs = P @ (np.where(keep, lam, 0.0) * dW)
+            res.append(ub - rhs / xi_n)          # Delta t / dx = 1 / xi_n
+        return res
+
+    # ----- public API ---------------------------------------------------------
+    def set_state(self, U0):
+        U0 = np.array(U0, dtype=np.float64)
+        assert U0.shape == (self.sys.p,) + tuple(reversed(self.n)), U0.shape
+        self.refresh_ch(U0)
+        self.xi = self.cfl_xi(U0)
+        self.f = self.equilibrium(U0, self.xi)              # Eq. (2b)
+        self.t = 0.0
+        self.steps = 0
+
+    def moments(self):
+        return self.f.sum(axis=0)                             # Eq. (3)
+
+    def step(self, t_end=None):
+        """One step of Fig. 5.  With t_end, the lattice speed is raised to land
+        on t_end with evenly spread steps (R3); returns False without stepping
+        once t >= t_end."""
+        xi = self.xi
+        if t_end is not None:
+            rem = t_end - self.t
+            if rem <= 1e-14 * max(1.0, abs(t_end)):
+                return False
+            m = max(1.0, np.ceil(rem * xi / self.dx - 1e-9))
+            xi = m * self.dx / rem
+        U = self.f.sum(axis=0)
+        feq = self.equilibrium(U, xi)                         # Eqs. (22)-(24)/(41)
+        fs = self.f - self.omega * (self.f - feq)             # Eq. (42)
+        fn = self.stream(fs)                                  # Eq. (43)
+        Un = fn.sum(axis=0)                                   # Eq. (3)
+        if self.bc == "characteristic":
+            ubl, ubr = self.char_bc(U, Un, xi)                # Eqs. (33)-(35)
+            Un[:, 0] = ubl
+            Un[:, -1] = ubr
+        self.refresh_ch(Un)
+        xin = self.cfl_xi(Un)                                 # Eq. (29)
+        if self.bc == "characteristic":
+            fb = self.equilibrium(np.stack([Un[:, 0], Un[:, -1]], axis=1), xin)
+            fn[:, :, 0] = fb[:, :, 0]                         # Eq. (36), R11
+            fn[:, :, -1] = fb[:, :, 1]
+        self.f = fn
+        self.t = self.t + self.dx / xi
+        if t_end is not None and abs(self.t - t_end) <= 1e-13 * max(1.0, abs(t_end)):
+            self.t = float(t_end)
+        self.xi = xin
+        self.steps += 1
+        return True
+
+    def run(self, nsteps):
+        for _ in range(int(nsteps)):
+            self.step()
+
+    def run_to(self, t_end, max_steps=10**7):
+        for _ in range(max_steps):
+            if not self.step(t_end):
+                break
+
+    def totals(self):
+        """Conserved totals sum_x U(x) dx^D (Thm 4.3: conserved on periodic grids)."""
+        U = self.moments()
+        axes = tuple(range(1, U.ndim))
+        return U.sum(axis=axes) * self.dx ** self.dim
+
+    def cell_centers(self):
+        cs = [self.lo[i] + (np.arange(self.n[i]) + 0.5) * self.dx for i in range(self.dim)]
+        return cs
