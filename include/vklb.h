@@ -1,0 +1,205 @@
+/*
+ * vklb.h -- C ABI of the B300 (sm_103a) weighted-upwind vector kinetic lattice
+ * Boltzmann (WU-VKLB) library, libvklb.so.
+ *
+ * The method is the one of Brown, Chaudhry and Shadid, "A Weighted Upwind Vector
+ * Kinetic Lattice Boltzmann Method For Hyperbolic Conservation Laws":
+ *   - the conservation law  dU/dt + sum_d dF^(d)(U)/dx_d = 0      (Sec. 2.1, Eq. 1)
+ *   - vector distributions f_q in R^p on the D1Q3 / D2Q5 lattices (Sec. 2.2, Eq. 38)
+ *   - weighted upwind equilibria                                   (Eqs. 22-24, 41)
+ *     built from the sigmoid-weighted eigen split of F            (Eqs. 25-27)
+ *   - collide  f* = f - omega (f - f^eq)                           (Eq. 42)
+ *   - stream   f_q(x + v_q dt) = f*_q(x)                           (Eq. 43)
+ *   - moments  U = sum_q f_q                                       (Eq. 3)
+ *   - CFL lattice speed  xi = max_j |lambda_j| / nu                (Eq. 29)
+ *   - periodic (Eq. 37) and characteristic (Eqs. 33-36) boundaries.
+ * One call to vklb_step advances the state by the flow chart of Fig. 5.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All pointers are plain host or device pointers; sizes are element counts
+ *    unless stated otherwise.  No call keeps a caller pointer after it returns.
+ *  - Conserved-state arrays are double, laid out fields-first, x fastest:
+ *        U[k * ny * nx + j * nx + i],  k = 0..p-1 (1D: ny = 1).
+ *    Field order: advection (u); shallow water (h, hu[, hv]) (Eq. 52);
+ *    Euler (rho, rho u[, rho v], E) (Eq. 54);
+ *    MHD-GLM (rho, rho u, rho v, rho w, E, Bx, By, Bz, psi) (Eq. 58).
+ *  - Every call returns a vklb_status.  Calls that enqueue GPU work are
+ *    asynchronous on the simulation's CUDA stream; a device-side fault of the
+ *    method (non-physical state, CFL violated with a fixed dt) is latched in a
+ *    device error word and returned by the next synchronising call
+ *    (vklb_sync, vklb_moments, vklb_conservation_totals, vklb_time,
+ *    vklb_get_state).  No call aborts the process.
+ *  - The library allocates its own device memory (cudaMalloc) for the
+ *    distributions and a few control words; vklb_destroy frees it.
+ */
+#ifndef VKLB_H
+#define VKLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VKLB_OK = 0,
+  VKLB_ERR_ARG = -1,          /* invalid argument (null pointer, bad size or parameter) */
+  VKLB_ERR_NOMEM = -2,        /* device or host allocation failed */
+  VKLB_ERR_CUDA = -3,         /* a CUDA runtime call failed (no device, launch error) */
+  VKLB_ERR_NONPHYSICAL = -4,  /* NaN or non-positive h / rho / p produced on the device */
+  VKLB_ERR_CFL = -5,          /* fixed lattice speed below max |lambda| (Eq. 28 violated) */
+  VKLB_ERR_TIMEOUT = -6,      /* reserved: a bounded device wait gave up */
+  VKLB_ERR_STATE = -7,        /* call out of order (e.g. stepping before vklb_set_state) */
+  VKLB_ERR_UNSUPPORTED = -8   /* combination not built (e.g. D1Q3 with MHD-GLM) */
+} vklb_status;
+
+/* Hyperbolic system (Sec. 2.1).  gamma: ideal-gas index (Euler, MHD-GLM);
+ * g: gravity (shallow water); ch_factor: c_h = ch_factor * max c_f for the GLM
+ * cleaning speed (Sec. 5.3, the paper uses 6); adv_speed: (a_x, a_y) for
+ * scalar advection. */
+typedef enum { VKLB_ADVECT = 0, VKLB_SWE = 1, VKLB_EULER = 2, VKLB_MHD_GLM = 3 } vklb_system_kind;
+typedef struct {
+  int32_t kind;
+  double gamma;
+  double g;
+  double ch_factor;
+  double adv_speed[2];
+} vklb_system;
+
+/* Lattices: D1Q3 (Sec. 2.2, Fig. 1) and D2Q5 (Sec. 3.4, Eq. 38). */
+typedef enum { VKLB_D1Q3 = 13, VKLB_D2Q5 = 25 } vklb_lattice;
+
+/* Uniform grid: n cells per dimension on [lo, hi]; cell centres
+ * x_i = lo + (i + 1/2) dx.  D2Q5 needs dx == dy (Sec. 3.4). */
+typedef struct {
+  int32_t dim;
+  int64_t n[2];
+  double lo[2];
+  double hi[2];
+} vklb_grid;
+
+/* Boundary kinds per side: periodic (Eq. 37) or characteristic /
+ * non-reflecting (Eqs. 33-36, 1D only). */
+typedef enum { VKLB_BC_PERIODIC = 0, VKLB_BC_CHARACTERISTIC = 1 } vklb_bc_kind;
+typedef struct {
+  int32_t lo[2];
+  int32_t hi[2];
+} vklb_bc;
+
+/* Equilibrium set (Sec. 2.2 / 3.1): weighted upwind (Eqs. 22-27, parameters c and
+ * k), centered flux (Eqs. 8-10, 39: c = 1/Q, F+- = F/2) or discontinuous upwind
+ * (Eqs. 12-18: c = 0, Heaviside weights).  omega: relaxation in (0, 2]
+ * (Sec. 2.3); cfl: nu of Eq. (29).  The paper uses c = 0.05, k = 2, nu = 0.9
+ * (Sec. 5). */
+typedef enum { VKLB_SET_WEIGHTED = 0, VKLB_SET_CENTERED = 1, VKLB_SET_DISCONTINUOUS = 2 } vklb_set;
+typedef struct {
+  int32_t set;
+  double c;
+  double k;
+  double omega;
+  double cfl;
+} vklb_weight;
+
+/* Arithmetic: FP64 everywhere; FP32 distributions and arithmetic (conservation
+ * totals still reduce in FP64); BF16 storage of the distributions with FP32
+ * arithmetic (an explicit experiment: half the bytes, lower accuracy). */
+typedef enum { VKLB_FP64 = 0, VKLB_FP32 = 1, VKLB_BF16_STORE = 2 } vklb_precision;
+
+typedef struct vklb_sim vklb_sim;
+typedef struct vklb_batch vklb_batch;
+
+/* Static facts about a simulation (filled by vklb_info). */
+typedef struct {
+  int32_t p;                 /* conserved fields */
+  int32_t q;                 /* lattice velocities (3 or 5) */
+  int32_t precision;         /* vklb_precision */
+  int32_t store_bytes;       /* bytes per stored distribution value */
+  int64_t cells;             /* nx * ny */
+  int64_t bytes_per_lup;     /* algorithmic bytes per cell update: 2 * q * p * store_bytes */
+  int64_t state_bytes;       /* bytes of one distribution buffer */
+  double dx;
+  int32_t tile_x, tile_y;    /* launch shape of the step kernel */
+  int32_t kernels_per_step;  /* kernel launches one vklb_step(1) makes */
+} vklb_info_t;
+
+/* Create a simulation.  dt > 0 fixes xi = dx / dt for every step; dt <= 0
+ * selects the adaptive CFL rule of Eq. (29).  cuda_stream is a cudaStream_t
+ * (NULL: the legacy default stream) on which every kernel of this simulation
+ * runs.  Parameter checks (returning VKLB_ERR_ARG): omega in (0, 2]
+ * (Sec. 2.3); 0 < cfl <= 1 (Eq. 28); dx == dy for D2Q5 (Sec. 3.4); lattice
+ * matches grid->dim; characteristic boundaries only on D1Q3.  On success
+ * *out owns two device distribution buffers of q * p * cells values each. */
+int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid,
+                const vklb_bc* bc, const vklb_weight* weight, double dt,
+                int32_t precision, void* cuda_stream, vklb_sim** out);
+
+/* Set U(x, 0) (layout above; host pointer if on_device == 0, else device).
+ * Initialises as Fig. 5: xi_0 from Eq. (29) over U (and c_h for MHD-GLM), then
+ * f_q = f_q^eq(U) (Eq. 2b); t = 0, steps = 0.  Enqueued on the stream; the
+ * host buffer may be reused when the call returns. */
+int vklb_set_state(vklb_sim* sim, const double* U, int32_t on_device);
+
+/* Launch shape of the step kernel (tile_x cells along x by tile_y rows per
+ * block); 0 keeps the built-in default.  Used by the autotuner. */
+int vklb_set_tiling(vklb_sim* sim, int32_t tile_x, int32_t tile_y);
+
+/* Enqueue n steps of Fig. 5 (no host synchronisation). */
+int vklb_step(vklb_sim* sim, int64_t n);
+
+/* Step until t == t_end: every step takes xi_eff = m dx / (t_end - t) with m
+ * the number of CFL-limited steps left, so the last step ends on t_end.
+ * Synchronises a few times to read t. */
+int vklb_step_to(vklb_sim* sim, double t_end);
+
+/* Wait for the stream and return the latched device error (VKLB_OK if none). */
+int vklb_sync(vklb_sim* sim);
+
+/* U = sum_q f_q (Eq. 3) in the layout above, as double, into a host (on_device
+ * == 0) or device buffer of p * cells values.  Synchronises. */
+int vklb_moments(vklb_sim* sim, double* U_out, int32_t on_device);
+
+/* totals[k] = sum_x U_k(x) dx^D in FP64 with a fixed reduction order
+ * (deterministic), host buffer of p values.  Conserved to rounding on periodic
+ * grids (Thm 4.3).  Synchronises. */
+int vklb_conservation_totals(vklb_sim* sim, double* totals);
+
+/* Current time, steps taken and the lattice speed of the next step.  Synchronises. */
+int vklb_time(vklb_sim* sim, double* t, int64_t* steps, double* xi);
+
+int vklb_info(const vklb_sim* sim, vklb_info_t* info);
+
+/* Device pointer of the current distribution buffer f[q][k][y][x] (store
+ * type of the precision).  Borrowed; valid until the next vklb_step. */
+int vklb_device_state(const vklb_sim* sim, void** f_dev);
+
+/* Checkpoint / resume: the blob holds the distributions and the control words
+ * (t, steps, xi, c_h).  vklb_state_bytes gives its size; get synchronises. */
+int vklb_state_bytes(const vklb_sim* sim, size_t* bytes);
+int vklb_get_state(vklb_sim* sim, void* blob, size_t bytes);
+int vklb_put_state(vklb_sim* sim, const void* blob, size_t bytes);
+
+int vklb_destroy(vklb_sim* sim);
+const char* vklb_strerror(int status);
+
+/* Batched form: n simulations with the same system kind, D2Q5 lattice,
+ * periodic boundaries, weight and precision but any grid sizes advance together,
+ * one kernel launch per step over a tile work-list spanning all of them (each
+ * keeps its own xi and c_h).  The batch borrows the simulations (they must
+ * outlive it); their per-simulation state is left as if each had been stepped
+ * alone.  vklb_batch_step(n) enqueues n steps on the stream of the first
+ * simulation; use_graph != 0 captures them in a CUDA graph and replays it. */
+int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out);
+int vklb_batch_set_tiling(vklb_batch* b, int32_t tile_x, int32_t tile_y);
+int vklb_batch_step(vklb_batch* b, int64_t n, int32_t use_graph);
+int vklb_batch_destroy(vklb_batch* b);
+
+/* Number of kernel launches this process has enqueued through the library. */
+int64_t vklb_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VKLB_H */

@@ -1,0 +1,54 @@
+// Device-resident control words of one simulation and the per-step scalars
+// (lattice speed xi, cleaning speed c_h, time t) derived from them.
+#pragma once
+#include "vk_math.cuh"
+
+namespace vk {
+
+// Three rotating slots: step n reads slot n % 3 (maxima over U^n, t^n), reduces
+// the maxima over U^{n+1} into slot (n+1) % 3 and clears slot (n+2) % 3, whose
+// last reader was step n-1 (already finished: kernel boundary).
+struct Ctl {
+  unsigned long long m1[3];  // max over cells and directions of max_j |lambda_j| (no cleaning waves), double bits
+  unsigned long long m2[3];  // MHD-GLM: max over cells and directions of c_f, double bits
+  double t[3];               // time at the start of the step that reads the slot
+  double xi_used[3];         // xi of the step that read the slot (for host queries)
+  long long nsteps;          // steps taken (launches that reached t_end do not count)
+  int32_t err;               // bit 0: non-physical state; bit 1: CFL violated (fixed xi)
+  int32_t pad;
+};
+
+enum : int { ERR_NONPHYS = 1, ERR_CFL = 2 };
+
+struct StepScalars {
+  double xi;   // lattice speed of this step
+  double ch;   // cleaning speed of this step (MHD-GLM)
+  bool done;   // t_end reached: nothing to do
+};
+
+// xi of Eq. (29) (or the fixed xi), c_h = ch_factor * max c_f (reading R4) and
+// the landing rule of vklb_step_to (reading R3).  Every thread of every block
+// evaluates it from the same words, so all agree.
+VK_HD StepScalars step_scalars(const Ctl* ctl, int slot, bool mhd, double ch_factor, double inv_nu,
+                               double fixed_xi, double t_end, double dx) {
+  StepScalars s;
+  double m1 = bits_to_double(ctl->m1[slot]);
+  double m2 = bits_to_double(ctl->m2[slot]);
+  s.ch = mhd ? ch_factor * m2 : 0.0;
+  double lam = mhd ? fmax(m1, s.ch) : m1;
+  s.xi = fixed_xi > 0.0 ? fixed_xi : lam * inv_nu;
+  s.done = false;
+  if (t_end > 0.0) {
+    double rem = t_end - ctl->t[slot];
+    if (rem <= 1e-14 * fmax(1.0, fabs(t_end))) {
+      s.done = true;
+    } else {
+      double m = ceil(rem * s.xi / dx - 1e-9);
+      if (m < 1.0) m = 1.0;
+      s.xi = m * dx / rem;
+    }
+  }
+  return s;
+}
+
+}  // namespace vk

@@ -1,0 +1,593 @@
+// CUDA kernels of the VKLB step (Sec. 3.5, Fig. 5) for sm_103a.
+//
+// Layout in HBM: f[q][k][y][x] (structure of arrays), q = lattice velocity,
+// k = conserved field, x fastest; two such buffers ping-pong between steps.
+//
+// step2d_kernel: one launch = one step on D2Q5, periodic (Eq. 37).  A block owns
+// a tile of TX columns x TY rows; each thread owns one column and marches up the
+// tile.  Per cell it loads the 5p values of f^n (coalesced across the warp),
+// forms U = sum_q f_q (Eq. 3), splits F^(1), F^(2) (Eqs. 25-27), builds the
+// equilibria (Eq. 41), collides (Eq. 42) and streams by pull (Eq. 43):
+//     f^{n+1}_q(x) = f*_q(x - v_q).
+// The x neighbours' f*_1, f*_2 go through shared memory (three row buffers, one
+// barrier per row); f*_4 of the row below and f*_5 of the row above stay in
+// registers.  The 1-cell ring around the tile is recomputed for just the one
+// component that streams inward (x ring: f*_1 / f*_2 from the x split only;
+// y ring: f*_4 / f*_5 from the y split only).  Knowing every f^{n+1} of its tile,
+// the block then forms U^{n+1} and reduces max_j |lambda_j| (and the MHD fast
+// speed) into the control words, so xi_{n+1} (Eq. 29) is ready for the next
+// launch with no second pass over f.
+//
+// step1d_kernel: D1Q3, one block runs many steps (tiny 1D grids are latency
+// bound), with the characteristic boundary (Eqs. 33-36) or periodic wrap.
+#pragma once
+#include "vk_ctl.cuh"
+#include "vk_systems.cuh"
+
+namespace vk {
+
+struct SysParams {
+  double gamma, g, ax, ay;
+};
+
+template <class Sys> VK_HD Sys make_sys(const SysParams& s);
+template <> VK_HD Advect<float, 1> make_sys(const SysParams& s) { Advect<float, 1> r; r.a[0] = (float)s.ax; r.a[1] = (float)s.ay; return r; }
+template <> VK_HD Advect<double, 1> make_sys(const SysParams& s) { Advect<double, 1> r; r.a[0] = s.ax; r.a[1] = s.ay; return r; }
+template <> VK_HD Advect<float, 2> make_sys(const SysParams& s) { Advect<float, 2> r; r.a[0] = (float)s.ax; r.a[1] = (float)s.ay; return r; }
+template <> VK_HD Advect<double, 2> make_sys(const SysParams& s) { Advect<double, 2> r; r.a[0] = s.ax; r.a[1] = s.ay; return r; }
+template <> VK_HD SWE<float, 1> make_sys(const SysParams& s) { SWE<float, 1> r; r.g = (float)s.g; return r; }
+template <> VK_HD SWE<double, 1> make_sys(const SysParams& s) { SWE<double, 1> r; r.g = s.g; return r; }
+template <> VK_HD SWE<float, 2> make_sys(const SysParams& s) { SWE<float, 2> r; r.g = (float)s.g; return r; }
+template <> VK_HD SWE<double, 2> make_sys(const SysParams& s) { SWE<double, 2> r; r.g = s.g; return r; }
+template <> VK_HD Euler<float, 1> make_sys(const SysParams& s) { Euler<float, 1> r; r.gamma = (float)s.gamma; return r; }
+template <> VK_HD Euler<double, 1> make_sys(const SysParams& s) { Euler<double, 1> r; r.gamma = s.gamma; return r; }
+template <> VK_HD Euler<float, 2> make_sys(const SysParams& s) { Euler<float, 2> r; r.gamma = (float)s.gamma; return r; }
+template <> VK_HD Euler<double, 2> make_sys(const SysParams& s) { Euler<double, 2> r; r.gamma = s.gamma; return r; }
+template <> VK_HD MHDGLM<float> make_sys(const SysParams& s) { MHDGLM<float> r; r.gamma = (float)s.gamma; return r; }
+template <> VK_HD MHDGLM<double> make_sys(const SysParams& s) { MHDGLM<double> r; r.gamma = s.gamma; return r; }
+
+// Everything one step of one simulation needs.
+template <class T>
+struct StepArgs {
+  T* f[2];         // ping-pong distribution buffers
+  int parity;      // f[parity] holds f^n
+  int nx, ny;
+  double dx, c, omega, k, inv_nu, fixed_xi, t_end, ch_factor;
+  int set;
+  int bc_lo, bc_hi;  // 1D: 0 periodic, 1 characteristic
+  Ctl* ctl;
+  int slot;        // n % 3
+  SysParams sp;
+};
+
+// Which post-collision components a cell must produce.
+enum CollideMode { C_FULL = 0, C_Q1 = 1, C_Q2 = 2, C_Q4 = 3, C_Q5 = 4 };
+
+// Collision (Eq. 42) of one D2Q5 cell with the weighted equilibria of Eq. (41):
+//   f1 = c U + F(1,+)/xi, f2 = c U - F(1,-)/xi, f4 = c U + F(2,+)/xi,
+//   f5 = c U - F(2,-)/xi, f3 = U - (f1 + f2 + f4 + f5) (= Eq. 41's rest term).
+template <class Sys, class T, class R, int MODE>
+__device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict__ fin, size_t plane,
+                                             size_t idx, R xinv, R c, R om, int set, R k, R ch,
+                                             R (&out)[5][Sys::P]) {
+  constexpr int P = Sys::P;
+  R f[5][P];
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int i = 0; i < P; ++i) f[q][i] = Store<T>::ld(fin + (size_t)(q * P + i) * plane + idx);
+  R U[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
+  R Fp[P], F[P];
+  if (MODE == C_FULL || MODE == C_Q1 || MODE == C_Q2) {
+    sys.split(U, 0, set, k, ch, Fp, F);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      R e1 = c * U[i] + Fp[i] * xinv;
+      R e2 = c * U[i] - (F[i] - Fp[i]) * xinv;
+      out[0][i] = f[0][i] + om * (e1 - f[0][i]);
+      out[1][i] = f[1][i] + om * (e2 - f[1][i]);
+      if (MODE == C_FULL) out[2][i] = e1 + e2;  // partial sum of the rest term
+    }
+  }
+  if (MODE == C_FULL || MODE == C_Q4 || MODE == C_Q5) {
+    sys.split(U, 1, set, k, ch, Fp, F);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      R e4 = c * U[i] + Fp[i] * xinv;
+      R e5 = c * U[i] - (F[i] - Fp[i]) * xinv;
+      out[3][i] = f[3][i] + om * (e4 - f[3][i]);
+      out[4][i] = f[4][i] + om * (e5 - f[4][i]);
+      if (MODE == C_FULL) {
+        R e3 = U[i] - (out[2][i] + e4 + e5);
+        out[2][i] = f[2][i] + om * (e3 - f[2][i]);
+      }
+    }
+  }
+}
+
+template <class R> __device__ __forceinline__ R round_store(R v, const float*) { return v; }
+template <class R> __device__ __forceinline__ R round_store(R v, const double*) { return v; }
+template <class R> __device__ __forceinline__ R round_store(R v, const __nv_bfloat16*) {
+  return (R)__bfloat162float(__float2bfloat16_rn((float)v));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide max of (a, b) and OR of bad; thread 0 commits them to slot s1.
+__device__ __forceinline__ void commit_max(double a, double b, bool bad, Ctl* ctl, int s1) {
+  __shared__ double red[2][32];
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = 0;
+  __syncthreads();
+  a = warp_max(a);
+  b = warp_max(b);
+  if (bad) sbad = 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    a = lane < nw ? red[0][lane] : 0.0;
+    b = lane < nw ? red[1][lane] : 0.0;
+    a = warp_max(a);
+    b = warp_max(b);
+    if (lane == 0) {
+      atomicMax(&ctl->m1[s1], double_to_bits(a));
+      atomicMax(&ctl->m2[s1], double_to_bits(b));
+      if (sbad) atomicOr(&ctl->err, ERR_NONPHYS);
+    }
+  }
+}
+
+// Per-step bookkeeping done once per launch by block 0: t^{n+1}, clearing the
+// slot of step n+2, the fixed-xi CFL check.
+__device__ __forceinline__ void step_bookkeeping(Ctl* ctl, int slot, const StepScalars& sc, double dx,
+                                                 double fixed_xi, bool mhd) {
+  const int s1 = (slot + 1) % 3, s2 = (slot + 2) % 3;
+  ctl->nsteps += 1;
+  ctl->t[s1] = ctl->t[slot] + dx / sc.xi;
+  ctl->xi_used[slot] = sc.xi;
+  ctl->m1[s2] = 0ull;
+  ctl->m2[s2] = 0ull;
+  if (fixed_xi > 0.0) {
+    double lam = bits_to_double(ctl->m1[slot]);
+    if (mhd) lam = fmax(lam, sc.ch);
+    if (lam > fixed_xi * (1.0 + 1e-12)) atomicOr(&ctl->err, ERR_CFL);
+  }
+}
+
+// ------------------------------------------------------------------ D2Q5 step
+template <class Sys, class T, class R>
+__device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by, int TX, int TY,
+                                            unsigned char* smem) {
+  constexpr int P = Sys::P;
+  const Sys sys = make_sys<Sys>(a.sp);
+  const int tx = threadIdx.x;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int nx = a.nx, ny = a.ny;
+  const int w = min(TX, nx - x0), h = min(TY, ny - y0);
+  const int x = x0 + tx;
+  const bool act = tx < w;
+  const size_t plane = (size_t)nx * ny;
+  const T* __restrict__ fin = a.f[a.parity];
+  T* __restrict__ fout = a.f[a.parity ^ 1];
+  const StepScalars sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+  const int s1 = (a.slot + 1) % 3;
+  if (sc.done) {
+    // t_end already reached: this launch is a no-op that keeps the ping-pong
+    // consistent (f^{n+1} = f^n, same control words).
+    if (act)
+      for (int r = 0; r < h; ++r)
+        for (int i = 0; i < 5 * P; ++i) {
+          size_t o = (size_t)i * plane + (size_t)(y0 + r) * nx + x;
+          fout[o] = fin[o];
+        }
+    if (bx == 0 && by == 0 && tx == 0) {
+      const int s2 = (a.slot + 2) % 3;
+      a.ctl->t[s1] = a.ctl->t[a.slot];
+      a.ctl->m1[s1] = a.ctl->m1[a.slot];
+      a.ctl->m2[s1] = a.ctl->m2[a.slot];
+      a.ctl->m1[s2] = 0ull;
+      a.ctl->m2[s2] = 0ull;
+    }
+    return;
+  }
+  if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, sc, a.dx, a.fixed_xi, Sys::MHD);
+  const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, om = (R)a.omega, kk = (R)a.k;
+  const int set = a.set;
+
+  R* rb1 = reinterpret_cast<R*>(smem);   // [3][P][TX]  f*_1 of the row
+  R* rb2 = rb1 + 3 * P * TX;             // [3][P][TX]  f*_2 of the row
+  R* ringL = rb2 + 3 * P * TX;           // [P][TY]     f*_1 at x0 - 1
+  R* ringR = ringL + P * TY;             // [P][TY]     f*_2 at x0 + w
+
+  // x ring: only the component that streams into the tile, from the x split
+  for (int t = tx; t < 2 * h; t += blockDim.x) {
+    const int side = t >= h;
+    const int r = side ? t - h : t;
+    const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
+    const size_t idx = (size_t)(y0 + r) * nx + xr;
+    R o[5][P];
+    if (!side) {
+      collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+      for (int i = 0; i < P; ++i) ringL[i * TY + r] = o[0][i];
+    } else {
+      collide_d2q5<Sys, T, R, C_Q2>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+      for (int i = 0; i < P; ++i) ringR[i * TY + r] = o[1][i];
+    }
+  }
+
+  R f4prev[P], f3c[P], f4c[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) f4prev[i] = f3c[i] = f4c[i] = R(0);
+  if (act) {
+    R o[5][P];
+    const int yb = (y0 - 1 + ny) % ny;
+    collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)yb * nx + x, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+    for (int i = 0; i < P; ++i) f4prev[i] = o[3][i];
+    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)y0 * nx + x, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      rb1[i * TX + tx] = o[0][i];
+      rb2[i * TX + tx] = o[1][i];
+      f3c[i] = o[2][i];
+      f4c[i] = o[3][i];
+    }
+  }
+
+  double m1 = 0.0, m2 = 0.0;
+  bool bad = false;
+  for (int r = 0; r < h; ++r) {
+    const int j = y0 + r;
+    R f5n[P], f3n[P], f4n[P];
+    const int nb = (r + 1) % 3, cb = r % 3;
+    if (act) {
+      R o[5][P];
+      if (r + 1 < h) {
+        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)(j + 1) * nx + x, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          rb1[(nb * P + i) * TX + tx] = o[0][i];
+          rb2[(nb * P + i) * TX + tx] = o[1][i];
+          f3n[i] = o[2][i];
+          f4n[i] = o[3][i];
+          f5n[i] = o[4][i];
+        }
+      } else {
+        const int yt = (y0 + h) % ny;
+        collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)yt * nx + x, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          f5n[i] = o[4][i];
+          f3n[i] = f4n[i] = R(0);
+        }
+      }
+    }
+    __syncthreads();
+    if (act) {
+      const size_t base = (size_t)j * nx + x;
+      R U[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        R g1 = tx == 0 ? ringL[i * TY + r] : rb1[(cb * P + i) * TX + tx - 1];
+        R g2 = tx == w - 1 ? ringR[i * TY + r] : rb2[(cb * P + i) * TX + tx + 1];
+        R g3 = f3c[i], g4 = f4prev[i], g5 = f5n[i];
+        Store<T>::st(fout + (size_t)(0 * P + i) * plane + base, g1);
+        Store<T>::st(fout + (size_t)(1 * P + i) * plane + base, g2);
+        Store<T>::st(fout + (size_t)(2 * P + i) * plane + base, g3);
+        Store<T>::st(fout + (size_t)(3 * P + i) * plane + base, g4);
+        Store<T>::st(fout + (size_t)(4 * P + i) * plane + base, g5);
+        const T* tp = nullptr;
+        U[i] = round_store(g1, tp) + round_store(g2, tp) + round_store(g3, tp) + round_store(g4, tp) +
+               round_store(g5, tp);
+      }
+      R a1, a2, b1, b2;
+      sys.speeds(U, 0, a1, a2);
+      sys.speeds(U, 1, b1, b2);
+      m1 = fmax(m1, (double)vmax(a1, b1));
+      m2 = fmax(m2, (double)vmax(a2, b2));
+      bad |= !sys.physical(U);
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      f4prev[i] = f4c[i];
+      f3c[i] = f3n[i];
+      f4c[i] = f4n[i];
+    }
+  }
+  commit_max(m1, m2, bad, a.ctl, s1);
+}
+
+template <class Sys, class T, class R>
+__global__ void step2d_kernel(StepArgs<T> a, int TX, int TY) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
+}
+
+// Batched form: one launch advances every simulation of the batch by one step.
+// work[b] = (simulation, tile x, tile y) of block b; desc[s] describes
+// simulation s with its parity / slot at the batch's step 0; step_off moves them.
+struct BatchWork {
+  int sim, bx, by;
+};
+
+template <class Sys, class T, class R>
+__global__ void step2d_batch_kernel(const StepArgs<T>* __restrict__ desc, const BatchWork* __restrict__ work,
+                                    int step_off, int TX, int TY) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BatchWork wk = work[blockIdx.x];
+  StepArgs<T> a = desc[wk.sim];
+  a.parity = (a.parity + step_off) & 1;
+  a.slot = (a.slot + step_off) % 3;
+  step2d_tile<Sys, T, R>(a, wk.bx, wk.by, TX, TY, smem);
+}
+
+// ------------------------------------------------------------------ D1Q3 steps
+// Weighted set in 1D, Eqs. (22)-(24): f1 = c U + F+/xi, f3 = c U - F-/xi,
+// f2 = (1 - 2c) U - (F+ - F-)/xi = U - f1 - f3.
+template <class Sys, class R>
+__device__ __forceinline__ void feq_d1q3(const Sys& sys, const R* U, R xinv, R c, int set, R k,
+                                         R (&e)[3][Sys::P]) {
+  constexpr int P = Sys::P;
+  R Fp[P], F[P];
+  sys.split(U, 0, set, k, R(0), Fp, F);
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    e[0][i] = c * U[i] + Fp[i] * xinv;
+    e[2][i] = c * U[i] - (F[i] - Fp[i]) * xinv;
+    e[1][i] = U[i] - (e[0][i] + e[2][i]);
+  }
+}
+
+template <class Sys, class T, class R>
+__global__ void step1d_kernel(StepArgs<T> a, int nsteps) {
+  constexpr int P = Sys::P;
+  const Sys sys = make_sys<Sys>(a.sp);
+  const int nx = a.nx;
+  const size_t plane = (size_t)nx;
+  const bool cl = a.bc_lo == 1, chi = a.bc_hi == 1;
+  __shared__ R Ub[2][P];
+  __shared__ double red[32];
+  int par = a.parity, slot = a.slot;
+  volatile Ctl* vc = a.ctl;
+  for (int st = 0; st < nsteps; ++st) {
+    StepScalars sc = step_scalars(a.ctl, slot, false, 0.0, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+    if (sc.done) break;
+    const T* fin = a.f[par];
+    T* fout = a.f[par ^ 1];
+    const R xinv = (R)(1.0 / sc.xi), c = (R)a.c, om = (R)a.omega, kk = (R)a.k;
+    // collide (Eq. 42) and push-stream (Eq. 43)
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      R f[3][P], U[P], e[3][P];
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int s = 0; s < P; ++s) f[q][s] = Store<T>::ld(fin + (size_t)(q * P + s) * plane + i);
+#pragma unroll
+      for (int s = 0; s < P; ++s) U[s] = f[0][s] + f[1][s] + f[2][s];
+      feq_d1q3<Sys, R>(sys, U, xinv, c, a.set, kk, e);
+      int ip = i + 1, im = i - 1;
+      bool okp = true, okm = true;
+      if (ip == nx) { if (chi) okp = false; else ip = 0; }
+      if (im < 0) { if (cl) okm = false; else im = nx - 1; }
+#pragma unroll
+      for (int s = 0; s < P; ++s) {
+        R g0 = f[0][s] + om * (e[0][s] - f[0][s]);
+        R g1 = f[1][s] + om * (e[1][s] - f[1][s]);
+        R g2 = f[2][s] + om * (e[2][s] - f[2][s]);
+        if (okp) Store<T>::st(fout + (size_t)(0 * P + s) * plane + ip, g0);
+        Store<T>::st(fout + (size_t)(1 * P + s) * plane + i, g1);
+        if (okm) Store<T>::st(fout + (size_t)(2 * P + s) * plane + im, g2);
+      }
+    }
+    // characteristic boundaries (Eqs. 33-35): U_b^{n+1} from U^n at x_b and its neighbour
+    if (threadIdx.x < 2 && ((threadIdx.x == 0 && cl) || (threadIdx.x == 1 && chi))) {
+      const int side = threadIdx.x;
+      const int ib = side == 0 ? 0 : nx - 1, in = side == 0 ? 1 : nx - 2;
+      R Ubv[P], Un[P], dU[P], rhs[P];
+#pragma unroll
+      for (int s = 0; s < P; ++s) {
+        Ubv[s] = Un[s] = R(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          Ubv[s] += Store<T>::ld(fin + (size_t)(q * P + s) * plane + ib);
+          Un[s] += Store<T>::ld(fin + (size_t)(q * P + s) * plane + in);
+        }
+        dU[s] = side == 0 ? Un[s] - Ubv[s] : Ubv[s] - Un[s];
+      }
+      sys.char_rhs(Ubv, dU, side, rhs);
+#pragma unroll
+      for (int s = 0; s < P; ++s) Ub[side][s] = Ubv[s] - rhs[s] * xinv;
+    }
+    __syncthreads();
+    // moments of f^{n+1} (Eq. 3) and the CFL max (Eq. 29)
+    double m1 = 0.0;
+    bool bad = false;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      R U[P];
+      if (i == 0 && cl) {
+#pragma unroll
+        for (int s = 0; s < P; ++s) U[s] = Ub[0][s];
+      } else if (i == nx - 1 && chi) {
+#pragma unroll
+        for (int s = 0; s < P; ++s) U[s] = Ub[1][s];
+      } else {
+#pragma unroll
+        for (int s = 0; s < P; ++s)
+          U[s] = Store<T>::ld(fout + (size_t)(0 * P + s) * plane + i) + Store<T>::ld(fout + (size_t)(1 * P + s) * plane + i) +
+                 Store<T>::ld(fout + (size_t)(2 * P + s) * plane + i);
+      }
+      R l1, l2;
+      sys.speeds(U, 0, l1, l2);
+      m1 = fmax(m1, (double)l1);
+      bad |= !sys.physical(U);
+    }
+    m1 = warp_max(m1);
+    const bool wbad = __any_sync(0xffffffffu, bad);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) red[wid] = wbad ? -1.0 : m1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double mm = 0.0;
+      bool bb = false;
+      for (int wv = 0; wv < nw; ++wv) {
+        if (red[wv] < 0.0) bb = true;
+        else mm = fmax(mm, red[wv]);
+      }
+      const int s1 = (slot + 1) % 3, s2 = (slot + 2) % 3;
+      vc->t[s1] = vc->t[slot] + a.dx / sc.xi;
+      vc->xi_used[slot] = sc.xi;
+      vc->nsteps = vc->nsteps + 1;
+      vc->m1[s1] = double_to_bits(mm);
+      vc->m2[s1] = 0ull;
+      vc->m1[s2] = 0ull;
+      vc->m2[s2] = 0ull;
+      if (bb) vc->err |= ERR_NONPHYS;
+      if (a.fixed_xi > 0.0 && bits_to_double(vc->m1[slot]) > a.fixed_xi * (1.0 + 1e-12)) vc->err |= ERR_CFL;
+    }
+    __syncthreads();
+    // boundary distributions f_q(x_b) = f_q^eq(U_b^{n+1}) with xi_{n+1} (Eq. 36, R11)
+    if (threadIdx.x < 2 && ((threadIdx.x == 0 && cl) || (threadIdx.x == 1 && chi))) {
+      const int side = threadIdx.x;
+      const int ib = side == 0 ? 0 : nx - 1;
+      const double xn = a.fixed_xi > 0.0 ? a.fixed_xi : bits_to_double(vc->m1[(slot + 1) % 3]) * a.inv_nu;
+      R e[3][P];
+      feq_d1q3<Sys, R>(sys, Ub[side], (R)(1.0 / xn), c, a.set, kk, e);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int s = 0; s < P; ++s) Store<T>::st(fout + (size_t)(q * P + s) * plane + ib, e[q][s]);
+    }
+    __syncthreads();
+    par ^= 1;
+    slot = (slot + 1) % 3;
+  }
+}
+
+// ------------------------------------------------------------- init / moments
+// Max of the wave speeds over U (double, [p][cells]) into slot 0.
+template <class Sys, class R, int DIM>
+__global__ void init_max_kernel(const double* __restrict__ U, size_t cells, SysParams sp, Ctl* ctl) {
+  constexpr int P = Sys::P;
+  const Sys sys = make_sys<Sys>(sp);
+  double m1 = 0.0, m2 = 0.0;
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
+    R u[P];
+#pragma unroll
+    for (int s = 0; s < P; ++s) u[s] = (R)U[s * cells + i];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      R a, b;
+      sys.speeds(u, d, a, b);
+      m1 = fmax(m1, (double)a);
+      m2 = fmax(m2, (double)b);
+    }
+    bad |= !sys.physical(u);
+  }
+  commit_max(m1, m2, bad, ctl, 0);
+}
+
+// f_q = f_q^eq(U) (Eq. 2b) with xi_0, c_h^0 from slot 0.
+template <class Sys, class T, class R, int DIM>
+__global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, StepArgs<T> a) {
+  constexpr int P = Sys::P;
+  const Sys sys = make_sys<Sys>(a.sp);
+  const StepScalars sc = step_scalars(a.ctl, 0, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, -1.0, a.dx);
+  const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, kk = (R)a.k;
+  T* f = a.f[a.parity];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
+    R u[P];
+#pragma unroll
+    for (int s = 0; s < P; ++s) u[s] = (R)U[s * cells + i];
+    if (DIM == 1) {
+      R e[3][P];
+      feq_d1q3<Sys, R>(sys, u, xinv, c, a.set, kk, e);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int s = 0; s < P; ++s) Store<T>::st(f + (size_t)(q * P + s) * cells + i, e[q][s]);
+    } else {
+      R Fp[P], F[P], e[5][P];
+      sys.split(u, 0, a.set, kk, ch, Fp, F);
+#pragma unroll
+      for (int s = 0; s < P; ++s) {
+        e[0][s] = c * u[s] + Fp[s] * xinv;
+        e[1][s] = c * u[s] - (F[s] - Fp[s]) * xinv;
+      }
+      sys.split(u, 1, a.set, kk, ch, Fp, F);
+#pragma unroll
+      for (int s = 0; s < P; ++s) {
+        e[3][s] = c * u[s] + Fp[s] * xinv;
+        e[4][s] = c * u[s] - (F[s] - Fp[s]) * xinv;
+        e[2][s] = u[s] - (e[0][s] + e[1][s] + e[3][s] + e[4][s]);
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int s = 0; s < P; ++s) Store<T>::st(f + (size_t)(q * P + s) * cells + i, e[q][s]);
+    }
+  }
+}
+
+// U_k = sum_q f_q,k (Eq. 3), as double.
+template <class T, int P, int Q>
+__global__ void moments_kernel(const T* __restrict__ f, size_t cells, double* __restrict__ U) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int s = 0; s < P; ++s) {
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc += (double)Store<T>::ld(f + (size_t)(q * P + s) * cells + i);
+      U[s * cells + i] = acc;
+    }
+  }
+}
+
+// Conservation totals, pass 1: block b sums the cells of its fixed chunk in
+// FP64 (fixed thread order, shuffle tree), writing part[s][b].
+template <class T, int P, int Q>
+__global__ void totals_pass1(const T* __restrict__ f, size_t cells, double* __restrict__ part) {
+  __shared__ double red[32];
+  const size_t chunk = (cells + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * chunk, hi = min(cells, lo + chunk);
+  for (int s = 0; s < P; ++s) {
+    double acc = 0.0;
+    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc += (double)Store<T>::ld(f + (size_t)(q * P + s) * cells + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      part[(size_t)s * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 2: one thread per field sums the partials in block order.
+__global__ void totals_pass2(const double* __restrict__ part, int nblocks, int P, double scale,
+                             double* __restrict__ out) {
+  const int s = threadIdx.x;
+  if (s >= P) return;
+  double t = 0.0;
+  for (int b = 0; b < nblocks; ++b) t += part[(size_t)s * nblocks + b];
+  out[s] = t * scale;
+}
+
+}  // namespace vk

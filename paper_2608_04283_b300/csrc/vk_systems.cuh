@@ -1,0 +1,391 @@
+// Hyperbolic systems and their weighted upwind flux splitting, closed form.
+//
+// For each system, split(U, d) returns the physical flux F = F^(d)(U) and
+//     F+ = sum_j alpha(lambda_j) phi_j r_j,   phi = P^-1 F          (Eqs. 16, 25, 26)
+// with alpha of Eq. (27) normalised by max_j |lambda_j| of the cell and direction;
+// F- = F - F+ (Eq. 11).  The eigen-structures are written in closed form:
+//   * shallow water (Eq. 52): r = (1, u -+ c, v), phi_{1,3} = h (u -+ c/2) / 2, and
+//     the shear wave carries no flux (phi_2 = 0);
+//   * Euler (Eq. 54): homogeneous of degree one, so phi_j = lambda_j l_j.U and
+//     F+ = rho/(2 gamma) [w1 (1, u-a, v, H-ua) + 2(gamma-1) w2 (1, u, v, q^2/2)
+//                         + w3 (1, u+a, v, H+ua)],  w_j = alpha_j lambda_j;
+//   * MHD-GLM (Eq. 58): the 9x9 Jacobian is block upper triangular in
+//     (rho, m, E, B_t | B_n, psi).  The 7 MHD waves use primitive eigenvectors
+//     with the Roe-Balsara normalisation (alpha_f, alpha_s, beta); the two
+//     cleaning waves +-c_h have phi_+- = (psi +- c_h B_n)/2, and their coupling to
+//     the MHD block enters through divided differences of alpha (see split_x).
+// The y direction is the x direction applied to the state with x and y swapped.
+#pragma once
+#include "vk_math.cuh"
+
+namespace vk {
+
+// ----------------------------------------------------------------- advection
+template <class R, int DIM>
+struct Advect {
+  static constexpr int P = 1;
+  static constexpr bool MHD = false;
+  R a[2];
+  VK_HD void split(const R* U, int d, int set, R k, R ch, R* Fp, R* F) const {
+    R ad = a[d];
+    F[0] = ad * U[0];
+    R lm = vabs(ad);
+    R al = lm > R(0) ? alpha_w(ad, k / lm, set) : R(0.5);
+    Fp[0] = al * F[0];
+  }
+  // m1: max |lambda| along d; m2: unused (fast speed of MHD)
+  VK_HD void speeds(const R* U, int d, R& m1, R& m2) const { m1 = vabs(a[d]); m2 = R(0); }
+  VK_HD bool physical(const R* U) const { return U[0] == U[0]; }
+  // Characteristic boundary (Eqs. 33-35): P diag(lambda_j, outgoing only) P^-1 dU.
+  VK_HD void char_rhs(const R* U, const R* dU, int side, R* out) const {
+    R l = a[0];
+    bool out_going = side == 0 ? l < R(0) : l > R(0);
+    out[0] = out_going ? l * dU[0] : R(0);
+  }
+};
+
+// ------------------------------------------------------------- shallow water
+template <class R, int DIM>
+struct SWE {
+  static constexpr int P = DIM + 1;
+  static constexpr bool MHD = false;
+  R g;
+  VK_HD void split(const R* U, int d, int set, R k, R ch, R* Fp, R* F) const {
+    const int in = 1 + d;           // normal momentum
+    const int it = 2 - d;           // tangential momentum (2D)
+    R h = U[0];
+    R ih = vrcp(h);
+    R un = U[in] * ih;
+    R c = vsqrt(g * h);
+    F[0] = U[in];
+    F[in] = U[in] * un + R(0.5) * g * h * h;
+    R ut = R(0);
+    if (DIM == 2) {
+      ut = U[it] * ih;
+      F[it] = U[in] * ut;
+    }
+    if (set == SET_CENTERED) {
+      for (int i = 0; i < P; ++i) Fp[i] = R(0.5) * F[i];
+      return;
+    }
+    R lmax = vabs(un) + c;
+    R kl = k * vrcp(lmax);
+    R a1 = alpha_w(un - c, kl, set);
+    R a3 = alpha_w(un + c, kl, set);
+    R p1 = a1 * R(0.5) * h * (un - R(0.5) * c);   // alpha_1 phi_1
+    R p3 = a3 * R(0.5) * h * (un + R(0.5) * c);   // alpha_3 phi_3
+    Fp[0] = p1 + p3;
+    Fp[in] = p1 * (un - c) + p3 * (un + c);
+    if (DIM == 2) Fp[it] = (p1 + p3) * ut;
+  }
+  VK_HD void speeds(const R* U, int d, R& m1, R& m2) const {
+    R h = U[0];
+    m1 = vabs(U[1 + d] / h) + vsqrt(g * h);
+    m2 = R(0);
+  }
+  VK_HD bool physical(const R* U) const { return U[0] > R(0); }
+  // Characteristic boundary (Eqs. 33-35), 1D: P diag(lambda_j, outgoing only) P^-1 dU
+  // with r_{1,2} = (1, u -+ c), l_1 = (u + c, -1)/(2c), l_2 = (c - u, 1)/(2c).
+  VK_HD void char_rhs(const R* U, const R* dU, int side, R* out) const {
+    R h = U[0], u = U[1] / h, c = vsqrt(g * h);
+    R i2c = R(0.5) / c;
+    R w1 = ((u + c) * dU[0] - dU[1]) * i2c;
+    R w2 = ((c - u) * dU[0] + dU[1]) * i2c;
+    R l1 = u - c, l2 = u + c;
+    R k1 = (side == 0 ? l1 < R(0) : l1 > R(0)) ? l1 * w1 : R(0);
+    R k2 = (side == 0 ? l2 < R(0) : l2 > R(0)) ? l2 * w2 : R(0);
+    out[0] = k1 + k2;
+    out[1] = k1 * l1 + k2 * l2;
+  }
+};
+
+// ------------------------------------------------------------------- Euler
+template <class R, int DIM>
+struct Euler {
+  static constexpr int P = DIM + 2;
+  static constexpr bool MHD = false;
+  R gamma;
+  VK_HD void split(const R* U, int d, int set, R k, R ch, R* Fp, R* F) const {
+    const int in = 1 + d, it = 2 - d, ie = P - 1;
+    R rho = U[0];
+    R ir = vrcp(rho);
+    R un = U[in] * ir;
+    R ut = DIM == 2 ? U[it] * ir : R(0);
+    R q2 = un * un + ut * ut;
+    R E = U[ie];
+    R p = (gamma - R(1)) * (E - R(0.5) * rho * q2);
+    F[0] = U[in];
+    F[in] = U[in] * un + p;
+    if (DIM == 2) F[it] = U[it] * un;
+    F[ie] = un * (E + p);
+    if (set == SET_CENTERED) {
+      for (int i = 0; i < P; ++i) Fp[i] = R(0.5) * F[i];
+      return;
+    }
+    R a = vsqrt(gamma * p * ir);
+    R H = (E + p) * ir;
+    R lmax = vabs(un) + a;
+    R kl = k * vrcp(lmax);
+    R l1 = un - a, l3 = un + a;
+    R w1 = alpha_w(l1, kl, set) * l1;
+    R w2 = alpha_w(un, kl, set) * un * R(2) * (gamma - R(1));
+    R w3 = alpha_w(l3, kl, set) * l3;
+    R s = R(0.5) * rho / gamma;
+    R wsum = w1 + w2 + w3;
+    Fp[0] = s * wsum;
+    Fp[in] = s * (w1 * l1 + w2 * un + w3 * l3);
+    if (DIM == 2) Fp[it] = s * wsum * ut;
+    Fp[ie] = s * (w1 * (H - un * a) + w2 * R(0.5) * q2 + w3 * (H + un * a));
+  }
+  VK_HD void speeds(const R* U, int d, R& m1, R& m2) const {
+    R rho = U[0];
+    R un = U[1 + d] / rho;
+    R ut = DIM == 2 ? U[2 - d] / rho : R(0);
+    R p = (gamma - R(1)) * (U[P - 1] - R(0.5) * rho * (un * un + ut * ut));
+    m1 = vabs(un) + vsqrt(gamma * p / rho);
+    m2 = R(0);
+  }
+  VK_HD bool physical(const R* U) const {
+    R rho = U[0];
+    R ke = U[1] * U[1];
+    if (DIM == 2) ke += U[2] * U[2];
+    R p = (gamma - R(1)) * (U[P - 1] - R(0.5) * ke / rho);
+    return rho > R(0) && p > R(0);
+  }
+  // Characteristic boundary (Eqs. 33-35), 1D Euler: r = (1, u-a, H-ua), (1, u, u^2/2),
+  // (1, u+a, H+ua); with b1 = (gamma-1)/a^2, b2 = b1 u^2/2 the dual rows are
+  // l1 = ((b2 + u/a), -(b1 u + 1/a), b1)/2, l2 = (1 - b2, b1 u, -b1),
+  // l3 = ((b2 - u/a), -(b1 u - 1/a), b1)/2.
+  VK_HD void char_rhs(const R* U, const R* dU, int side, R* out) const {
+    R rho = U[0], u = U[1] / rho, E = U[2];
+    R p = (gamma - R(1)) * (E - R(0.5) * rho * u * u);
+    R a = vsqrt(gamma * p / rho), H = (E + p) / rho;
+    R b1 = (gamma - R(1)) / (a * a), b2 = R(0.5) * u * u * b1, ia = R(1) / a;
+    R w1 = R(0.5) * ((b2 + u * ia) * dU[0] - (b1 * u + ia) * dU[1] + b1 * dU[2]);
+    R w2 = (R(1) - b2) * dU[0] + b1 * u * dU[1] - b1 * dU[2];
+    R w3 = R(0.5) * ((b2 - u * ia) * dU[0] - (b1 * u - ia) * dU[1] + b1 * dU[2]);
+    R lam[3] = {u - a, u, u + a};
+    R k[3] = {w1, w2, w3};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      bool og = side == 0 ? lam[j] < R(0) : lam[j] > R(0);
+      k[j] = og ? lam[j] * k[j] : R(0);
+    }
+    out[0] = k[0] + k[1] + k[2];
+    out[1] = k[0] * (u - a) + k[1] * u + k[2] * (u + a);
+    out[2] = k[0] * (H - u * a) + k[1] * R(0.5) * u * u + k[2] * (H + u * a);
+  }
+};
+
+// ----------------------------------------------------------------- MHD-GLM
+// Fast-wave normalisation (alpha_f, alpha_s) of Roe & Balsara, computed from
+//   d = c_f^2 - c_s^2 = sqrt((a^2 - bx^2)^2 + bt^2 (2 a^2 + 2 bx^2 + bt^2)),
+// X = a^2 - c_s^2, Y = c_f^2 - a^2 with X Y = a^2 bt^2 (no cancellation):
+//   alpha_f^2 = X / d, alpha_s^2 = Y / d.  At d = 0 (bt = 0, a = |bx|) all three
+// speeds coincide and any basis of the eigenspace serves; alpha_f = alpha_s = 1/sqrt 2.
+template <class T>
+VK_HD void mhd_norm(T a2, T bx2, T bt2, T& af, T& as, T& d) {
+  T dd = (a2 - bx2) * (a2 - bx2) + bt2 * (T(2) * a2 + T(2) * bx2 + bt2);
+  d = vsqrt(dd);
+  T b2 = bx2 + bt2;
+  T X, Y;
+  if (a2 >= b2) {
+    X = T(0.5) * ((a2 - b2) + d);
+    Y = X > T(0) ? a2 * bt2 / X : T(0);
+  } else {
+    Y = T(0.5) * ((b2 - a2) + d);
+    X = Y > T(0) ? a2 * bt2 / Y : T(0);
+  }
+  if (d > T(0)) {
+    af = vsqrt(vmax(X / d, T(0)));
+    as = vsqrt(vmax(Y / d, T(0)));
+  } else {
+    af = as = T(0.70710678118654752440);
+  }
+}
+
+template <class R>
+struct MHDGLM {
+  static constexpr int P = 9;
+  static constexpr bool MHD = true;
+  R gamma;
+
+  // Fast speed c_f along the normal whose field component is bn.
+  VK_HD R fast(R rho, R p, R bn, R bb) const {
+    R ir = R(1) / rho;
+    R a2 = gamma * p * ir;
+    R bx2 = bn * bn * ir;
+    R bt2 = (bb - bn * bn) * ir;
+    R dd = (a2 - bx2) * (a2 - bx2) + bt2 * (R(2) * a2 + R(2) * bx2 + bt2);
+    return vsqrt(R(0.5) * (a2 + bx2 + bt2 + vsqrt(dd)));
+  }
+
+  VK_HD void speeds(const R* U, int d, R& m1, R& m2) const {
+    R rho = U[0];
+    R bb = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
+    R ke = (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho;
+    R p = (gamma - R(1)) * (U[4] - R(0.5) * ke - R(0.5) * bb);
+    R cf = fast(rho, p, U[5 + d], bb);
+    m1 = vabs(U[1 + d] / rho) + cf;
+    m2 = cf;
+  }
+
+  VK_HD bool physical(const R* U) const {
+    R rho = U[0];
+    R bb = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
+    R ke = (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho;
+    R p = (gamma - R(1)) * (U[4] - R(0.5) * ke - R(0.5) * bb);
+    return rho > R(0) && p > R(0);
+  }
+
+  VK_HD void split(const R* Uin, int d, int set, R k, R ch, R* Fp, R* F) const {
+    if (d == 0) {
+      split_x(Uin, set, k, ch, Fp, F);
+      return;
+    }
+    // y direction: swap (mx, my) and (Bx, By), split along x, swap back
+    R U[9] = {Uin[0], Uin[2], Uin[1], Uin[3], Uin[4], Uin[6], Uin[5], Uin[7], Uin[8]};
+    R a[9], b[9];
+    split_x(U, set, k, ch, a, b);
+    Fp[0] = a[0]; Fp[1] = a[2]; Fp[2] = a[1]; Fp[3] = a[3]; Fp[4] = a[4];
+    Fp[5] = a[6]; Fp[6] = a[5]; Fp[7] = a[7]; Fp[8] = a[8];
+    F[0] = b[0]; F[1] = b[2]; F[2] = b[1]; F[3] = b[3]; F[4] = b[4];
+    F[5] = b[6]; F[6] = b[5]; F[7] = b[7]; F[8] = b[8];
+  }
+
+  VK_HD void split_x(const R* U, int set, R k, R ch, R* Fp, R* F) const {
+    const R rho = U[0];
+    const R ir = vrcp(rho);
+    const R u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+    const R E = U[4], bx = U[5], by = U[6], bz = U[7], psi = U[8];
+    const R bt2 = by * by + bz * bz;
+    const R bb = bx * bx + bt2;
+    const R q2 = u * u + v * v + w * w;
+    const R gm1 = gamma - R(1);
+    const R p = gm1 * (E - R(0.5) * rho * q2 - R(0.5) * bb);
+    const R pt = p + R(0.5) * bb;
+    const R bu = bx * u + by * v + bz * w;
+    // physical flux, Eq. (58), x component
+    F[0] = U[1];
+    F[1] = U[1] * u + pt - bx * bx;
+    F[2] = U[2] * u - bx * by;
+    F[3] = U[3] * u - bx * bz;
+    F[4] = (E + pt) * u - bu * bx;
+    F[5] = psi;
+    F[6] = u * by - bx * v;
+    F[7] = u * bz - bx * w;
+    F[8] = ch * ch * bx;
+    if (set == SET_CENTERED) {
+      for (int i = 0; i < 9; ++i) Fp[i] = R(0.5) * F[i];
+      return;
+    }
+    // wave speeds
+    const R a2 = gamma * p * ir;
+    const R bx2 = bx * bx * ir;
+    const R btt = bt2 * ir;
+    R af, as, dcs;
+    mhd_norm<R>(a2, bx2, btt, af, as, dcs);
+    if (sizeof(R) == 4 && !(dcs > R(1e-3) * (a2 + bx2 + btt))) {
+      // near-degenerate fast/slow/Alfven speeds: normalise in FP64
+      double af64, as64, d64;
+      mhd_norm<double>((double)a2, (double)bx2, (double)btt, af64, as64, d64);
+      af = (R)af64;
+      as = (R)as64;
+    }
+    const R cf2 = R(0.5) * (a2 + bx2 + btt + dcs);
+    const R cf = vsqrt(cf2);
+    const R cs = cf2 > R(0) ? vsqrt(a2 * bx2 / cf2) : R(0);
+    const R ca = vsqrt(bx2);
+    const R a = vsqrt(a2);
+    const R sr = vsqrt(rho);
+    R bty, btz;
+    const R bt = vsqrt(bt2);
+    if (bt > R(1e-30) * (vabs(bx) + R(1e-30))) {
+      R ib = vrcp(bt);
+      bty = by * ib;
+      btz = bz * ib;
+    } else {
+      bty = btz = R(0.70710678118654752440);
+    }
+    const R s = bx >= R(0) ? R(1) : R(-1);
+
+    // sigmoid weights, normalised by the largest |lambda| of the cell (R1)
+    const R lmax = vmax(vabs(u) + cf, ch);
+    const R kl = k * vrcp(lmax);
+    const R lam[7] = {u - cf, u - ca, u - cs, u, u + cs, u + ca, u + cf};
+    R al[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) al[j] = alpha_w(lam[j], kl, set);
+    const R alp = alpha_w(ch, kl, set), alm = alpha_w(-ch, kl, set);
+    const R php = R(0.5) * (psi + ch * bx), phm = R(0.5) * (psi - ch * bx);
+
+    // G = M^-1 F7 (primitive increments of the flux), ga = M^-1 dF7/dBx
+    const R ia2 = vrcp(a2);
+    const R Gr = F[0];
+    const R Gu = (F[1] - u * F[0]) * ir, Gv = (F[2] - v * F[0]) * ir, Gw = (F[3] - w * F[0]) * ir;
+    const R Gp = gm1 * (F[4] + R(0.5) * q2 * F[0] - (u * F[1] + v * F[2] + w * F[3]) - (by * F[6] + bz * F[7]));
+    const R Gy = F[6], Gz = F[7];
+    const R hu = -gamma * bx * ir, hv = -by * ir, hw = -bz * ir;
+    const R hp = gm1 * (v * by + w * bz), hy = -v, hz = -w;
+
+    // shared projections
+    const R isr_a = vrcp(sr * a);
+    const R Tu = R(0.5) * Gu * ia2, Tt = R(0.5) * s * (bty * Gv + btz * Gw) * ia2;
+    const R Tp = R(0.5) * Gp * ia2 * ir, TB = R(0.5) * (bty * Gy + btz * Gz) * isr_a;
+    const R Tq = R(0.5) * (-btz * Gv + bty * Gw), TQ = R(0.5) * s * (btz * Gy - bty * Gz) * vrcp(sr);
+    const R Hu = R(0.5) * hu * ia2, Ht = R(0.5) * s * (bty * hv + btz * hw) * ia2;
+    const R Hp = R(0.5) * hp * ia2 * ir, HB = R(0.5) * (bty * hy + btz * hz) * isr_a;
+    const R Hq = R(0.5) * (-btz * hv + bty * hw), HQ = R(0.5) * s * (btz * hy - bty * hz) * vrcp(sr);
+
+    // l_j . G and l_j . ga in the order of lam[]
+    R lG[7], lH[7];
+    lG[0] = -(af * cf * Tu - as * cs * Tt) + af * Tp + as * TB;   // fast -
+    lG[6] = +(af * cf * Tu - as * cs * Tt) + af * Tp + as * TB;   // fast +
+    lG[2] = -(as * cs * Tu + af * cf * Tt) + as * Tp - af * TB;   // slow -
+    lG[4] = +(as * cs * Tu + af * cf * Tt) + as * Tp - af * TB;   // slow +
+    lG[1] = Tq - TQ;                                              // Alfven -
+    lG[5] = Tq + TQ;                                              // Alfven +
+    lG[3] = Gr - Gp * ia2;                                        // entropy
+    lH[0] = -(af * cf * Hu - as * cs * Ht) + af * Hp + as * HB;
+    lH[6] = +(af * cf * Hu - as * cs * Ht) + af * Hp + as * HB;
+    lH[2] = -(as * cs * Hu + af * cf * Ht) + as * Hp - af * HB;
+    lH[4] = +(as * cs * Hu + af * cf * Ht) + as * Hp - af * HB;
+    lH[1] = Hq - HQ;
+    lH[5] = Hq + HQ;
+    lH[3] = -hp * ia2;
+
+    // coefficients c_j = alpha_j l_j.G + l_j.ga sum_+- phi_+- (alpha_j - alpha_+-)/(lam_j - lam_+-)
+    R cc[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      R ddp = alpha_dd(al[j], lam[j], alp, ch, kl, lmax, set);
+      R ddm = alpha_dd(al[j], lam[j], alm, -ch, kl, lmax, set);
+      cc[j] = al[j] * lG[j] + lH[j] * (php * ddp + phm * ddm);
+    }
+    // S = sum_j c_j r_j (primitive), then F+_7 = M S
+    const R fs = cc[6] + cc[0], fd = cc[6] - cc[0];
+    const R ss = cc[4] + cc[2], sd = cc[4] - cc[2];
+    const R as_ = cc[5] + cc[1], ad = cc[5] - cc[1];
+    const R Sr = rho * (af * fs + as * ss) + cc[3];
+    const R Su = af * cf * fd + as * cs * sd;
+    const R tr = s * (-as * cs * fd + af * cf * sd);
+    const R Sv = bty * tr - btz * as_;
+    const R Sw = btz * tr + bty * as_;
+    const R Sp = rho * a2 * (af * fs + as * ss);
+    const R tb = sr * a * (as * fs - af * ss);
+    const R Sy = bty * tb + s * sr * btz * ad;
+    const R Sz = btz * tb - s * sr * bty * ad;
+    Fp[0] = Sr;
+    Fp[1] = u * Sr + rho * Su;
+    Fp[2] = v * Sr + rho * Sv;
+    Fp[3] = w * Sr + rho * Sw;
+    Fp[4] = Sp / gm1 + R(0.5) * q2 * Sr + rho * (u * Su + v * Sv + w * Sw) + by * Sy + bz * Sz;
+    Fp[6] = Sy;
+    Fp[7] = Sz;
+    // cleaning block: e_+- = (1, +-c_h)
+    Fp[5] = alp * php + alm * phm;
+    Fp[8] = ch * (alp * php - alm * phm);
+  }
+};
+
+}  // namespace vk

@@ -1,0 +1,660 @@
+// Host side of libvklb.so: the C ABI declared in include/vklb.h.
+//
+// A simulation owns two device buffers of q * p * cells distributions (store
+// type of its precision), one Ctl block of control words and small scratch
+// buffers for reductions.  Every kernel runs on the simulation's stream; no call
+// synchronises except those documented as synchronising.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vk_kernels.cuh"
+#include "vklb.h"
+
+using namespace vk;
+
+namespace {
+std::atomic<long long> g_launches{0};
+
+const int kRedBlocks = 296;  // conservation-total pass 1: 2 blocks per SM on 148 SMs
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? VKLB_OK : VKLB_ERR_CUDA; }
+}  // namespace
+
+struct Ops;
+
+struct vklb_sim {
+  int kind, lattice, dim, P, Q, prec, store_bytes;
+  int64_t nx, ny, cells;
+  double dx, ch_factor;
+  SysParams sp;
+  int set;
+  double c, k, omega, cfl, fixed_xi;
+  int bc_lo, bc_hi;
+  cudaStream_t stream;
+  void* f[2];
+  int cur;                 // f[cur] holds the current state
+  long long launched;      // step launches so far (slot = launched % 3)
+  Ctl* ctl;
+  double* part;            // [p][kRedBlocks] partial sums
+  double* dvec;            // [p] device totals
+  double* stage;           // [p][cells] double staging for set_state / moments
+  int tile_x, tile_y;
+  bool ready;
+  const Ops* ops;
+};
+
+struct Ops {
+  int (*init)(vklb_sim*, const double*);
+  int (*step)(vklb_sim*, int64_t, double);   // enqueue n step launches with t_end
+  int (*moments)(vklb_sim*, double*);
+  int (*totals)(vklb_sim*, double*);
+  int (*batch)(vklb_batch*, int64_t, int);
+  size_t real_bytes;
+  size_t args_bytes;
+};
+
+struct vklb_batch {
+  std::vector<vklb_sim*> sims;
+  int tile_x, tile_y;
+  void* d_desc;
+  BatchWork* d_work;
+  int nwork;
+  std::vector<unsigned char> h_desc;
+  cudaStream_t stream;
+  const Ops* ops;
+  int64_t graph_n;
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+};
+
+namespace {
+
+template <class T>
+StepArgs<T> make_args(const vklb_sim* s, double t_end) {
+  StepArgs<T> a;
+  a.f[0] = (T*)s->f[0];
+  a.f[1] = (T*)s->f[1];
+  a.parity = s->cur;
+  a.nx = (int)s->nx;
+  a.ny = (int)s->ny;
+  a.dx = s->dx;
+  a.c = s->c;
+  a.omega = s->omega;
+  a.k = s->k;
+  a.inv_nu = 1.0 / s->cfl;
+  a.fixed_xi = s->fixed_xi;
+  a.t_end = t_end;
+  a.ch_factor = s->ch_factor;
+  a.set = s->set;
+  a.bc_lo = s->bc_lo;
+  a.bc_hi = s->bc_hi;
+  a.ctl = s->ctl;
+  a.slot = (int)(s->launched % 3);
+  a.sp = s->sp;
+  return a;
+}
+
+int grid_for(size_t cells, int block) {
+  size_t g = (cells + block - 1) / block;
+  if (g > 148 * 16) g = 148 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <class Sys, class T, class R, int DIM>
+struct Impl {
+  static constexpr int P = Sys::P;
+  static constexpr int Q = DIM == 1 ? 3 : 5;
+
+  static int init(vklb_sim* s, const double* dU) {
+    StepArgs<T> a = make_args<T>(s, -1.0);
+    a.parity = s->cur;
+    const int blk = 256;
+    init_max_kernel<Sys, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, s->sp, s->ctl);
+    init_feq_kernel<Sys, T, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, a);
+    g_launches += 2;
+    return cuda_status(cudaGetLastError());
+  }
+
+  static size_t smem_bytes(int tx, int ty) { return (size_t)(6 * P * tx + 2 * P * ty) * sizeof(R); }
+
+  static int step(vklb_sim* s, int64_t n, double t_end) {
+    if constexpr (DIM == 1) {
+      int blk = (int)(((s->nx + 31) / 32) * 32);
+      if (blk > 1024) blk = 1024;
+      if (blk < 64) blk = 64;
+      StepArgs<T> a = make_args<T>(s, t_end);
+      // n steps in one launch; with t_end the kernel may stop early, so the
+      // caller re-reads the step counter (vklb_step_to).
+      step1d_kernel<Sys, T, R><<<1, blk, 0, s->stream>>>(a, (int)n);
+      g_launches += 1;
+      int st = cuda_status(cudaGetLastError());
+      if (st) return st;
+      if (t_end <= 0.0) {
+        s->cur ^= (int)(n & 1);
+        s->launched += n;
+      }
+      return VKLB_OK;
+    } else {
+      const int TX = s->tile_x, TY = s->tile_y;
+      const size_t sm = smem_bytes(TX, TY);
+      static bool attr_set = false;
+      if (!attr_set) {
+        cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+      }
+      dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
+      for (int64_t i = 0; i < n; ++i) {
+        StepArgs<T> a = make_args<T>(s, t_end);
+        step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
+        s->cur ^= 1;
+        s->launched += 1;
+      }
+      g_launches += n;
+      return cuda_status(cudaGetLastError());
+    }
+  }
+
+  static int moments(vklb_sim* s, double* dU) {
+    const int blk = 256;
+    moments_kernel<T, P, Q><<<grid_for(s->cells, blk), blk, 0, s->stream>>>((const T*)s->f[s->cur], (size_t)s->cells, dU);
+    g_launches += 1;
+    return cuda_status(cudaGetLastError());
+  }
+
+  static int totals(vklb_sim* s, double* host) {
+    totals_pass1<T, P, Q><<<kRedBlocks, 256, 0, s->stream>>>((const T*)s->f[s->cur], (size_t)s->cells, s->part);
+    double scale = DIM == 1 ? s->dx : s->dx * s->dx;
+    totals_pass2<<<1, 32, 0, s->stream>>>(s->part, kRedBlocks, P, scale, s->dvec);
+    g_launches += 2;
+    int st = cuda_status(cudaGetLastError());
+    if (st) return st;
+    return cuda_status(cudaMemcpyAsync(host, s->dvec, sizeof(double) * P, cudaMemcpyDeviceToHost, s->stream));
+  }
+};
+
+template <class Sys, class T, class R, int DIM>
+struct BatchImpl {
+  static void launch(vklb_batch* b, int64_t n) {
+    if constexpr (DIM == 2) {
+    const int TX = b->tile_x, TY = b->tile_y;
+    const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes(TX, TY);
+    for (int64_t i = 0; i < n; ++i)
+      step2d_batch_kernel<Sys, T, R><<<b->nwork, TX, sm, b->stream>>>((const StepArgs<T>*)b->d_desc, b->d_work,
+                                                                       (int)i, TX, TY);
+    }
+  }
+  static int step(vklb_batch* b, int64_t n, int use_graph) {
+    if constexpr (DIM != 2) {
+      return VKLB_ERR_UNSUPPORTED;
+    } else {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set = true;
+    }
+    StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
+    for (size_t i = 0; i < b->sims.size(); ++i) h[i] = make_args<T>(b->sims[i], -1.0);
+    int st = cuda_status(cudaMemcpyAsync(b->d_desc, h, b->h_desc.size(), cudaMemcpyHostToDevice, b->stream));
+    if (st) return st;
+    if (use_graph) {
+      if (!b->gexec || b->graph_n != n) {
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->gexec = nullptr;
+        b->graph = nullptr;
+        if ((st = cuda_status(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)))) return st;
+        launch(b, n);
+        if ((st = cuda_status(cudaStreamEndCapture(b->stream, &b->graph)))) return st;
+        if ((st = cuda_status(cudaGraphInstantiate(&b->gexec, b->graph, 0)))) return st;
+        b->graph_n = n;
+      }
+      if ((st = cuda_status(cudaGraphLaunch(b->gexec, b->stream)))) return st;
+    } else {
+      launch(b, n);
+    }
+    g_launches += n;
+    if ((st = cuda_status(cudaGetLastError()))) return st;
+    for (vklb_sim* s : b->sims) {
+      s->cur ^= (int)(n & 1);
+      s->launched += n;
+    }
+    return VKLB_OK;
+    }
+  }
+};
+
+template <class Sys, class T, class R, int DIM>
+const Ops* ops_of() {
+  static const Ops o = {&Impl<Sys, T, R, DIM>::init,    &Impl<Sys, T, R, DIM>::step,
+                        &Impl<Sys, T, R, DIM>::moments, &Impl<Sys, T, R, DIM>::totals,
+                        &BatchImpl<Sys, T, R, DIM>::step, sizeof(R), sizeof(StepArgs<T>)};
+  return &o;
+}
+
+template <template <class, int> class S, int DIM>
+const Ops* pick_prec(int prec) {
+  if (prec == VKLB_FP64) return ops_of<S<double, DIM>, double, double, DIM>();
+  if (prec == VKLB_FP32) return ops_of<S<float, DIM>, float, float, DIM>();
+  return ops_of<S<float, DIM>, __nv_bfloat16, float, DIM>();
+}
+
+const Ops* pick_ops(int kind, int dim, int prec) {
+  if (kind == VKLB_ADVECT) return dim == 1 ? pick_prec<Advect, 1>(prec) : pick_prec<Advect, 2>(prec);
+  if (kind == VKLB_SWE) return dim == 1 ? pick_prec<SWE, 1>(prec) : pick_prec<SWE, 2>(prec);
+  if (kind == VKLB_EULER) return dim == 1 ? pick_prec<Euler, 1>(prec) : pick_prec<Euler, 2>(prec);
+  if (kind == VKLB_MHD_GLM && dim == 2) {
+    if (prec == VKLB_FP64) return ops_of<MHDGLM<double>, double, double, 2>();
+    if (prec == VKLB_FP32) return ops_of<MHDGLM<float>, float, float, 2>();
+    return ops_of<MHDGLM<float>, __nv_bfloat16, float, 2>();
+  }
+  return nullptr;
+}
+
+int fields_of(int kind, int dim) {
+  switch (kind) {
+    case VKLB_ADVECT: return 1;
+    case VKLB_SWE: return dim + 1;
+    case VKLB_EULER: return dim + 2;
+    case VKLB_MHD_GLM: return 9;
+  }
+  return 0;
+}
+
+int read_ctl(vklb_sim* s, Ctl* h) {
+  int st = cuda_status(cudaMemcpyAsync(h, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  if (st) return st;
+  return cuda_status(cudaStreamSynchronize(s->stream));
+}
+
+int err_of(const Ctl& h) {
+  if (h.err & ERR_NONPHYS) return VKLB_ERR_NONPHYSICAL;
+  if (h.err & ERR_CFL) return VKLB_ERR_CFL;
+  return VKLB_OK;
+}
+
+void free_sim(vklb_sim* s) {
+  if (!s) return;
+  cudaFree(s->f[0]);
+  cudaFree(s->f[1]);
+  cudaFree(s->ctl);
+  cudaFree(s->part);
+  cudaFree(s->dvec);
+  cudaFree(s->stage);
+  delete s;
+}
+
+const uint32_t kMagic = 0x564b4c42u;  // "VKLB"
+struct BlobHeader {
+  uint32_t magic, kind, P, Q, prec, slot;
+  int64_t nx, ny, launched;
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* vklb_strerror(int status) {
+  switch (status) {
+    case VKLB_OK: return "ok";
+    case VKLB_ERR_ARG: return "invalid argument";
+    case VKLB_ERR_NOMEM: return "out of memory";
+    case VKLB_ERR_CUDA: return "CUDA runtime error";
+    case VKLB_ERR_NONPHYSICAL: return "non-physical state (NaN or non-positive depth/density/pressure)";
+    case VKLB_ERR_CFL: return "fixed lattice speed below the largest wave speed (CFL violated)";
+    case VKLB_ERR_TIMEOUT: return "bounded device wait gave up";
+    case VKLB_ERR_STATE: return "call out of order";
+    case VKLB_ERR_UNSUPPORTED: return "unsupported combination";
+  }
+  return "unknown status";
+}
+
+int64_t vklb_launch_count(void) { return g_launches.load(); }
+
+int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, const vklb_bc* bc,
+                const vklb_weight* weight, double dt, int32_t precision, void* cuda_stream, vklb_sim** out) {
+  if (!sys || !grid || !bc || !weight || !out) return VKLB_ERR_ARG;
+  *out = nullptr;
+  const int dim = grid->dim;
+  if (!((lattice == VKLB_D1Q3 && dim == 1) || (lattice == VKLB_D2Q5 && dim == 2))) return VKLB_ERR_ARG;
+  if (precision < VKLB_FP64 || precision > VKLB_BF16_STORE) return VKLB_ERR_ARG;
+  if (weight->set < 0 || weight->set > 2) return VKLB_ERR_ARG;
+  if (!(weight->omega > 0.0 && weight->omega <= 2.0)) return VKLB_ERR_ARG;   // Sec. 2.3
+  if (!(weight->cfl > 0.0 && weight->cfl <= 1.0)) return VKLB_ERR_ARG;       // Eq. (28)
+  if (!(weight->k >= 0.0)) return VKLB_ERR_ARG;
+  const int64_t nx = grid->n[0], ny = dim == 2 ? grid->n[1] : 1;
+  if (nx < 1 || ny < 1 || nx > (1 << 30) || ny > (1 << 30)) return VKLB_ERR_ARG;
+  if (nx < 3 && dim == 1) return VKLB_ERR_ARG;
+  const double dx = (grid->hi[0] - grid->lo[0]) / (double)nx;
+  if (!(dx > 0.0)) return VKLB_ERR_ARG;
+  if (dim == 2) {
+    const double dy = (grid->hi[1] - grid->lo[1]) / (double)ny;
+    if (!(fabs(dx - dy) <= 1e-12 * dx)) return VKLB_ERR_ARG;                  // Sec. 3.4
+  }
+  for (int i = 0; i < dim; ++i)
+    if (bc->lo[i] != bc->hi[i] && dim == 2) return VKLB_ERR_ARG;
+  if (dim == 2 && (bc->lo[0] != VKLB_BC_PERIODIC || bc->lo[1] != VKLB_BC_PERIODIC)) return VKLB_ERR_UNSUPPORTED;
+  if (dim == 1 && ((bc->lo[0] != VKLB_BC_PERIODIC && bc->lo[0] != VKLB_BC_CHARACTERISTIC) ||
+                   (bc->hi[0] != VKLB_BC_PERIODIC && bc->hi[0] != VKLB_BC_CHARACTERISTIC)))
+    return VKLB_ERR_ARG;
+  if (dim == 1 && (bc->lo[0] == VKLB_BC_PERIODIC) != (bc->hi[0] == VKLB_BC_PERIODIC)) return VKLB_ERR_ARG;
+  const Ops* ops = pick_ops(sys->kind, dim, precision);
+  if (!ops) return VKLB_ERR_UNSUPPORTED;
+  if ((sys->kind == VKLB_EULER || sys->kind == VKLB_MHD_GLM) && !(sys->gamma > 1.0)) return VKLB_ERR_ARG;
+  if (sys->kind == VKLB_SWE && !(sys->g > 0.0)) return VKLB_ERR_ARG;
+  if (sys->kind == VKLB_MHD_GLM && !(sys->ch_factor > 0.0)) return VKLB_ERR_ARG;
+
+  vklb_sim* s = new (std::nothrow) vklb_sim();
+  if (!s) return VKLB_ERR_NOMEM;
+  s->kind = sys->kind;
+  s->lattice = lattice;
+  s->dim = dim;
+  s->P = fields_of(sys->kind, dim);
+  s->Q = dim == 1 ? 3 : 5;
+  s->prec = precision;
+  s->store_bytes = precision == VKLB_FP64 ? 8 : (precision == VKLB_FP32 ? 4 : 2);
+  s->nx = nx;
+  s->ny = ny;
+  s->cells = nx * ny;
+  s->dx = dx;
+  s->ch_factor = sys->ch_factor;
+  s->sp.gamma = sys->gamma;
+  s->sp.g = sys->g;
+  s->sp.ax = sys->adv_speed[0];
+  s->sp.ay = sys->adv_speed[1];
+  s->set = weight->set;
+  // centered set: c = 1/Q (Eqs. 8-10, 39); discontinuous set: c = 0 (Eqs. 12-14)
+  s->c = weight->set == VKLB_SET_CENTERED ? 1.0 / s->Q : (weight->set == VKLB_SET_DISCONTINUOUS ? 0.0 : weight->c);
+  s->k = weight->k;
+  s->omega = weight->omega;
+  s->cfl = weight->cfl;
+  s->fixed_xi = dt > 0.0 ? dx / dt : 0.0;
+  s->bc_lo = bc->lo[0];
+  s->bc_hi = bc->hi[0];
+  s->stream = (cudaStream_t)cuda_stream;
+  s->tile_x = 64;
+  s->tile_y = 16;
+  s->ops = ops;
+  const size_t fbytes = (size_t)s->Q * s->P * (size_t)s->cells * s->store_bytes;
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&s->f[0], fbytes)) != cudaSuccess || (e = cudaMalloc(&s->f[1], fbytes)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&s->ctl, sizeof(Ctl))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&s->part, sizeof(double) * s->P * kRedBlocks)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&s->dvec, sizeof(double) * s->P)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&s->stage, sizeof(double) * s->P * (size_t)s->cells)) != cudaSuccess) {
+    free_sim(s);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? VKLB_ERR_NOMEM : VKLB_ERR_CUDA;
+  }
+  *out = s;
+  return VKLB_OK;
+}
+
+int vklb_destroy(vklb_sim* s) {
+  if (!s) return VKLB_ERR_ARG;
+  cudaStreamSynchronize(s->stream);
+  free_sim(s);
+  return cuda_status(cudaGetLastError());
+}
+
+int vklb_set_state(vklb_sim* s, const double* U, int32_t on_device) {
+  if (!s || !U) return VKLB_ERR_ARG;
+  const size_t bytes = sizeof(double) * s->P * (size_t)s->cells;
+  int st = cuda_status(cudaMemcpyAsync(s->stage, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                       s->stream));
+  if (st) return st;
+  if ((st = cuda_status(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), s->stream)))) return st;
+  s->cur = 0;
+  s->launched = 0;
+  if ((st = s->ops->init(s, s->stage))) return st;
+  if (!on_device) {
+    // the caller may reuse U as soon as we return
+    if ((st = cuda_status(cudaStreamSynchronize(s->stream)))) return st;
+  }
+  s->ready = true;
+  return VKLB_OK;
+}
+
+int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
+  if (!s) return VKLB_ERR_ARG;
+  if (tx == 0) tx = 64;
+  if (ty == 0) ty = 16;
+  if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
+  if ((size_t)(6 * s->P * tx + 2 * s->P * ty) * s->ops->real_bytes > 200 * 1024) return VKLB_ERR_ARG;
+  s->tile_x = tx;
+  s->tile_y = ty;
+  return VKLB_OK;
+}
+
+int vklb_step(vklb_sim* s, int64_t n) {
+  if (!s || n < 0) return VKLB_ERR_ARG;
+  if (!s->ready) return VKLB_ERR_STATE;
+  if (n == 0) return VKLB_OK;
+  return s->ops->step(s, n, -1.0);
+}
+
+int vklb_step_to(vklb_sim* s, double t_end) {
+  if (!s || !(t_end > 0.0)) return VKLB_ERR_ARG;
+  if (!s->ready) return VKLB_ERR_STATE;
+  for (int iter = 0; iter < 1000; ++iter) {
+    Ctl h;
+    int st = read_ctl(s, &h);
+    if (st) return st;
+    if ((st = err_of(h))) return st;
+    const int slot = (int)(s->launched % 3);
+    StepScalars sc = step_scalars(&h, slot, s->kind == VKLB_MHD_GLM, s->ch_factor, 1.0 / s->cfl, s->fixed_xi, t_end, s->dx);
+    if (sc.done) return VKLB_OK;
+    // steps left if xi stayed as it is now
+    double m = ceil((t_end - h.t[slot]) * sc.xi / s->dx - 1e-9);
+    if (!std::isfinite(m) || !(sc.xi > 0.0)) return VKLB_ERR_NONPHYSICAL;
+    if (m > 1e8) return VKLB_ERR_ARG;  // more than 1e8 steps left: refuse rather than enqueue them
+    if (m < 1) m = 1;
+    if (s->dim == 1) {
+      const long long before = h.nsteps;
+      int64_t chunk = (int64_t)m + 16;
+      if ((st = s->ops->step(s, chunk, t_end))) return st;
+      if ((st = read_ctl(s, &h))) return st;
+      const long long took = h.nsteps - before;
+      s->cur ^= (int)(took & 1);
+      s->launched += took;
+    } else {
+      if ((st = s->ops->step(s, (int64_t)m, t_end))) return st;
+    }
+  }
+  return VKLB_ERR_STATE;
+}
+
+int vklb_sync(vklb_sim* s) {
+  if (!s) return VKLB_ERR_ARG;
+  Ctl h;
+  int st = read_ctl(s, &h);
+  if (st) return st;
+  return err_of(h);
+}
+
+int vklb_moments(vklb_sim* s, double* U, int32_t on_device) {
+  if (!s || !U) return VKLB_ERR_ARG;
+  if (!s->ready) return VKLB_ERR_STATE;
+  int st = s->ops->moments(s, s->stage);
+  if (st) return st;
+  const size_t bytes = sizeof(double) * s->P * (size_t)s->cells;
+  if ((st = cuda_status(cudaMemcpyAsync(U, s->stage, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                        s->stream))))
+    return st;
+  return vklb_sync(s);
+}
+
+int vklb_conservation_totals(vklb_sim* s, double* totals) {
+  if (!s || !totals) return VKLB_ERR_ARG;
+  if (!s->ready) return VKLB_ERR_STATE;
+  int st = s->ops->totals(s, totals);
+  if (st) return st;
+  return vklb_sync(s);
+}
+
+int vklb_time(vklb_sim* s, double* t, int64_t* steps, double* xi) {
+  if (!s) return VKLB_ERR_ARG;
+  if (!s->ready) return VKLB_ERR_STATE;
+  Ctl h;
+  int st = read_ctl(s, &h);
+  if (st) return st;
+  const int slot = (int)(s->launched % 3);
+  StepScalars sc = step_scalars(&h, slot, s->kind == VKLB_MHD_GLM, s->ch_factor, 1.0 / s->cfl, s->fixed_xi, -1.0, s->dx);
+  if (t) *t = h.t[slot];
+  if (steps) *steps = h.nsteps;
+  if (xi) *xi = sc.xi;
+  return err_of(h);
+}
+
+int vklb_info(const vklb_sim* s, vklb_info_t* info) {
+  if (!s || !info) return VKLB_ERR_ARG;
+  info->p = s->P;
+  info->q = s->Q;
+  info->precision = s->prec;
+  info->store_bytes = s->store_bytes;
+  info->cells = s->cells;
+  info->bytes_per_lup = 2LL * s->Q * s->P * s->store_bytes;
+  info->state_bytes = (int64_t)s->Q * s->P * s->cells * s->store_bytes;
+  info->dx = s->dx;
+  info->tile_x = s->tile_x;
+  info->tile_y = s->tile_y;
+  info->kernels_per_step = 1;
+  return VKLB_OK;
+}
+
+int vklb_device_state(const vklb_sim* s, void** f_dev) {
+  if (!s || !f_dev) return VKLB_ERR_ARG;
+  *f_dev = s->f[s->cur];
+  return VKLB_OK;
+}
+
+int vklb_state_bytes(const vklb_sim* s, size_t* bytes) {
+  if (!s || !bytes) return VKLB_ERR_ARG;
+  *bytes = sizeof(BlobHeader) + sizeof(Ctl) + (size_t)s->Q * s->P * s->cells * s->store_bytes;
+  return VKLB_OK;
+}
+
+int vklb_get_state(vklb_sim* s, void* blob, size_t bytes) {
+  size_t need = 0;
+  if (!s || !blob || vklb_state_bytes(s, &need) || bytes < need) return VKLB_ERR_ARG;
+  if (!s->ready) return VKLB_ERR_STATE;
+  BlobHeader hdr = {kMagic, (uint32_t)s->kind, (uint32_t)s->P, (uint32_t)s->Q, (uint32_t)s->prec,
+                    (uint32_t)(s->launched % 3), s->nx, s->ny, s->launched};
+  memcpy(blob, &hdr, sizeof(hdr));
+  char* p = (char*)blob + sizeof(hdr);
+  int st = cuda_status(cudaMemcpyAsync(p, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  if (st) return st;
+  const size_t fb = (size_t)s->Q * s->P * s->cells * s->store_bytes;
+  if ((st = cuda_status(cudaMemcpyAsync(p + sizeof(Ctl), s->f[s->cur], fb, cudaMemcpyDeviceToHost, s->stream)))) return st;
+  if ((st = cuda_status(cudaStreamSynchronize(s->stream)))) return st;
+  Ctl h;
+  memcpy(&h, p, sizeof(h));
+  return err_of(h);
+}
+
+int vklb_put_state(vklb_sim* s, const void* blob, size_t bytes) {
+  size_t need = 0;
+  if (!s || !blob || vklb_state_bytes(s, &need) || bytes < need) return VKLB_ERR_ARG;
+  BlobHeader hdr;
+  memcpy(&hdr, blob, sizeof(hdr));
+  if (hdr.magic != kMagic || (int)hdr.kind != s->kind || (int)hdr.P != s->P || (int)hdr.Q != s->Q ||
+      (int)hdr.prec != s->prec || hdr.nx != s->nx || hdr.ny != s->ny)
+    return VKLB_ERR_ARG;
+  const char* p = (const char*)blob + sizeof(hdr);
+  int st = cuda_status(cudaMemcpyAsync(s->ctl, p, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
+  if (st) return st;
+  s->cur = 0;
+  s->launched = hdr.launched;
+  const size_t fb = (size_t)s->Q * s->P * s->cells * s->store_bytes;
+  if ((st = cuda_status(cudaMemcpyAsync(s->f[0], p + sizeof(Ctl), fb, cudaMemcpyHostToDevice, s->stream)))) return st;
+  if ((st = cuda_status(cudaStreamSynchronize(s->stream)))) return st;
+  s->ready = true;
+  return VKLB_OK;
+}
+
+// ------------------------------------------------------------------- batches
+static int batch_build_work(vklb_batch* b) {
+  std::vector<BatchWork> w;
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    const vklb_sim* s = b->sims[i];
+    const int gx = (int)((s->nx + b->tile_x - 1) / b->tile_x), gy = (int)((s->ny + b->tile_y - 1) / b->tile_y);
+    for (int by = 0; by < gy; ++by)
+      for (int bx = 0; bx < gx; ++bx) w.push_back(BatchWork{(int)i, bx, by});
+  }
+  if (b->d_work) cudaFree(b->d_work);
+  b->d_work = nullptr;
+  if (cudaMalloc((void**)&b->d_work, sizeof(BatchWork) * w.size()) != cudaSuccess) return VKLB_ERR_NOMEM;
+  b->nwork = (int)w.size();
+  int st = cuda_status(cudaMemcpy(b->d_work, w.data(), sizeof(BatchWork) * w.size(), cudaMemcpyHostToDevice));
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->graph_n = 0;
+  return st;
+}
+
+int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
+  if (n < 1 || !sims || !out) return VKLB_ERR_ARG;
+  *out = nullptr;
+  const vklb_sim* s0 = sims[0];
+  if (!s0 || s0->dim != 2) return VKLB_ERR_UNSUPPORTED;
+  for (int i = 0; i < n; ++i) {
+    const vklb_sim* s = sims[i];
+    if (!s || !s->ready) return VKLB_ERR_STATE;
+    if (s->ops != s0->ops || s->set != s0->set) return VKLB_ERR_ARG;
+  }
+  vklb_batch* b = new (std::nothrow) vklb_batch();
+  if (!b) return VKLB_ERR_NOMEM;
+  b->sims.assign(sims, sims + n);
+  b->tile_x = 64;
+  b->tile_y = 16;
+  b->stream = s0->stream;
+  b->ops = s0->ops;
+  b->h_desc.resize(s0->ops->args_bytes * n);
+  if (cudaMalloc(&b->d_desc, b->h_desc.size()) != cudaSuccess) {
+    delete b;
+    return VKLB_ERR_NOMEM;
+  }
+  int st = batch_build_work(b);
+  if (st) {
+    vklb_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return VKLB_OK;
+}
+
+int vklb_batch_set_tiling(vklb_batch* b, int32_t tx, int32_t ty) {
+  if (!b) return VKLB_ERR_ARG;
+  if (tx == 0) tx = 64;
+  if (ty == 0) ty = 16;
+  if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
+  if ((size_t)(6 * b->sims[0]->P * tx + 2 * b->sims[0]->P * ty) * b->ops->real_bytes > 200 * 1024) return VKLB_ERR_ARG;
+  b->tile_x = tx;
+  b->tile_y = ty;
+  return batch_build_work(b);
+}
+
+int vklb_batch_step(vklb_batch* b, int64_t n, int32_t use_graph) {
+  if (!b || n < 0) return VKLB_ERR_ARG;
+  if (n == 0) return VKLB_OK;
+  return b->ops->batch(b, n, use_graph);
+}
+
+int vklb_batch_destroy(vklb_batch* b) {
+  if (!b) return VKLB_ERR_ARG;
+  cudaStreamSynchronize(b->stream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_desc);
+  cudaFree(b->d_work);
+  delete b;
+  return VKLB_OK;
+}
+
+}  // extern "C"

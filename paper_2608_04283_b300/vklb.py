@@ -1,0 +1,254 @@
+"""Thin ctypes binding of libvklb.so (C ABI in include/vklb.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+the library.  Importing this module raises if the library has not been built
+(``python -m paper_2608_04283_b300.build``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvklb.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libvklb.so is not built: run `python -m paper_2608_04283_b300.build`")
+_lib = C.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------------ constants
+OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_NONPHYSICAL, ERR_CFL, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+ADVECT, SWE, EULER, MHD_GLM = 0, 1, 2, 3
+D1Q3, D2Q5 = 13, 25
+BC_PERIODIC, BC_CHARACTERISTIC = 0, 1
+SET_WEIGHTED, SET_CENTERED, SET_DISCONTINUOUS = 0, 1, 2
+FP64, FP32, BF16_STORE = 0, 1, 2
+
+SYSTEM_KIND = {"advection": ADVECT, "swe": SWE, "euler": EULER, "mhd_glm": MHD_GLM}
+SET_KIND = {"weighted": SET_WEIGHTED, "centered": SET_CENTERED, "discontinuous": SET_DISCONTINUOUS}
+PRECISION = {"fp64": FP64, "fp32": FP32, "bf16": BF16_STORE}
+
+
+class System(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("gamma", C.c_double), ("g", C.c_double),
+                ("ch_factor", C.c_double), ("adv_speed", C.c_double * 2)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int64 * 2), ("lo", C.c_double * 2), ("hi", C.c_double * 2)]
+
+
+class BC(C.Structure):
+    _fields_ = [("lo", C.c_int32 * 2), ("hi", C.c_int32 * 2)]
+
+
+class Weight(C.Structure):
+    _fields_ = [("set", C.c_int32), ("c", C.c_double), ("k", C.c_double), ("omega", C.c_double),
+                ("cfl", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("p", C.c_int32), ("q", C.c_int32), ("precision", C.c_int32), ("store_bytes", C.c_int32),
+                ("cells", C.c_int64), ("bytes_per_lup", C.c_int64), ("state_bytes", C.c_int64),
+                ("dx", C.c_double), ("tile_x", C.c_int32), ("tile_y", C.c_int32),
+                ("kernels_per_step", C.c_int32)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIGS = {
+    "vklb_create": (C.c_int, [C.POINTER(System), C.c_int32, C.POINTER(Grid), C.POINTER(BC), C.POINTER(Weight),
+                              C.c_double, C.c_int32, _P, C.POINTER(_P)]),
+    "vklb_set_state": (C.c_int, [_P, _P, C.c_int32]),
+    "vklb_set_tiling": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "vklb_step": (C.c_int, [_P, C.c_int64]),
+    "vklb_step_to": (C.c_int, [_P, C.c_double]),
+    "vklb_sync": (C.c_int, [_P]),
+    "vklb_moments": (C.c_int, [_P, _P, C.c_int32]),
+    "vklb_conservation_totals": (C.c_int, [_P, _D]),
+    "vklb_time": (C.c_int, [_P, _D, C.POINTER(C.c_int64), _D]),
+    "vklb_info": (C.c_int, [_P, C.POINTER(Info)]),
+    "vklb_device_state": (C.c_int, [_P, C.POINTER(_P)]),
+    "vklb_state_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+    "vklb_get_state": (C.c_int, [_P, _P, C.c_size_t]),
+    "vklb_put_state": (C.c_int, [_P, _P, C.c_size_t]),
+    "vklb_destroy": (C.c_int, [_P]),
+    "vklb_strerror": (C.c_char_p, [C.c_int]),
+    "vklb_batch_create": (C.c_int, [C.c_int32, C.POINTER(_P), C.POINTER(_P)]),
+    "vklb_batch_set_tiling": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "vklb_batch_step": (C.c_int, [_P, C.c_int64, C.c_int32]),
+    "vklb_batch_destroy": (C.c_int, [_P]),
+    "vklb_launch_count": (C.c_int64, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class VKLBError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_lib.vklb_strerror(status).decode()} ({status})")
+
+
+def _check(st, where):
+    if st != OK:
+        raise VKLBError(st, where)
+
+
+def launch_count():
+    return int(_lib.vklb_launch_count())
+
+
+def lib():
+    return _lib
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Sim:
+    """One simulation (see vklb_create).  ``system`` in advection / swe / euler /
+    mhd_glm; ``n`` = (nx,) or (nx, ny); ``lo``/``hi`` domain corners."""
+
+    def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted", c=0.05, k=2.0, omega=1.0,
+                 cfl=0.9, dt=0.0, precision="fp32", gamma=1.4, g=9.81, ch_factor=6.0, adv_speed=(1.0, 0.0),
+                 stream=None):
+        n = tuple(int(v) for v in n)
+        dim = len(n)
+        lo = tuple(float(v) for v in np.atleast_1d(lo))
+        hi = tuple(float(v) for v in np.atleast_1d(hi))
+        s = System(SYSTEM_KIND[system], float(gamma), float(g), float(ch_factor),
+                   (C.c_double * 2)(*[float(v) for v in adv_speed]))
+        grid = Grid(dim, (C.c_int64 * 2)(n[0], n[1] if dim == 2 else 1),
+                    (C.c_double * 2)(lo[0], lo[1] if dim == 2 else 0.0),
+                    (C.c_double * 2)(hi[0], hi[1] if dim == 2 else 1.0))
+        kind = BC_PERIODIC if bc == "periodic" else BC_CHARACTERISTIC
+        b = BC((C.c_int32 * 2)(kind, kind), (C.c_int32 * 2)(kind, kind))
+        w = Weight(SET_KIND[set_kind], float(c), float(k), float(omega), float(cfl))
+        self._h = _P()
+        self.system, self.n, self.dim = system, n, dim
+        self.precision = precision
+        self._stream = stream
+        _check(_lib.vklb_create(C.byref(s), D1Q3 if dim == 1 else D2Q5, C.byref(grid), C.byref(b), C.byref(w),
+                                float(dt), PRECISION[precision], _stream_handle(stream), C.byref(self._h)),
+               "vklb_create")
+        self.info = Info()
+        _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
+        self.p = self.info.p
+        self.shape = (self.p,) + tuple(reversed(n))
+
+    # ------------------------------------------------------------------ core
+    @property
+    def handle(self):
+        return self._h
+
+    def set_state(self, U):
+        """U: numpy float64 [p, (ny,) nx] on the host, or a torch CUDA float64 tensor."""
+        if hasattr(U, "is_cuda") and U.is_cuda:
+            assert U.dtype.__str__() == "torch.float64" and U.is_contiguous() and tuple(U.shape) == self.shape
+            _check(_lib.vklb_set_state(self._h, _P(U.data_ptr()), 1), "vklb_set_state")
+            return
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        if U.shape != self.shape:
+            raise ValueError(f"state shape {U.shape} != {self.shape}")
+        _check(_lib.vklb_set_state(self._h, U.ctypes.data_as(_P), 0), "vklb_set_state")
+
+    def set_tiling(self, tx, ty):
+        _check(_lib.vklb_set_tiling(self._h, int(tx), int(ty)), "vklb_set_tiling")
+        _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
+
+    def step(self, n=1):
+        _check(_lib.vklb_step(self._h, int(n)), "vklb_step")
+
+    def step_to(self, t_end):
+        _check(_lib.vklb_step_to(self._h, float(t_end)), "vklb_step_to")
+
+    def sync(self):
+        _check(_lib.vklb_sync(self._h), "vklb_sync")
+
+    def moments(self, out=None):
+        """U = sum_q f_q as float64: numpy on the host, or into a torch CUDA tensor ``out``."""
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            _check(_lib.vklb_moments(self._h, _P(out.data_ptr()), 1), "vklb_moments")
+            return out
+        U = np.empty(self.shape, dtype=np.float64)
+        _check(_lib.vklb_moments(self._h, U.ctypes.data_as(_P), 0), "vklb_moments")
+        return U
+
+    def totals(self):
+        t = np.empty(self.p, dtype=np.float64)
+        _check(_lib.vklb_conservation_totals(self._h, t.ctypes.data_as(_D)), "vklb_conservation_totals")
+        return t
+
+    def time(self):
+        t = C.c_double()
+        n = C.c_int64()
+        xi = C.c_double()
+        _check(_lib.vklb_time(self._h, C.byref(t), C.byref(n), C.byref(xi)), "vklb_time")
+        return t.value, n.value, xi.value
+
+    def device_state(self):
+        p = _P()
+        _check(_lib.vklb_device_state(self._h, C.byref(p)), "vklb_device_state")
+        return p.value
+
+    def get_state(self):
+        nb = C.c_size_t()
+        _check(_lib.vklb_state_bytes(self._h, C.byref(nb)), "vklb_state_bytes")
+        buf = np.empty(nb.value, dtype=np.uint8)
+        _check(_lib.vklb_get_state(self._h, buf.ctypes.data_as(_P), nb.value), "vklb_get_state")
+        return buf
+
+    def put_state(self, blob):
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(_lib.vklb_put_state(self._h, blob.ctypes.data_as(_P), blob.size), "vklb_put_state")
+
+    def close(self):
+        if self._h:
+            _check(_lib.vklb_destroy(self._h), "vklb_destroy")
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched stepping of simulations that share system, precision and weight."""
+
+    def __init__(self, sims, tile=None):
+        self.sims = list(sims)
+        arr = (_P * len(self.sims))(*[s.handle for s in self.sims])
+        self._h = _P()
+        _check(_lib.vklb_batch_create(len(self.sims), arr, C.byref(self._h)), "vklb_batch_create")
+        if tile is not None:
+            self.set_tiling(*tile)
+
+    def set_tiling(self, tx, ty):
+        _check(_lib.vklb_batch_set_tiling(self._h, int(tx), int(ty)), "vklb_batch_set_tiling")
+
+    def step(self, n=1, graph=True):
+        _check(_lib.vklb_batch_step(self._h, int(n), 1 if graph else 0), "vklb_batch_step")
+
+    def close(self):
+        if self._h:
+            _check(_lib.vklb_batch_destroy(self._h), "vklb_batch_destroy")
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
