@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark of the WU-VKLB step (weighted upwind vector kinetic lattice
+Boltzmann, fused collide-and-stream) on B300.
+
+Default workload: 2D Euler isentropic vortex (gamma 1.4, strength 5, background
+rho = p = 1, velocity (1, 1)) on a periodic [0, 10]^2 grid of 1024^2 cells, D2Q5,
+4 conserved fields, FP32 distributions, omega = 2, CFL 0.3, c = 0.05, k = 2.
+A bench step is one time step of Fig. 5 (one kernel launch).  Each timed step is
+bracketed by CUDA events on the simulation's stream, after a 256 MiB write that
+flushes L2 (the 84 MB state would otherwise stay partly L2-resident).  Every
+200 steps the state is re-initialised outside the timed events: at omega = 2 the
+weighted set amplifies rounding (see the design notes) and an FP32 run would
+leave the physical range after about 400 steps.
+
+--impl reference times the FP64 CPU oracle (oracle/, test infrastructure) on the
+host cores on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--workload euler_vortex_1024|mhd_orszag_tang_2048] [--no-extras] [--no-cpu-baseline]
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2608_04283_b300 import inputs  # noqa: E402
+
+WORKLOADS = {
+    "euler_vortex_1024": dict(
+        system="euler", n=(1024, 1024), lo=(0.0, 0.0), hi=(10.0, 10.0),
+        kw=dict(omega=2.0, cfl=0.3, c=0.05, k=2.0, gamma=1.4),
+        ic=lambda: inputs.isentropic_vortex(1024),
+        name="2D Euler isentropic vortex 1024x1024, periodic [0,10]^2, D2Q5, 4 fields, omega 2, CFL 0.3"),
+    "mhd_orszag_tang_2048": dict(
+        system="mhd_glm", n=(2048, 2048), lo=(0.0, 0.0), hi=(2 * np.pi, 2 * np.pi),
+        kw=dict(omega=1.0, cfl=0.3, c=0.05, k=2.0, gamma=5.0 / 3.0, ch_factor=6.0),
+        ic=lambda: inputs.orszag_tang(2048),
+        name="2D ideal MHD-GLM Orszag-Tang 2048x2048, periodic [0,2pi]^2, D2Q5, 9 fields, omega 1, CFL 0.3"),
+}
+REINIT_EVERY = 200
+FLUSH_BYTES = 256 << 20
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2608_04283_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def tiling_for(system, precision, n):
+    tab = json.load(open(os.path.join(ROOT, "paper_2608_04283_b300", "tuning.json")))
+    ent = tab.get(f"{system}/{precision}")
+    if not ent:
+        return None
+    side = max(n)
+    best = min(ent.keys(), key=lambda k: abs(int(k) - side))
+    return tuple(ent[best])
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def traffic_record(kernel_key):
+    """Per-launch DRAM bytes of the step kernel from a committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel_key)
+    if not e or e.get("csrc_hash") != csrc_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- oracle arm
+def oracle_mlups(wl, rows, steps, warmup):
+    """The FP64 oracle as it stands on a bounded sample: a strip of ``rows`` rows
+    of the workload grid (periodic), one oracle step per bench step."""
+    from oracle import systems as osys
+    from oracle import vklb as ovklb
+    from threadpoolctl import threadpool_info
+    nx = wl["n"][0]
+    U = np.ascontiguousarray(wl["ic"]()[:, :rows, :])
+    dx = (wl["hi"][0] - wl["lo"][0]) / nx
+    kw = wl["kw"]
+    if wl["system"] == "euler":
+        sysm = osys.Euler(kw["gamma"], 2)
+    else:
+        sysm = osys.MHDGLM(kw["gamma"])
+    sim = ovklb.Sim(sysm, (nx, rows), (0.0, 0.0), (nx * dx, rows * dx), omega=kw["omega"], nu=kw["cfl"],
+                    c=kw["c"], k=kw["k"], ch_factor=kw.get("ch_factor", 6.0))
+    sim.set_state(U)
+    sim.run(warmup)
+    t0 = time.perf_counter()
+    sim.run(steps)
+    dt = time.perf_counter() - t0
+    threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    return nx * rows * steps / dt / 1e6, dt, threads
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    rows = 64
+    val, dt, threads = oracle_mlups(wl, rows, args.steps, args.warmup)
+    sample = f"{rows} x {wl['n'][0]} strip of the {wl['n'][0]}^2 grid per step, {args.steps} timed steps"
+    line = {"metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "description": wl["name"], "parallelism": "host cores"},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- CUDA arm
+def timed_steps(torch, sim, stream, U0_dev, steps, warmup, flush_buf, reinit_every=REINIT_EVERY):
+    """Per-step event timing on the simulation's stream; L2 flushed before each step."""
+    sim.set_state(U0_dev)
+    with torch.cuda.stream(stream):
+        for i in range(warmup):
+            flush_buf.fill_(i & 0xFF)
+            sim.step(1)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            if i > 0 and i % reinit_every == 0:
+                sim.set_state(U0_dev)
+            flush_buf.fill_(i & 0xFF)
+            ev0[i].record(stream)
+            sim.step(1)
+            ev1[i].record(stream)
+    torch.cuda.synchronize()
+    durs = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])   # ms
+    return durs
+
+
+def run_ours(args, wl):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2608_04283_b300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2608_04283_b300 import vklb
+
+    prec = args.precision
+    stream = torch.cuda.Stream()
+    sim = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, stream=stream, **wl["kw"])
+    tile = tiling_for(wl["system"], prec, wl["n"])
+    if tile:
+        sim.set_tiling(*tile)
+    U0 = wl["ic"]()
+    U0_dev = torch.from_numpy(U0).cuda()
+    flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    cells = wl["n"][0] * wl["n"][1]
+    bpl = sim.info.bytes_per_lup
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = vklb.launch_count()
+    durs = timed_steps(torch, sim, stream, U0_dev, args.steps, args.warmup, flush_buf)
+    l1 = vklb.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = float(durs.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * cells * args.steps / (total_ms * 1e-3) / 1e6
+    mean_ms = total_ms / args.steps
+    achieved = bpl * cells / (mean_ms * 1e-3) / 1e9
+    peaks, peak_src = measured_peaks()
+    key = f"step2d/{wl['system']}/{prec}/{wl['n'][0]}x{wl['n'][1]}/{sim.info.tile_x}x{sim.info.tile_y}"
+    traffic = traffic_record(key)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_src + " (burst)",
+                "algorithmic_bytes_per_lup": bpl, "kernel": "step2d_kernel"}
+
+    extras = {}
+    acc = None
+    e2e = None
+    cpu = None
+    if rank == 0:
+        acc = accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps=50)
+        e2e = end_to_end(torch, vklb, wl, prec, tile, steps=min(args.steps, REINIT_EVERY), U0=U0)
+        if not args.no_extras and args.workload == "euler_vortex_1024":
+            extras["mhd_orszag_tang_2048"] = secondary(torch, vklb, WORKLOADS["mhd_orszag_tang_2048"], prec,
+                                                       flush_buf, steps=100)
+            extras["batched_swe_256"] = batched_swe(torch, vklb)
+        if world == 1 and not args.no_cpu_baseline:
+            v, dt, threads = oracle_mlups(wl, wl["n"][1], 1, 0)
+            cpu = {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                   "sample": f"one oracle step of the full {wl['n'][0]}x{wl['n'][1]} grid ({dt:.1f} s)"}
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-store/f32"}[prec],
+                "data": "synthetic",
+                "config": {"workload": args.workload, "description": wl["name"], "cells": cells,
+                           "precision": prec, "tile": [sim.info.tile_x, sim.info.tile_y],
+                           "l2": "256 MiB write before every timed step",
+                           "reinit_every": REINIT_EVERY, "parallelism": "replicas" if world > 1 else "single"},
+                "hbm_gbs": achieved, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(l1 - l0), "clocks": clk, "accuracy_fp32_vs_fp64": acc,
+                "step_ms": {"median": float(np.median(durs)), "p10": float(np.percentile(durs, 10)),
+                            "p90": float(np.percentile(durs, 90))},
+                "extras": extras}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps):
+    """L1 / Linf of the benchmarked precision against the FP64 CUDA path (which the
+    parity tests tie to the oracle at <= 1e-11) after ``steps`` steps."""
+    if prec == "fp64":
+        return None
+    U0 = wl["ic"]()
+    out = {}
+    res = []
+    for p in (prec, "fp64"):
+        s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=p, **wl["kw"])
+        if tile and p == prec:
+            s.set_tiling(*tile)
+        s.set_state(U0)
+        s.step(steps)
+        res.append(s.moments())
+        s.close()
+    a, b = res
+    out["steps"] = steps
+    out["rel_l1_max_field"] = float(max(np.abs(a[k] - b[k]).sum() / max(np.abs(b[k]).sum(), 1e-300)
+                                        for k in range(a.shape[0])))
+    out["rel_linf_max_field"] = float(max(np.abs(a[k] - b[k]).max() / max(np.abs(b[k]).max(), 1e-300)
+                                          for k in range(a.shape[0])))
+    return out
+
+
+def end_to_end(torch, vklb, wl, prec, tile, steps, U0):
+    """Through the public API with host buffers: pinned U0 -> vklb_set_state (H2D),
+    ``steps`` x vklb_step, vklb_moments -> pinned host (D2H), wall clock."""
+    host_in = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True).numpy()
+    host_in[...] = U0
+    host_out = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True).numpy()
+    s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, **wl["kw"])
+    if tile:
+        s.set_tiling(*tile)
+    s.set_state(host_in)
+    s.step(2)
+    s.moments(out=host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(host_in)
+    s.step(steps)
+    s.moments(out=host_out)
+    dt = time.perf_counter() - t0
+    s.close()
+    cells = wl["n"][0] * wl["n"][1]
+    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": int(U0.nbytes / steps), "d2h_bytes_per_step": int(U0.nbytes / steps),
+            "steps_per_solve": steps,
+            "note": "one solve = H2D of U0 (pinned), the steps, D2H of U (pinned); bytes amortised per step"}
+
+
+def secondary(torch, vklb, wl, prec, flush_buf, steps):
+    stream = torch.cuda.Stream()
+    s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, stream=stream, **wl["kw"])
+    tile = tiling_for(wl["system"], prec, wl["n"])
+    if tile:
+        s.set_tiling(*tile)
+    U0 = torch.from_numpy(wl["ic"]()).cuda()
+    durs = timed_steps(torch, s, stream, U0, steps, 5, flush_buf)
+    cells = wl["n"][0] * wl["n"][1]
+    mean_ms = float(durs.mean())
+    bpl = s.info.bytes_per_lup
+    peaks, src = measured_peaks()
+    gbs = bpl * cells / (mean_ms * 1e-3) / 1e9
+    s.close()
+    return {"workload": wl["name"], "MLUPS": cells / (mean_ms * 1e-3) / 1e6, "ms_per_step": mean_ms,
+            "hbm_gbs": gbs, "frac_of_peak": gbs / peaks["hbm_gbs"], "bytes_per_lup": bpl,
+            "tile": [s.info.tile_x, s.info.tile_y], "steps": steps}
+
+
+def batched_swe(torch, vklb, count=256, steps=500):
+    """Batched form: 256 seeded SWE instances (sides 64..1024, Gaussian humps),
+    500 steps each, one launch per step over all instances (CUDA graph), against
+    the same instances launched one at a time.  Reports solves/s."""
+    specs = inputs.swe_humps_batch(count, seed=0)
+    tile = tiling_for("swe", "fp32", (256, 256)) or (64, 16)
+    stream = torch.cuda.Stream()
+    sims = []
+    U0s = []
+    for sp in specs:
+        s = vklb.Sim("swe", (sp.n, sp.n), (0, 0), (1, 1), omega=1.0, cfl=0.3, precision="fp32", stream=stream)
+        s.set_tiling(*tile)
+        U0 = torch.from_numpy(inputs.swe_hump_2d(sp.n, sp.amp, sp.x0, sp.y0, sp.sigma)).cuda()
+        U0s.append(U0)
+        sims.append(s)
+    cells = sum(sp.n * sp.n for sp in specs)
+    for s, U in zip(sims, U0s):
+        s.set_state(U)
+    b = vklb.Batch(sims, tile=tile)
+    b.step(5, graph=True)          # warm-up (graph capture of 5 steps)
+    torch.cuda.synchronize()
+    for s, U in zip(sims, U0s):
+        s.set_state(U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps, graph=True)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    batch_out = [sims[i].moments() for i in (0, count // 2, count - 1)]
+    for s, U in zip(sims, U0s):
+        s.set_state(U)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in sims:
+        s.step(steps)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    plain_out = [sims[i].moments() for i in (0, count // 2, count - 1)]
+    same = all(np.array_equal(a, c) for a, c in zip(batch_out, plain_out))
+    b.close()
+    for s in sims:
+        s.close()
+    return {"instances": count, "steps": steps, "cells_total": cells, "tile": list(tile),
+            "batched_solves_per_s": count / tb, "plain_solves_per_s": count / tp,
+            "batched_MLUPS": cells * steps / tb / 1e6, "plain_MLUPS": cells * steps / tp / 1e6,
+            "speedup": tp / tb, "batched_equals_plain_bitwise": bool(same),
+            "note": "wall clock incl. launch; batched = one launch per step over all instances in one CUDA graph"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="euler_vortex_1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -69,6 +69,8 @@ struct vklb_batch {
   int64_t graph_n;
   cudaGraph_t graph;
   cudaGraphExec_t gexec;
+  cudaStream_t own;        // private stream: graphs cannot be captured on the legacy stream
+  cudaEvent_t ev_in, ev_out;
 };
 
 namespace {
@@ -184,7 +186,7 @@ struct BatchImpl {
     const int TX = b->tile_x, TY = b->tile_y;
     const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes(TX, TY);
     for (int64_t i = 0; i < n; ++i)
-      step2d_batch_kernel<Sys, T, R><<<b->nwork, TX, sm, b->stream>>>((const StepArgs<T>*)b->d_desc, b->d_work,
+      step2d_batch_kernel<Sys, T, R><<<b->nwork, TX, sm, b->own>>>((const StepArgs<T>*)b->d_desc, b->d_work,
                                                                        (int)i, TX, TY);
     }
   }
@@ -199,26 +201,39 @@ struct BatchImpl {
     }
     StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
     for (size_t i = 0; i < b->sims.size(); ++i) h[i] = make_args<T>(b->sims[i], -1.0);
-    int st = cuda_status(cudaMemcpyAsync(b->d_desc, h, b->h_desc.size(), cudaMemcpyHostToDevice, b->stream));
-    if (st) return st;
+    // order after the work already queued on the simulations' streams
+    int st = VKLB_OK;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+      if (i > 0 && b->sims[i]->stream == b->sims[i - 1]->stream) continue;
+      if ((st = cuda_status(cudaEventRecord(b->ev_in, b->sims[i]->stream)))) return st;
+      if ((st = cuda_status(cudaStreamWaitEvent(b->own, b->ev_in, 0)))) return st;
+    }
+    // pageable source: the runtime stages it before returning, so h may be reused
+    if ((st = cuda_status(cudaMemcpyAsync(b->d_desc, h, b->h_desc.size(), cudaMemcpyHostToDevice, b->own)))) return st;
     if (use_graph) {
       if (!b->gexec || b->graph_n != n) {
         if (b->gexec) cudaGraphExecDestroy(b->gexec);
         if (b->graph) cudaGraphDestroy(b->graph);
         b->gexec = nullptr;
         b->graph = nullptr;
-        if ((st = cuda_status(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)))) return st;
+        if ((st = cuda_status(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal)))) return st;
         launch(b, n);
-        if ((st = cuda_status(cudaStreamEndCapture(b->stream, &b->graph)))) return st;
+        if ((st = cuda_status(cudaStreamEndCapture(b->own, &b->graph)))) return st;
         if ((st = cuda_status(cudaGraphInstantiate(&b->gexec, b->graph, 0)))) return st;
         b->graph_n = n;
       }
-      if ((st = cuda_status(cudaGraphLaunch(b->gexec, b->stream)))) return st;
+      if ((st = cuda_status(cudaGraphLaunch(b->gexec, b->own)))) return st;
     } else {
       launch(b, n);
     }
     g_launches += n;
     if ((st = cuda_status(cudaGetLastError()))) return st;
+    // later work on the simulations' streams waits for the batch
+    if ((st = cuda_status(cudaEventRecord(b->ev_out, b->own)))) return st;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+      if (i > 0 && b->sims[i]->stream == b->sims[i - 1]->stream) continue;
+      if ((st = cuda_status(cudaStreamWaitEvent(b->sims[i]->stream, b->ev_out, 0)))) return st;
+    }
     for (vklb_sim* s : b->sims) {
       s->cur ^= (int)(n & 1);
       s->launched += n;
@@ -272,8 +287,9 @@ int read_ctl(vklb_sim* s, Ctl* h) {
 }
 
 int err_of(const Ctl& h) {
-  if (h.err & ERR_NONPHYS) return VKLB_ERR_NONPHYSICAL;
+  // a violated CFL bound (fixed xi) is the cause of any non-physical state after it
   if (h.err & ERR_CFL) return VKLB_ERR_CFL;
+  if (h.err & ERR_NONPHYS) return VKLB_ERR_NONPHYSICAL;
   return VKLB_OK;
 }
 
@@ -620,6 +636,12 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
     delete b;
     return VKLB_ERR_NOMEM;
   }
+  if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    vklb_batch_destroy(b);
+    return VKLB_ERR_CUDA;
+  }
   int st = batch_build_work(b);
   if (st) {
     vklb_batch_destroy(b);
@@ -648,11 +670,14 @@ int vklb_batch_step(vklb_batch* b, int64_t n, int32_t use_graph) {
 
 int vklb_batch_destroy(vklb_batch* b) {
   if (!b) return VKLB_ERR_ARG;
-  cudaStreamSynchronize(b->stream);
+  if (b->own) cudaStreamSynchronize(b->own);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
   cudaFree(b->d_desc);
   cudaFree(b->d_work);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->own) cudaStreamDestroy(b->own);
   delete b;
   return VKLB_OK;
 }

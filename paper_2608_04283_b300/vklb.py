@@ -181,6 +181,10 @@ class Sim:
         if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
             _check(_lib.vklb_moments(self._h, _P(out.data_ptr()), 1), "vklb_moments")
             return out
+        if out is not None:
+            assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == self.shape
+            _check(_lib.vklb_moments(self._h, out.ctypes.data_as(_P), 0), "vklb_moments")
+            return out
         U = np.empty(self.shape, dtype=np.float64)
         _check(_lib.vklb_moments(self._h, U.ctypes.data_as(_P), 0), "vklb_moments")
         return U
