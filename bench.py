@@ -168,7 +168,11 @@ def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    rows = 64
+    # strip height chosen so the whole run stays near 90 s of oracle work
+    # (the oracle does about 1.1e-5 s per Euler cell update on one host)
+    per_cell = 1.1e-5 if wl["system"] == "euler" else 2.5e-5
+    rows = int(90.0 / (args.steps + args.warmup) / (wl["n"][0] * per_cell))
+    rows = max(1, min(64, rows))
     val, dt, threads = oracle_mlups(wl, rows, args.steps, args.warmup)
     sample = f"{rows} x {wl['n'][0]} strip of the {wl['n'][0]}^2 grid per step, {args.steps} timed steps"
     line = {"metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
