@@ -139,12 +139,23 @@ def dist_env():
 
 
 # ----------------------------------------------------------------- oracle arm
+def blas_threads():
+    """Threads numpy's BLAS may use for the oracle (its batched solves and
+    products are the only multi-threaded parts)."""
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            if os.environ.get(var):
+                return int(os.environ[var])
+        return os.cpu_count() or 1
+
 def oracle_mlups(wl, rows, steps, warmup):
     """The FP64 oracle as it stands on a bounded sample: a strip of ``rows`` rows
     of the workload grid (periodic), one oracle step per bench step."""
     from oracle import systems as osys
     from oracle import vklb as ovklb
-    from threadpoolctl import threadpool_info
     nx = wl["n"][0]
     U = np.ascontiguousarray(wl["ic"]()[:, :rows, :])
     dx = (wl["hi"][0] - wl["lo"][0]) / nx
@@ -160,7 +171,7 @@ def oracle_mlups(wl, rows, steps, warmup):
     t0 = time.perf_counter()
     sim.run(steps)
     dt = time.perf_counter() - t0
-    threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    threads = blas_threads()
     return nx * rows * steps / dt / 1e6, dt, threads
 
 

@@ -122,6 +122,8 @@ typedef struct {
   double dx;
   int32_t tile_x, tile_y;    /* launch shape of the step kernel */
   int32_t kernels_per_step;  /* kernel launches one vklb_step(1) makes */
+  int32_t variant;           /* step kernel: 0 plain loads, 1 bulk-copy (TMA) row pipeline */
+  int64_t pitch;             /* elements per row of a device distribution plane (>= nx) */
 } vklb_info_t;
 
 /* Create a simulation.  dt > 0 fixes xi = dx / dt for every step; dt <= 0
@@ -144,6 +146,11 @@ int vklb_set_state(vklb_sim* sim, const double* U, int32_t on_device);
 /* Launch shape of the step kernel (tile_x cells along x by tile_y rows per
  * block); 0 keeps the built-in default.  Used by the autotuner. */
 int vklb_set_tiling(vklb_sim* sim, int32_t tile_x, int32_t tile_y);
+
+/* Step-kernel variant for D2Q5: 0 = plain coalesced loads, 1 = rows streamed
+ * into shared memory by bulk asynchronous copies (TMA) with `stages` rows in
+ * flight (2..8).  Both compute the same arithmetic.  Default: 1 with 4 stages. */
+int vklb_set_variant(vklb_sim* sim, int32_t variant, int32_t stages);
 
 /* Enqueue n steps of Fig. 5 (no host synchronisation). */
 int vklb_step(vklb_sim* sim, int64_t n);
@@ -170,8 +177,9 @@ int vklb_time(vklb_sim* sim, double* t, int64_t* steps, double* xi);
 
 int vklb_info(const vklb_sim* sim, vklb_info_t* info);
 
-/* Device pointer of the current distribution buffer f[q][k][y][x] (store
- * type of the precision).  Borrowed; valid until the next vklb_step. */
+/* Device pointer of the current distribution buffer, laid out
+ * f[(q * p + k) * ny * pitch + y * pitch + x] in the store type of the
+ * precision (pitch from vklb_info).  Borrowed; valid until the next vklb_step. */
 int vklb_device_state(const vklb_sim* sim, void** f_dev);
 
 /* Checkpoint / resume: the blob holds the distributions and the control words

@@ -18,7 +18,7 @@ struct Ctl {
   int32_t pad;
 };
 
-enum : int { ERR_NONPHYS = 1, ERR_CFL = 2 };
+enum : int { ERR_NONPHYS = 1, ERR_CFL = 2, ERR_TIMEOUT = 4 };
 
 struct StepScalars {
   double xi;   // lattice speed of this step

@@ -52,6 +52,7 @@ struct StepArgs {
   T* f[2];         // ping-pong distribution buffers
   int parity;      // f[parity] holds f^n
   int nx, ny;
+  int pitch;       // elements per row of a distribution plane (>= nx; plane = pitch * ny)
   double dx, c, omega, k, inv_nu, fixed_xi, t_end, ch_factor;
   int set;
   int bc_lo, bc_hi;  // 1D: 0 periodic, 1 characteristic
@@ -176,7 +177,8 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);
   const int x = x0 + tx;
   const bool act = tx < w;
-  const size_t plane = (size_t)nx * ny;
+  const int pitch = a.pitch;
+  const size_t plane = (size_t)pitch * ny;
   const T* __restrict__ fin = a.f[a.parity];
   T* __restrict__ fout = a.f[a.parity ^ 1];
   const StepScalars sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
@@ -187,7 +189,7 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     if (act)
       for (int r = 0; r < h; ++r)
         for (int i = 0; i < 5 * P; ++i) {
-          size_t o = (size_t)i * plane + (size_t)(y0 + r) * nx + x;
+          size_t o = (size_t)i * plane + (size_t)(y0 + r) * pitch + x;
           fout[o] = fin[o];
         }
     if (bx == 0 && by == 0 && tx == 0) {
@@ -214,7 +216,7 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     const int side = t >= h;
     const int r = side ? t - h : t;
     const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
-    const size_t idx = (size_t)(y0 + r) * nx + xr;
+    const size_t idx = (size_t)(y0 + r) * pitch + xr;
     R o[5][P];
     if (!side) {
       collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
@@ -233,10 +235,10 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
   if (act) {
     R o[5][P];
     const int yb = (y0 - 1 + ny) % ny;
-    collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)yb * nx + x, xinv, c, om, set, kk, ch, o);
+    collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)yb * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
     for (int i = 0; i < P; ++i) f4prev[i] = o[3][i];
-    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)y0 * nx + x, xinv, c, om, set, kk, ch, o);
+    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)y0 * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       rb1[i * TX + tx] = o[0][i];
@@ -255,7 +257,7 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     if (act) {
       R o[5][P];
       if (r + 1 < h) {
-        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)(j + 1) * nx + x, xinv, c, om, set, kk, ch, o);
+        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)(j + 1) * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
           rb1[(nb * P + i) * TX + tx] = o[0][i];
@@ -266,7 +268,7 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
         }
       } else {
         const int yt = (y0 + h) % ny;
-        collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)yt * nx + x, xinv, c, om, set, kk, ch, o);
+        collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)yt * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
           f5n[i] = o[4][i];
@@ -276,7 +278,7 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     }
     __syncthreads();
     if (act) {
-      const size_t base = (size_t)j * nx + x;
+      const size_t base = (size_t)j * pitch + x;
       R U[P];
 #pragma unroll
       for (int i = 0; i < P; ++i) {
@@ -309,10 +311,329 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
   commit_max(m1, m2, bad, a.ctl, s1);
 }
 
+// ------------------------------------------------- D2Q5 step, bulk-copy rows
+// Same arithmetic as step2d_tile, but the rows of f^n reach the block through
+// shared memory: an extra producer warp issues 1D bulk asynchronous copies
+// (cp.async.bulk, the TMA engine) of every distribution plane's row segment
+// [x0, x0 + TX) plus the two 16-byte chunks holding the x-ring cells, D rows
+// ahead, each stage completing on its own mbarrier.  The per-row block barrier
+// that already exchanges f*_1 / f*_2 between neighbours also tells the producer
+// that a stage has been consumed.  The producer warp's lanes 0 and 1 collide the
+// two x-ring cells of each row (the consumers never diverge for the ring).
+// Every mbarrier wait is bounded; a wait that gives up sets ERR_TIMEOUT and the
+// block leaves the tile after all threads agree, waiting (bounded) for its
+// copies still in flight.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+      : "memory");
+  return done != 0;
+}
+// Gives up after about kWaitRounds suspended polls (a few seconds at most).
+constexpr uint32_t kWaitRounds = 1u << 17;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitRounds; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+template <class T>
+struct TmaLayout {
+  int TX, TY, D, SW;        // tile, stages, stage row width in elements
+  size_t stage_elems;       // elements of one stage
+  size_t off_stage, off_rb, off_ring, bytes;
+  template <class R, int P>
+  VK_HD static TmaLayout make(int TX, int TY, int D) {
+    TmaLayout L;
+    L.TX = TX;
+    L.TY = TY;
+    L.D = D;
+    L.SW = TX + 2 * (16 / (int)sizeof(T));
+    L.stage_elems = (size_t)5 * P * L.SW;
+    L.off_stage = 128;
+    L.off_rb = L.off_stage + (size_t)D * L.stage_elems * sizeof(T);
+    L.off_rb = (L.off_rb + 15) & ~(size_t)15;
+    L.off_ring = L.off_rb + (size_t)6 * P * TX * sizeof(R);
+    L.bytes = L.off_ring + (size_t)6 * P * sizeof(R) + 16;
+    return L;
+  }
+};
+
+template <class Sys, class T, class R>
+__device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, int by, int TX, int TY, int D,
+                                                unsigned char* smem) {
+  constexpr int P = Sys::P;
+  constexpr int NPL = 5 * P;
+  constexpr int CH = 16 / (int)sizeof(T);
+  const TmaLayout<T> L = TmaLayout<T>::template make<R, P>(TX, TY, D);
+  const int SW = L.SW;
+  const Sys sys = make_sys<Sys>(a.sp);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const bool consumer = tid < TX;
+  const bool producer = !consumer;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+  const int w = min(TX, nx - x0), h = min(TY, ny - y0);
+  const int x = x0 + tid;
+  const bool act = consumer && tid < w;
+  const size_t plane = (size_t)pitch * ny;
+  const T* __restrict__ fin = a.f[a.parity];
+  T* __restrict__ fout = a.f[a.parity ^ 1];
+  const StepScalars sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+  const int s1 = (a.slot + 1) % 3;
+  if (sc.done) {
+    if (act)
+      for (int r = 0; r < h; ++r)
+        for (int i = 0; i < NPL; ++i) {
+          size_t o = (size_t)i * plane + (size_t)(y0 + r) * pitch + x;
+          fout[o] = fin[o];
+        }
+    if (bx == 0 && by == 0 && tid == 0) {
+      const int s2 = (a.slot + 2) % 3;
+      a.ctl->t[s1] = a.ctl->t[a.slot];
+      a.ctl->m1[s1] = a.ctl->m1[a.slot];
+      a.ctl->m2[s1] = a.ctl->m2[a.slot];
+      a.ctl->m1[s2] = 0ull;
+      a.ctl->m2[s2] = 0ull;
+    }
+    return;
+  }
+  if (bx == 0 && by == 0 && tid == 0) step_bookkeeping(a.ctl, a.slot, sc, a.dx, a.fixed_xi, Sys::MHD);
+  const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, om = (R)a.omega, kk = (R)a.k;
+  const int set = a.set;
+
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  T* stages = reinterpret_cast<T*>(smem + L.off_stage);
+  R* rb1 = reinterpret_cast<R*>(smem + L.off_rb);   // [3][P][TX]
+  R* rb2 = rb1 + 3 * P * TX;                       // [3][P][TX]
+  R* ringL = reinterpret_cast<R*>(smem + L.off_ring);  // [3][P]
+  R* ringR = ringL + 3 * P;                            // [3][P]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_ring + 6 * P * sizeof(R));
+
+  const int nrows = h + 2;   // y ring below, h tile rows, y ring above
+  const int xl = (x0 - 1 + nx) % nx, xr = (x0 + w) % nx;
+  const int xlc = (xl / CH) * CH, xrc = (xr / CH) * CH;
+  const int colL = TX + (xl - xlc), colR = TX + CH + (xr - xrc);
+  const uint32_t main_bytes = (uint32_t)((((size_t)w * sizeof(T)) + 15) & ~(size_t)15);
+
+  auto row_y = [&](int j) -> int {
+    if (j == 0) return (y0 - 1 + ny) % ny;
+    if (j == nrows - 1) return (y0 + h) % ny;
+    return y0 + j - 1;
+  };
+  // producer warp: stream row j into stage j % D
+  auto issue = [&](int j) {
+    const int s = j % D;
+    T* st = stages + (size_t)s * L.stage_elems;
+    const bool interior = j >= 1 && j <= h;
+    const uint32_t bytes = (uint32_t)NPL * (main_bytes + (interior ? 32u : 0u));
+    const T* src = fin + (size_t)row_y(j) * pitch;
+    fence_proxy_async_smem();
+    if (lane == 0) mbar_arrive_expect_tx(&bars[s], bytes);
+    __syncwarp();
+    for (int i = lane; i < NPL; i += 32) {
+      const T* ps = src + (size_t)i * plane;
+      T* pd = st + (size_t)i * SW;
+      bulk_g2s(pd, ps + x0, main_bytes, &bars[s]);
+      if (interior) {
+        bulk_g2s(pd + TX, ps + xlc, 16u, &bars[s]);
+        bulk_g2s(pd + TX + CH, ps + xrc, 16u, &bars[s]);
+      }
+    }
+  };
+  auto stage_of = [&](int j) -> const T* { return stages + (size_t)(j % D) * L.stage_elems; };
+
+  if (tid == 0) {
+    for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+    *abort_flag = 0;
+  }
+  __syncthreads();
+  int issued = 0;
+  if (producer) {
+    for (int j = 0; j < min(D, nrows); ++j) issue(j);
+  }
+  issued = min(D, nrows);
+
+  R f4prev[P], f3c[P], f4c[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) f4prev[i] = f3c[i] = f4c[i] = R(0);
+  bool ok = true;
+  if (consumer) {
+    ok = mbar_wait_bounded(&bars[0], 0u);
+    if (ok && act) {
+      R o[5][P];
+      collide_d2q5<Sys, T, R, C_Q4>(sys, stage_of(0), (size_t)SW, (size_t)tid, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+      for (int i = 0; i < P; ++i) f4prev[i] = o[3][i];
+    }
+    ok = ok && mbar_wait_bounded(&bars[1 % D], (uint32_t)((1 / D) & 1));
+    if (ok && act) {
+      R o[5][P];
+      collide_d2q5<Sys, T, R, C_FULL>(sys, stage_of(1), (size_t)SW, (size_t)tid, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        rb1[i * TX + tid] = o[0][i];
+        rb2[i * TX + tid] = o[1][i];
+        f3c[i] = o[2][i];
+        f4c[i] = o[3][i];
+      }
+    }
+  } else if (lane < 2) {
+    ok = mbar_wait_bounded(&bars[1 % D], (uint32_t)((1 / D) & 1));
+    if (ok) {
+      R o[5][P];
+      if (lane == 0) {
+        collide_d2q5<Sys, T, R, C_Q1>(sys, stage_of(1), (size_t)SW, (size_t)colL, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+        for (int i = 0; i < P; ++i) ringL[i] = o[0][i];
+      } else {
+        collide_d2q5<Sys, T, R, C_Q2>(sys, stage_of(1), (size_t)SW, (size_t)colR, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+        for (int i = 0; i < P; ++i) ringR[i] = o[1][i];
+      }
+    }
+  }
+  if (!ok) *abort_flag = 1;
+  __syncthreads();
+  bool aborted = *abort_flag != 0;
+  int pending_from = 0;    // first stream row not yet consumed by every thread
+  if (!aborted) {
+    pending_from = 2;
+    for (int j = issued; j < min(2 + D, nrows); ++j)
+      if (producer) issue(j);
+    issued = min(2 + D, nrows);
+  }
+
+  double m1 = 0.0, m2 = 0.0;
+  bool bad = false;
+  for (int r = 0; r < h && !aborted; ++r) {
+    const int j = r + 2;                 // stream row computed now (tile row r+1 or the top ring)
+    const bool full = r + 1 < h;
+    const int nb = (r + 1) % 3, cb = r % 3;
+    R f5n[P], f3n[P], f4n[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) f5n[i] = f3n[i] = f4n[i] = R(0);
+    const uint32_t par = (uint32_t)((j / D) & 1);
+    if (consumer) {
+      ok = mbar_wait_bounded(&bars[j % D], par);
+      if (ok && act) {
+        R o[5][P];
+        if (full) {
+          collide_d2q5<Sys, T, R, C_FULL>(sys, stage_of(j), (size_t)SW, (size_t)tid, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            rb1[(nb * P + i) * TX + tid] = o[0][i];
+            rb2[(nb * P + i) * TX + tid] = o[1][i];
+            f3n[i] = o[2][i];
+            f4n[i] = o[3][i];
+            f5n[i] = o[4][i];
+          }
+        } else {
+          collide_d2q5<Sys, T, R, C_Q5>(sys, stage_of(j), (size_t)SW, (size_t)tid, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+          for (int i = 0; i < P; ++i) f5n[i] = o[4][i];
+        }
+      }
+    } else if (lane < 2 && full) {
+      ok = mbar_wait_bounded(&bars[j % D], par);
+      if (ok) {
+        R o[5][P];
+        if (lane == 0) {
+          collide_d2q5<Sys, T, R, C_Q1>(sys, stage_of(j), (size_t)SW, (size_t)colL, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+          for (int i = 0; i < P; ++i) ringL[nb * P + i] = o[0][i];
+        } else {
+          collide_d2q5<Sys, T, R, C_Q2>(sys, stage_of(j), (size_t)SW, (size_t)colR, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+          for (int i = 0; i < P; ++i) ringR[nb * P + i] = o[1][i];
+        }
+      }
+    }
+    if (!ok) *abort_flag = 1;
+    __syncthreads();
+    aborted = *abort_flag != 0;
+    if (aborted) break;
+    pending_from = j + 1;
+    if (j + D < nrows) {
+      if (producer) issue(j + D);
+      issued = j + D + 1;
+    }
+    if (act) {
+      const size_t base = (size_t)(y0 + r) * pitch + x;
+      R U[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        R g1 = tid == 0 ? ringL[cb * P + i] : rb1[(cb * P + i) * TX + tid - 1];
+        R g2 = tid == w - 1 ? ringR[cb * P + i] : rb2[(cb * P + i) * TX + tid + 1];
+        R g3 = f3c[i], g4 = f4prev[i], g5 = f5n[i];
+        Store<T>::st(fout + (size_t)(0 * P + i) * plane + base, g1);
+        Store<T>::st(fout + (size_t)(1 * P + i) * plane + base, g2);
+        Store<T>::st(fout + (size_t)(2 * P + i) * plane + base, g3);
+        Store<T>::st(fout + (size_t)(3 * P + i) * plane + base, g4);
+        Store<T>::st(fout + (size_t)(4 * P + i) * plane + base, g5);
+        const T* tp = nullptr;
+        U[i] = round_store(g1, tp) + round_store(g2, tp) + round_store(g3, tp) + round_store(g4, tp) +
+               round_store(g5, tp);
+      }
+      R a1, a2, b1, b2;
+      sys.speeds(U, 0, a1, a2);
+      sys.speeds(U, 1, b1, b2);
+      m1 = fmax(m1, (double)vmax(a1, b1));
+      m2 = fmax(m2, (double)vmax(a2, b2));
+      bad |= !sys.physical(U);
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      f4prev[i] = f4c[i];
+      f3c[i] = f3n[i];
+      f4c[i] = f4n[i];
+    }
+  }
+  if (aborted) {
+    // a wait gave up: report it and let the copies still in flight land first
+    if (tid == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
+    if (producer && lane == 0) {
+      for (int j = pending_from; j < issued; ++j) mbar_wait_bounded(&bars[j % D], (uint32_t)((j / D) & 1));
+    }
+    __syncthreads();
+    return;
+  }
+  commit_max(m1, m2, bad, a.ctl, s1);
+}
+
 template <class Sys, class T, class R>
 __global__ void step2d_kernel(StepArgs<T> a, int TX, int TY) {
   extern __shared__ __align__(16) unsigned char smem[];
   step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
+}
+
+template <class Sys, class T, class R>
+__global__ void step2d_tma_kernel(StepArgs<T> a, int TX, int TY, int D) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  step2d_tile_tma<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, D, smem);
 }
 
 // Batched form: one launch advances every simulation of the batch by one step.
@@ -322,15 +643,18 @@ struct BatchWork {
   int sim, bx, by;
 };
 
-template <class Sys, class T, class R>
+template <class Sys, class T, class R, int VARIANT>
 __global__ void step2d_batch_kernel(const StepArgs<T>* __restrict__ desc, const BatchWork* __restrict__ work,
-                                    int step_off, int TX, int TY) {
-  extern __shared__ __align__(16) unsigned char smem[];
+                                    int step_off, int TX, int TY, int D) {
+  extern __shared__ __align__(128) unsigned char smem[];
   const BatchWork wk = work[blockIdx.x];
   StepArgs<T> a = desc[wk.sim];
   a.parity = (a.parity + step_off) & 1;
   a.slot = (a.slot + step_off) % 3;
-  step2d_tile<Sys, T, R>(a, wk.bx, wk.by, TX, TY, smem);
+  if (VARIANT == 1)
+    step2d_tile_tma<Sys, T, R>(a, wk.bx, wk.by, TX, TY, D, smem);
+  else
+    step2d_tile<Sys, T, R>(a, wk.bx, wk.by, TX, TY, smem);
 }
 
 // ------------------------------------------------------------------ D1Q3 steps
@@ -499,7 +823,8 @@ __global__ void init_max_kernel(const double* __restrict__ U, size_t cells, SysP
   commit_max(m1, m2, bad, ctl, 0);
 }
 
-// f_q = f_q^eq(U) (Eq. 2b) with xi_0, c_h^0 from slot 0.
+// f_q = f_q^eq(U) (Eq. 2b) with xi_0, c_h^0 from slot 0.  U is dense [p][ny][nx];
+// f is pitched [q][p][ny][pitch].
 template <class Sys, class T, class R, int DIM>
 __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, StepArgs<T> a) {
   constexpr int P = Sys::P;
@@ -507,7 +832,10 @@ __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, Step
   const StepScalars sc = step_scalars(a.ctl, 0, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, -1.0, a.dx);
   const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, kk = (R)a.k;
   T* f = a.f[a.parity];
+  const size_t plane = (size_t)a.pitch * a.ny;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t y = i / a.nx, x = i - y * a.nx;
+    const size_t o = y * a.pitch + x;
     R u[P];
 #pragma unroll
     for (int s = 0; s < P; ++s) u[s] = (R)U[s * cells + i];
@@ -517,7 +845,7 @@ __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, Step
 #pragma unroll
       for (int q = 0; q < 3; ++q)
 #pragma unroll
-        for (int s = 0; s < P; ++s) Store<T>::st(f + (size_t)(q * P + s) * cells + i, e[q][s]);
+        for (int s = 0; s < P; ++s) Store<T>::st(f + (size_t)(q * P + s) * plane + o, e[q][s]);
     } else {
       R Fp[P], F[P], e[5][P];
       sys.split(u, 0, a.set, kk, ch, Fp, F);
@@ -536,20 +864,23 @@ __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, Step
 #pragma unroll
       for (int q = 0; q < 5; ++q)
 #pragma unroll
-        for (int s = 0; s < P; ++s) Store<T>::st(f + (size_t)(q * P + s) * cells + i, e[q][s]);
+        for (int s = 0; s < P; ++s) Store<T>::st(f + (size_t)(q * P + s) * plane + o, e[q][s]);
     }
   }
 }
 
-// U_k = sum_q f_q,k (Eq. 3), as double.
+// U_k = sum_q f_q,k (Eq. 3), as double, dense [p][ny][nx] from pitched f.
 template <class T, int P, int Q>
-__global__ void moments_kernel(const T* __restrict__ f, size_t cells, double* __restrict__ U) {
+__global__ void moments_kernel(const T* __restrict__ f, int nx, int ny, int pitch, double* __restrict__ U) {
+  const size_t cells = (size_t)nx * ny, plane = (size_t)pitch * ny;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t y = i / nx, x = i - y * nx;
+    const size_t o = y * pitch + x;
 #pragma unroll
     for (int s = 0; s < P; ++s) {
       double acc = 0.0;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) acc += (double)Store<T>::ld(f + (size_t)(q * P + s) * cells + i);
+      for (int q = 0; q < Q; ++q) acc += (double)Store<T>::ld(f + (size_t)(q * P + s) * plane + o);
       U[s * cells + i] = acc;
     }
   }
@@ -558,15 +889,19 @@ __global__ void moments_kernel(const T* __restrict__ f, size_t cells, double* __
 // Conservation totals, pass 1: block b sums the cells of its fixed chunk in
 // FP64 (fixed thread order, shuffle tree), writing part[s][b].
 template <class T, int P, int Q>
-__global__ void totals_pass1(const T* __restrict__ f, size_t cells, double* __restrict__ part) {
+__global__ void totals_pass1(const T* __restrict__ f, int nx, int ny, int pitch, double* __restrict__ part) {
   __shared__ double red[32];
+  const size_t cells = (size_t)nx * ny, plane = (size_t)pitch * ny;
   const size_t chunk = (cells + gridDim.x - 1) / gridDim.x;
   const size_t lo = blockIdx.x * chunk, hi = min(cells, lo + chunk);
   for (int s = 0; s < P; ++s) {
     double acc = 0.0;
-    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const size_t y = i / nx, x = i - y * nx;
+      const size_t o = y * pitch + x;
 #pragma unroll
-      for (int q = 0; q < Q; ++q) acc += (double)Store<T>::ld(f + (size_t)(q * P + s) * cells + i);
+      for (int q = 0; q < Q; ++q) acc += (double)Store<T>::ld(f + (size_t)(q * P + s) * plane + o);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

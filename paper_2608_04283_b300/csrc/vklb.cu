@@ -28,7 +28,7 @@ struct Ops;
 
 struct vklb_sim {
   int kind, lattice, dim, P, Q, prec, store_bytes;
-  int64_t nx, ny, cells;
+  int64_t nx, ny, cells, pitch;
   double dx, ch_factor;
   SysParams sp;
   int set;
@@ -43,6 +43,7 @@ struct vklb_sim {
   double* dvec;            // [p] device totals
   double* stage;           // [p][cells] double staging for set_state / moments
   int tile_x, tile_y;
+  int variant, stages;     // step kernel: 0 plain, 1 bulk-copy row pipeline with `stages` rows in flight
   bool ready;
   const Ops* ops;
 };
@@ -53,6 +54,7 @@ struct Ops {
   int (*moments)(vklb_sim*, double*);
   int (*totals)(vklb_sim*, double*);
   int (*batch)(vklb_batch*, int64_t, int);
+  size_t (*smem)(int variant, int p, int tx, int ty, int stages);
   size_t real_bytes;
   size_t args_bytes;
 };
@@ -63,6 +65,7 @@ struct vklb_batch {
   void* d_desc;
   BatchWork* d_work;
   int nwork;
+  int variant, stages;
   std::vector<unsigned char> h_desc;
   cudaStream_t stream;
   const Ops* ops;
@@ -83,6 +86,7 @@ StepArgs<T> make_args(const vklb_sim* s, double t_end) {
   a.parity = s->cur;
   a.nx = (int)s->nx;
   a.ny = (int)s->ny;
+  a.pitch = (int)s->pitch;
   a.dx = s->dx;
   a.c = s->c;
   a.omega = s->omega;
@@ -123,6 +127,10 @@ struct Impl {
   }
 
   static size_t smem_bytes(int tx, int ty) { return (size_t)(6 * P * tx + 2 * P * ty) * sizeof(R); }
+  static size_t smem_bytes_v(int variant, int tx, int ty, int d) {
+    if (variant == 1) return TmaLayout<T>::template make<R, P>(tx, ty, d).bytes;
+    return smem_bytes(tx, ty);
+  }
 
   static int step(vklb_sim* s, int64_t n, double t_end) {
     if constexpr (DIM == 1) {
@@ -142,17 +150,21 @@ struct Impl {
       }
       return VKLB_OK;
     } else {
-      const int TX = s->tile_x, TY = s->tile_y;
-      const size_t sm = smem_bytes(TX, TY);
+      const int TX = s->tile_x, TY = s->tile_y, D = s->stages;
+      const size_t sm = smem_bytes_v(s->variant, TX, TY, D);
       static bool attr_set = false;
       if (!attr_set) {
         cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
       }
       dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
       for (int64_t i = 0; i < n; ++i) {
         StepArgs<T> a = make_args<T>(s, t_end);
-        step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
+        if (s->variant == 1)
+          step2d_tma_kernel<Sys, T, R><<<grid, TX + 32, sm, s->stream>>>(a, TX, TY, D);
+        else
+          step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         s->cur ^= 1;
         s->launched += 1;
       }
@@ -163,13 +175,15 @@ struct Impl {
 
   static int moments(vklb_sim* s, double* dU) {
     const int blk = 256;
-    moments_kernel<T, P, Q><<<grid_for(s->cells, blk), blk, 0, s->stream>>>((const T*)s->f[s->cur], (size_t)s->cells, dU);
+    moments_kernel<T, P, Q><<<grid_for(s->cells, blk), blk, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx,
+                                                                            (int)s->ny, (int)s->pitch, dU);
     g_launches += 1;
     return cuda_status(cudaGetLastError());
   }
 
   static int totals(vklb_sim* s, double* host) {
-    totals_pass1<T, P, Q><<<kRedBlocks, 256, 0, s->stream>>>((const T*)s->f[s->cur], (size_t)s->cells, s->part);
+    totals_pass1<T, P, Q><<<kRedBlocks, 256, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx, (int)s->ny,
+                                                             (int)s->pitch, s->part);
     double scale = DIM == 1 ? s->dx : s->dx * s->dx;
     totals_pass2<<<1, 32, 0, s->stream>>>(s->part, kRedBlocks, P, scale, s->dvec);
     g_launches += 2;
@@ -183,11 +197,16 @@ template <class Sys, class T, class R, int DIM>
 struct BatchImpl {
   static void launch(vklb_batch* b, int64_t n) {
     if constexpr (DIM == 2) {
-    const int TX = b->tile_x, TY = b->tile_y;
-    const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes(TX, TY);
-    for (int64_t i = 0; i < n; ++i)
-      step2d_batch_kernel<Sys, T, R><<<b->nwork, TX, sm, b->own>>>((const StepArgs<T>*)b->d_desc, b->d_work,
-                                                                       (int)i, TX, TY);
+    const int TX = b->tile_x, TY = b->tile_y, D = b->stages;
+    const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(b->variant, TX, TY, D);
+    for (int64_t i = 0; i < n; ++i) {
+      if (b->variant == 1)
+        step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX + 32, sm, b->own>>>(
+            (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+      else
+        step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(
+            (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+    }
     }
   }
   static int step(vklb_batch* b, int64_t n, int use_graph) {
@@ -196,7 +215,8 @@ struct BatchImpl {
     } else {
     static bool attr_set = false;
     if (!attr_set) {
-      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr_set = true;
     }
     StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
@@ -244,10 +264,16 @@ struct BatchImpl {
 };
 
 template <class Sys, class T, class R, int DIM>
+size_t smem_of(int variant, int p, int tx, int ty, int stages) {
+  return Impl<Sys, T, R, DIM>::smem_bytes_v(variant, tx, ty, stages);
+}
+
+template <class Sys, class T, class R, int DIM>
 const Ops* ops_of() {
   static const Ops o = {&Impl<Sys, T, R, DIM>::init,    &Impl<Sys, T, R, DIM>::step,
                         &Impl<Sys, T, R, DIM>::moments, &Impl<Sys, T, R, DIM>::totals,
-                        &BatchImpl<Sys, T, R, DIM>::step, sizeof(R), sizeof(StepArgs<T>)};
+                        &BatchImpl<Sys, T, R, DIM>::step, &smem_of<Sys, T, R, DIM>,
+                        sizeof(R),                        sizeof(StepArgs<T>)};
   return &o;
 }
 
@@ -288,6 +314,7 @@ int read_ctl(vklb_sim* s, Ctl* h) {
 
 int err_of(const Ctl& h) {
   // a violated CFL bound (fixed xi) is the cause of any non-physical state after it
+  if (h.err & ERR_TIMEOUT) return VKLB_ERR_TIMEOUT;
   if (h.err & ERR_CFL) return VKLB_ERR_CFL;
   if (h.err & ERR_NONPHYS) return VKLB_ERR_NONPHYSICAL;
   return VKLB_OK;
@@ -376,6 +403,10 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->nx = nx;
   s->ny = ny;
   s->cells = nx * ny;
+  // 2D rows are padded to 32 elements so that every row of a distribution
+  // plane starts on a 64-byte (bf16) / 128-byte (fp32) / 256-byte (fp64)
+  // boundary, as the bulk copies of the step kernel need.
+  s->pitch = dim == 2 ? ((nx + 31) / 32) * 32 : nx;
   s->dx = dx;
   s->ch_factor = sys->ch_factor;
   s->sp.gamma = sys->gamma;
@@ -394,8 +425,10 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->stream = (cudaStream_t)cuda_stream;
   s->tile_x = 64;
   s->tile_y = 16;
+  s->variant = dim == 2 ? 1 : 0;
+  s->stages = 4;
   s->ops = ops;
-  const size_t fbytes = (size_t)s->Q * s->P * (size_t)s->cells * s->store_bytes;
+  const size_t fbytes = (size_t)s->Q * s->P * (size_t)s->pitch * s->ny * s->store_bytes;
   cudaError_t e = cudaSuccess;
   if ((e = cudaMalloc(&s->f[0], fbytes)) != cudaSuccess || (e = cudaMalloc(&s->f[1], fbytes)) != cudaSuccess ||
       (e = cudaMalloc((void**)&s->ctl, sizeof(Ctl))) != cudaSuccess ||
@@ -440,9 +473,20 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
   if (tx == 0) tx = 64;
   if (ty == 0) ty = 16;
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
-  if ((size_t)(6 * s->P * tx + 2 * s->P * ty) * s->ops->real_bytes > 200 * 1024) return VKLB_ERR_ARG;
+  if (s->ops->smem(s->variant, s->P, tx, ty, s->stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->tile_x = tx;
   s->tile_y = ty;
+  return VKLB_OK;
+}
+
+int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
+  if (!s || variant < 0 || variant > 1) return VKLB_ERR_ARG;
+  if (stages == 0) stages = 4;
+  if (stages < 2 || stages > 8) return VKLB_ERR_ARG;
+  if (s->dim != 2 && variant == 1) return VKLB_ERR_UNSUPPORTED;
+  if (s->ops->smem(variant, s->P, s->tile_x, s->tile_y, stages) > 200 * 1024) return VKLB_ERR_ARG;
+  s->variant = variant;
+  s->stages = stages;
   return VKLB_OK;
 }
 
@@ -534,11 +578,13 @@ int vklb_info(const vklb_sim* s, vklb_info_t* info) {
   info->store_bytes = s->store_bytes;
   info->cells = s->cells;
   info->bytes_per_lup = 2LL * s->Q * s->P * s->store_bytes;
-  info->state_bytes = (int64_t)s->Q * s->P * s->cells * s->store_bytes;
+  info->state_bytes = (int64_t)s->Q * s->P * s->pitch * s->ny * s->store_bytes;
+  info->pitch = s->pitch;
   info->dx = s->dx;
   info->tile_x = s->tile_x;
   info->tile_y = s->tile_y;
   info->kernels_per_step = 1;
+  info->variant = s->variant;
   return VKLB_OK;
 }
 
@@ -550,7 +596,7 @@ int vklb_device_state(const vklb_sim* s, void** f_dev) {
 
 int vklb_state_bytes(const vklb_sim* s, size_t* bytes) {
   if (!s || !bytes) return VKLB_ERR_ARG;
-  *bytes = sizeof(BlobHeader) + sizeof(Ctl) + (size_t)s->Q * s->P * s->cells * s->store_bytes;
+  *bytes = sizeof(BlobHeader) + sizeof(Ctl) + (size_t)s->Q * s->P * s->pitch * s->ny * s->store_bytes;
   return VKLB_OK;
 }
 
@@ -564,7 +610,7 @@ int vklb_get_state(vklb_sim* s, void* blob, size_t bytes) {
   char* p = (char*)blob + sizeof(hdr);
   int st = cuda_status(cudaMemcpyAsync(p, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
   if (st) return st;
-  const size_t fb = (size_t)s->Q * s->P * s->cells * s->store_bytes;
+  const size_t fb = (size_t)s->Q * s->P * s->pitch * s->ny * s->store_bytes;
   if ((st = cuda_status(cudaMemcpyAsync(p + sizeof(Ctl), s->f[s->cur], fb, cudaMemcpyDeviceToHost, s->stream)))) return st;
   if ((st = cuda_status(cudaStreamSynchronize(s->stream)))) return st;
   Ctl h;
@@ -585,7 +631,7 @@ int vklb_put_state(vklb_sim* s, const void* blob, size_t bytes) {
   if (st) return st;
   s->cur = 0;
   s->launched = hdr.launched;
-  const size_t fb = (size_t)s->Q * s->P * s->cells * s->store_bytes;
+  const size_t fb = (size_t)s->Q * s->P * s->pitch * s->ny * s->store_bytes;
   if ((st = cuda_status(cudaMemcpyAsync(s->f[0], p + sizeof(Ctl), fb, cudaMemcpyHostToDevice, s->stream)))) return st;
   if ((st = cuda_status(cudaStreamSynchronize(s->stream)))) return st;
   s->ready = true;
@@ -622,13 +668,16 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
   for (int i = 0; i < n; ++i) {
     const vklb_sim* s = sims[i];
     if (!s || !s->ready) return VKLB_ERR_STATE;
-    if (s->ops != s0->ops || s->set != s0->set) return VKLB_ERR_ARG;
+    if (s->ops != s0->ops || s->set != s0->set || s->variant != s0->variant || s->stages != s0->stages)
+      return VKLB_ERR_ARG;
   }
   vklb_batch* b = new (std::nothrow) vklb_batch();
   if (!b) return VKLB_ERR_NOMEM;
   b->sims.assign(sims, sims + n);
-  b->tile_x = 64;
-  b->tile_y = 16;
+  b->tile_x = s0->tile_x;
+  b->tile_y = s0->tile_y;
+  b->variant = s0->variant;
+  b->stages = s0->stages;
   b->stream = s0->stream;
   b->ops = s0->ops;
   b->h_desc.resize(s0->ops->args_bytes * n);
@@ -656,7 +705,7 @@ int vklb_batch_set_tiling(vklb_batch* b, int32_t tx, int32_t ty) {
   if (tx == 0) tx = 64;
   if (ty == 0) ty = 16;
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
-  if ((size_t)(6 * b->sims[0]->P * tx + 2 * b->sims[0]->P * ty) * b->ops->real_bytes > 200 * 1024) return VKLB_ERR_ARG;
+  if (b->ops->smem(b->variant, b->sims[0]->P, tx, ty, b->stages) > 200 * 1024) return VKLB_ERR_ARG;
   b->tile_x = tx;
   b->tile_y = ty;
   return batch_build_work(b);

@@ -54,7 +54,7 @@ class Info(C.Structure):
     _fields_ = [("p", C.c_int32), ("q", C.c_int32), ("precision", C.c_int32), ("store_bytes", C.c_int32),
                 ("cells", C.c_int64), ("bytes_per_lup", C.c_int64), ("state_bytes", C.c_int64),
                 ("dx", C.c_double), ("tile_x", C.c_int32), ("tile_y", C.c_int32),
-                ("kernels_per_step", C.c_int32)]
+                ("kernels_per_step", C.c_int32), ("variant", C.c_int32), ("pitch", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -64,6 +64,7 @@ _SIGS = {
                               C.c_double, C.c_int32, _P, C.POINTER(_P)]),
     "vklb_set_state": (C.c_int, [_P, _P, C.c_int32]),
     "vklb_set_tiling": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "vklb_set_variant": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "vklb_step": (C.c_int, [_P, C.c_int64]),
     "vklb_step_to": (C.c_int, [_P, C.c_double]),
     "vklb_sync": (C.c_int, [_P]),
@@ -165,6 +166,11 @@ class Sim:
 
     def set_tiling(self, tx, ty):
         _check(_lib.vklb_set_tiling(self._h, int(tx), int(ty)), "vklb_set_tiling")
+        _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
+
+    def set_variant(self, variant, stages=0):
+        """0: plain coalesced loads; 1: bulk-copy (TMA) row pipeline with ``stages`` rows in flight."""
+        _check(_lib.vklb_set_variant(self._h, int(variant), int(stages)), "vklb_set_variant")
         _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
 
     def step(self, n=1):

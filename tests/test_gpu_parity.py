@@ -29,13 +29,15 @@ def _vortex(nx, ny):
     return np.ascontiguousarray(inputs.isentropic_vortex(nx, lo=0.0, hi=10.0)[:, :ny, :])
 
 
-def _run_pair(vk, name, U0, n, lo, hi, steps, precision, tile=None, oracle_kw=None, **kw):
+def _run_pair(vk, name, U0, n, lo, hi, steps, precision, tile=None, oracle_kw=None, variant=None, **kw):
     okw = dict(oracle_kw or {})
     sysm = {"euler": lambda: systems.Euler(kw.get("gamma", 1.4), len(n)),
             "swe": lambda: systems.ShallowWater(kw.get("g", 9.81), len(n)),
             "mhd_glm": lambda: systems.MHDGLM(kw.get("gamma", 5 / 3)),
             "advection": lambda: systems.Advection(kw.get("adv_speed", (1.0, 0.0)), len(n))}[name]()
     sim = vk.Sim(name, n, lo, hi, precision=precision, **kw)
+    if variant is not None:
+        sim.set_variant(*variant)
     if tile:
         sim.set_tiling(*tile)
     sim.set_state(U0)
@@ -54,11 +56,15 @@ def _run_pair(vk, name, U0, n, lo, hi, steps, precision, tile=None, oracle_kw=No
     return got, ref.moments(), (t, nst, xi), (ref.t, ref.steps, ref.xi), sim
 
 
-@pytest.mark.parametrize("tile", [None, (32, 8), (64, 4)])
-def test_euler_vortex_fp64(vk, tile):
+@pytest.mark.parametrize("variant", [(1, 4), (1, 2), (0, 0), (1, 8)])
+@pytest.mark.parametrize("tile", [None, (32, 8), (64, 4), (32, 40)])
+def test_euler_vortex_fp64(vk, tile, variant):
+    """Both step-kernel variants (plain loads; bulk-copy row pipeline with 2-8
+    stages) and several tilings, including tiles taller than the grid."""
     n = (48, 40)
     lo, hi = _box(n, 10.0)
-    got, want, gt, rt, _ = _run_pair(vk, "euler", _vortex(*n), n, lo, hi, 30, "fp64", tile=tile, omega=2.0, cfl=0.3)
+    got, want, gt, rt, _ = _run_pair(vk, "euler", _vortex(*n), n, lo, hi, 30, "fp64", tile=tile, omega=2.0, cfl=0.3,
+                                     variant=variant)
     assert max_rel(got, want).max() <= 1e-11
     assert gt[1] == rt[1] == 30
     assert abs(gt[0] - rt[0]) <= 1e-12 * rt[0]
@@ -101,13 +107,15 @@ def test_swe_hump_2d(vk, precision, tol):
     assert err.max() <= tol, err
 
 
+@pytest.mark.parametrize("variant", [(1, 4), (0, 0)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
-def test_mhd_orszag_tang(vk, precision, tol):
+def test_mhd_orszag_tang(vk, precision, tol, variant):
     n = (36, 32)
     L = 2 * np.pi
     U0 = np.ascontiguousarray(inputs.orszag_tang(36)[:, :32, :])
     lo, hi = (0.0, 0.0), (L, L * 32 / 36)
-    got, want, gt, rt, _ = _run_pair(vk, "mhd_glm", U0, n, lo, hi, 20, precision, omega=1.0, cfl=0.3, gamma=5 / 3)
+    got, want, gt, rt, _ = _run_pair(vk, "mhd_glm", U0, n, lo, hi, 20, precision, omega=1.0, cfl=0.3, gamma=5 / 3,
+                                     variant=variant)
     err = max_rel(got, want) if precision == "fp64" else rel_l1(got, want)
     assert err.max() <= tol, err
     if precision == "fp64":
