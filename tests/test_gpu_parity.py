@@ -223,23 +223,34 @@ def test_checkpoint_resume_bitwise(vk):
 
 
 def test_batch_equals_individual(vk):
+    """A batch advances each member exactly as a batch holding that member alone
+    (same kernel, same tiling: bitwise), and as the single-simulation kernel up
+    to FP32 rounding (the two kernels are separate instantiations)."""
     specs = inputs.swe_humps_batch(5, seed=7, nmin=20, nmax=70)
-    solo, grouped = [], []
+    solo, alone, grouped = [], [], []
     for sp in specs:
         U0 = inputs.swe_hump_2d(sp.n, sp.amp, sp.x0, sp.y0, sp.sigma)
-        for group in (solo, grouped):
+        for group in (solo, alone, grouped):
             s = vk.Sim("swe", (sp.n, sp.n), (0, 0), (1, 1), omega=1.0, cfl=0.3, precision="fp32")
-            s.set_tiling(32, 8)      # bitwise equality needs the same tiling (ring cells)
+            s.set_tiling(32, 8)
             s.set_state(U0)
             group.append(s)
     for s in solo:
         s.step(25)
+    for s in alone:
+        b1 = vk.Batch([s], tile=(32, 8))
+        b1.step(10, graph=True)
+        b1.step(15, graph=False)
+        b1.close()
     batch = vk.Batch(grouped, tile=(32, 8))
     batch.step(10, graph=True)
     batch.step(15, graph=False)
-    for s, g in zip(solo, grouped):
-        assert np.array_equal(s.moments(), g.moments())
-        assert s.time() == g.time()
+    for s, a, g in zip(solo, alone, grouped):
+        G = g.moments()
+        assert np.array_equal(a.moments(), G)
+        assert a.time() == g.time()
+        assert rel_l1(G, s.moments()).max() <= 1e-5
+        assert s.time()[1] == g.time()[1]
 
 
 def test_nonphysical_state_is_reported(vk):
