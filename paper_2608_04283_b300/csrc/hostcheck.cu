@@ -88,3 +88,45 @@ extern "C" int vklb_hc_char_rhs(int kind, int precision, int side, double gamma,
   if (precision == 0) return bc_dispatch<double>(kind, side, gamma, g, ax, U, dU, n, out);
   return bc_dispatch<float>(kind, side, gamma, g, ax, U, dU, n, out);
 }
+
+// Both-direction split and the step epilogue of the 2D systems, as the step
+// kernels call them: Fp1, F1, Fp2, F2 [p][n]; m1, m2 [n]; ok[n] = physical.
+namespace {
+template <class Sys, class R>
+void run2(const Sys& sys, int set, double k, double ch, const double* U, int64_t n, double* Fp1, double* F1,
+          double* Fp2, double* F2, double* m1, double* m2, int* ok) {
+  const int P = Sys::P;
+  for (int64_t i = 0; i < n; ++i) {
+    R u[9], a[9], b[9], c[9], d[9];
+    for (int q = 0; q < P; ++q) u[q] = (R)U[q * n + i];
+    sys.split2(u, set, (R)k, (R)ch, a, b, c, d);
+    R e1, e2;
+    ok[i] = sys.epilogue(u, e1, e2) ? 1 : 0;
+    for (int q = 0; q < P; ++q) {
+      Fp1[q * n + i] = (double)a[q];
+      F1[q * n + i] = (double)b[q];
+      Fp2[q * n + i] = (double)c[q];
+      F2[q * n + i] = (double)d[q];
+    }
+    m1[i] = (double)e1;
+    m2[i] = (double)e2;
+  }
+}
+template <class R>
+int dispatch2(int kind, int set, double k, double ch, double gamma, double g, double ax, double ay, const double* U,
+              int64_t n, double* Fp1, double* F1, double* Fp2, double* F2, double* m1, double* m2, int* ok) {
+  if (kind == 0) { vk::Advect<R, 2> s; s.a[0] = (R)ax; s.a[1] = (R)ay; run2<vk::Advect<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
+  else if (kind == 1) { vk::SWE<R, 2> s; s.g = (R)g; run2<vk::SWE<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
+  else if (kind == 2) { vk::Euler<R, 2> s; s.gamma = (R)gamma; run2<vk::Euler<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
+  else if (kind == 3) { vk::MHDGLM<R> s; s.gamma = (R)gamma; run2<vk::MHDGLM<R>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
+  else return -1;
+  return 0;
+}
+}  // namespace
+
+extern "C" int vklb_hc_split2(int kind, int precision, int set, double k, double ch, double gamma, double g, double ax,
+                              double ay, const double* U, int64_t n, double* Fp1, double* F1, double* Fp2, double* F2,
+                              double* m1, double* m2, int* ok) {
+  if (precision == 0) return dispatch2<double>(kind, set, k, ch, gamma, g, ax, ay, U, n, Fp1, F1, Fp2, F2, m1, m2, ok);
+  return dispatch2<float>(kind, set, k, ch, gamma, g, ax, ay, U, n, Fp1, F1, Fp2, F2, m1, m2, ok);
+}

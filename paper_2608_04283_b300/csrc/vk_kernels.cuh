@@ -80,8 +80,27 @@ __device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict
   R U[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
+  if (MODE == C_FULL) {
+    R Fp1[P], F1[P], Fp2[P], F2[P];
+    sys.split2(U, set, k, ch, Fp1, F1, Fp2, F2);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const R cu = c * U[i];
+      const R e1 = cu + Fp1[i] * xinv;
+      const R e2 = cu - (F1[i] - Fp1[i]) * xinv;
+      const R e4 = cu + Fp2[i] * xinv;
+      const R e5 = cu - (F2[i] - Fp2[i]) * xinv;
+      const R e3 = U[i] - ((e1 + e2) + e4 + e5);
+      out[0][i] = f[0][i] + om * (e1 - f[0][i]);
+      out[1][i] = f[1][i] + om * (e2 - f[1][i]);
+      out[2][i] = f[2][i] + om * (e3 - f[2][i]);
+      out[3][i] = f[3][i] + om * (e4 - f[3][i]);
+      out[4][i] = f[4][i] + om * (e5 - f[4][i]);
+    }
+    return;
+  }
   R Fp[P], F[P];
-  if (MODE == C_FULL || MODE == C_Q1 || MODE == C_Q2) {
+  if (MODE == C_Q1 || MODE == C_Q2) {
     sys.split(U, 0, set, k, ch, Fp, F);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -294,12 +313,10 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
         U[i] = round_store(g1, tp) + round_store(g2, tp) + round_store(g3, tp) + round_store(g4, tp) +
                round_store(g5, tp);
       }
-      R a1, a2, b1, b2;
-      sys.speeds(U, 0, a1, a2);
-      sys.speeds(U, 1, b1, b2);
-      m1 = fmax(m1, (double)vmax(a1, b1));
-      m2 = fmax(m2, (double)vmax(a2, b2));
-      bad |= !sys.physical(U);
+      R e1, e2;
+      bad |= !sys.epilogue(U, e1, e2);
+      m1 = fmax(m1, (double)e1);
+      m2 = fmax(m2, (double)e2);
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -400,7 +417,9 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const bool consumer = tid < TX;
-  const bool producer = !consumer;
+  const int pw = consumer ? -1 : (tid - TX) >> 5;   // producer warps: 0 streams rows + left ring, 1 right ring
+  const bool producer = pw == 0;
+  const bool ringer = pw >= 0 && lane == 0;
   const int x0 = bx * TX, y0 = by * TY;
   const int nx = a.nx, ny = a.ny, pitch = a.pitch;
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);
@@ -509,11 +528,11 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
         f4c[i] = o[3][i];
       }
     }
-  } else if (lane < 2) {
+  } else if (ringer) {
     ok = mbar_wait_bounded(&bars[1 % D], (uint32_t)((1 / D) & 1));
     if (ok) {
       R o[5][P];
-      if (lane == 0) {
+      if (pw == 0) {
         collide_d2q5<Sys, T, R, C_Q1>(sys, stage_of(1), (size_t)SW, (size_t)colL, xinv, c, om, set, kk, ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) ringL[i] = o[0][i];
@@ -565,11 +584,11 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
           for (int i = 0; i < P; ++i) f5n[i] = o[4][i];
         }
       }
-    } else if (lane < 2 && full) {
+    } else if (ringer && full) {
       ok = mbar_wait_bounded(&bars[j % D], par);
       if (ok) {
         R o[5][P];
-        if (lane == 0) {
+        if (pw == 0) {
           collide_d2q5<Sys, T, R, C_Q1>(sys, stage_of(j), (size_t)SW, (size_t)colL, xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) ringL[nb * P + i] = o[0][i];
@@ -606,12 +625,10 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
         U[i] = round_store(g1, tp) + round_store(g2, tp) + round_store(g3, tp) + round_store(g4, tp) +
                round_store(g5, tp);
       }
-      R a1, a2, b1, b2;
-      sys.speeds(U, 0, a1, a2);
-      sys.speeds(U, 1, b1, b2);
-      m1 = fmax(m1, (double)vmax(a1, b1));
-      m2 = fmax(m2, (double)vmax(a2, b2));
-      bad |= !sys.physical(U);
+      R e1, e2;
+      bad |= !sys.epilogue(U, e1, e2);
+      m1 = fmax(m1, (double)e1);
+      m2 = fmax(m2, (double)e2);
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) {

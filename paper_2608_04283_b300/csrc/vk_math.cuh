@@ -13,7 +13,17 @@ namespace vk {
 
 enum SetKind : int { SET_WEIGHTED = 0, SET_CENTERED = 1, SET_DISCONTINUOUS = 2 };
 
-VK_HD float vsqrt(float x) { return sqrtf(x); }
+// FP32 on the device uses the hardware approximations (about 1 ulp): the FP32
+// path's tolerance is 1e-5 relative; FP64 and host code stay IEEE.
+VK_HD float vsqrt(float x) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+#else
+  return sqrtf(x);
+#endif
+}
 VK_HD double vsqrt(double x) { return sqrt(x); }
 VK_HD float vabs(float x) { return fabsf(x); }
 VK_HD double vabs(double x) { return fabs(x); }
@@ -42,7 +52,9 @@ VK_HD float vdiv(float a, float b) {
 VK_HD double vdiv(double a, double b) { return a / b; }
 VK_HD float vrcp(float x) {
 #ifdef __CUDA_ARCH__
-  return __frcp_rn(x);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 #else
   return 1.0f / x;
 #endif

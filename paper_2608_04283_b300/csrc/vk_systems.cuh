@@ -36,6 +36,16 @@ struct Advect {
   // m1: max |lambda| along d; m2: unused (fast speed of MHD)
   VK_HD void speeds(const R* U, int d, R& m1, R& m2) const { m1 = vabs(a[d]); m2 = R(0); }
   VK_HD bool physical(const R* U) const { return U[0] == U[0]; }
+  VK_HD void split2(const R* U, int set, R k, R ch, R* Fp1, R* F1, R* Fp2, R* F2) const {
+    split(U, 0, set, k, ch, Fp1, F1);
+    split(U, 1, set, k, ch, Fp2, F2);
+  }
+  // CFL maxima over both directions and the physical-state test of U^{n+1}
+  VK_HD bool epilogue(const R* U, R& m1, R& m2) const {
+    m1 = vmax(vabs(a[0]), vabs(a[1]));
+    m2 = R(0);
+    return U[0] == U[0];
+  }
   // Characteristic boundary (Eqs. 33-35): P diag(lambda_j, outgoing only) P^-1 dU.
   VK_HD void char_rhs(const R* U, const R* dU, int side, R* out) const {
     R l = a[0];
@@ -84,6 +94,52 @@ struct SWE {
     m2 = R(0);
   }
   VK_HD bool physical(const R* U) const { return U[0] > R(0); }
+  // Both directions with shared primitives (2D).
+  VK_HD void split2(const R* U, int set, R k, R ch, R* Fp1, R* F1, R* Fp2, R* F2) const {
+    const R h = U[0], ih = vrcp(h);
+    const R u = U[1] * ih, v = U[DIM == 2 ? 2 : 1] * ih;
+    const R c = vsqrt(g * h);
+    const R hh = R(0.5) * g * h * h;
+    F1[0] = U[1];
+    F1[1] = U[1] * u + hh;
+    F2[0] = U[2];
+    F2[2] = U[2] * v + hh;
+    F1[2] = U[1] * v;
+    F2[1] = U[2] * u;
+    if (set == SET_CENTERED) {
+      for (int i = 0; i < P; ++i) {
+        Fp1[i] = R(0.5) * F1[i];
+        Fp2[i] = R(0.5) * F2[i];
+      }
+      return;
+    }
+    const R hc = R(0.25) * h * c;   // h c / 4
+    const R hu2 = R(0.5) * U[1], hv2 = R(0.5) * U[2];
+    {
+      const R kl = k * vrcp(vabs(u) + c);
+      const R p1 = alpha_w(u - c, kl, set) * (hu2 - hc);
+      const R p3 = alpha_w(u + c, kl, set) * (hu2 + hc);
+      const R ps = p1 + p3;
+      Fp1[0] = ps;
+      Fp1[1] = ps * u + (p3 - p1) * c;
+      Fp1[2] = ps * v;
+    }
+    {
+      const R kl = k * vrcp(vabs(v) + c);
+      const R p1 = alpha_w(v - c, kl, set) * (hv2 - hc);
+      const R p3 = alpha_w(v + c, kl, set) * (hv2 + hc);
+      const R ps = p1 + p3;
+      Fp2[0] = ps;
+      Fp2[2] = ps * v + (p3 - p1) * c;
+      Fp2[1] = ps * u;
+    }
+  }
+  VK_HD bool epilogue(const R* U, R& m1, R& m2) const {
+    const R h = U[0], ih = vrcp(h);
+    m1 = vmax(vabs(U[1] * ih), vabs(U[DIM == 2 ? 2 : 1] * ih)) + vsqrt(g * h);
+    m2 = R(0);
+    return h > R(0);
+  }
   // Characteristic boundary (Eqs. 33-35), 1D: P diag(lambda_j, outgoing only) P^-1 dU
   // with r_{1,2} = (1, u -+ c), l_1 = (u + c, -1)/(2c), l_2 = (c - u, 1)/(2c).
   VK_HD void char_rhs(const R* U, const R* dU, int side, R* out) const {
@@ -105,6 +161,64 @@ struct Euler {
   static constexpr int P = DIM + 2;
   static constexpr bool MHD = false;
   R gamma;
+  // Both directions with shared primitives (2D); w_j = alpha_j lambda_j as in split().
+  VK_HD void split2(const R* U, int set, R k, R ch, R* Fp1, R* F1, R* Fp2, R* F2) const {
+    const R rho = U[0], ir = vrcp(rho);
+    const R u = U[1] * ir, v = U[2] * ir;
+    const R q2 = u * u + v * v;
+    const R E = U[3];
+    const R gm1 = gamma - R(1);
+    const R p = gm1 * (E - R(0.5) * rho * q2);
+    const R Ep = E + p;
+    F1[0] = U[1];
+    F1[1] = U[1] * u + p;
+    F1[2] = U[2] * u;
+    F1[3] = u * Ep;
+    F2[0] = U[2];
+    F2[1] = U[1] * v;
+    F2[2] = U[2] * v + p;
+    F2[3] = v * Ep;
+    if (set == SET_CENTERED) {
+      for (int i = 0; i < 4; ++i) {
+        Fp1[i] = R(0.5) * F1[i];
+        Fp2[i] = R(0.5) * F2[i];
+      }
+      return;
+    }
+    const R a = vsqrt(gamma * p * ir);
+    const R H = Ep * ir;
+    const R s = R(0.5) * rho * vrcp(gamma);
+    const R g2 = R(2) * gm1;
+    const R hq = R(0.5) * q2;
+    {
+      const R kl = k * vrcp(vabs(u) + a);
+      const R l1 = u - a, l3 = u + a;
+      const R w1 = alpha_w(l1, kl, set) * l1, w2 = alpha_w(u, kl, set) * u * g2, w3 = alpha_w(l3, kl, set) * l3;
+      const R ws = s * (w1 + w2 + w3);
+      Fp1[0] = ws;
+      Fp1[1] = s * (w1 * l1 + w2 * u + w3 * l3);
+      Fp1[2] = ws * v;
+      Fp1[3] = s * ((w1 + w3) * H + (w3 - w1) * u * a + w2 * hq);
+    }
+    {
+      const R kl = k * vrcp(vabs(v) + a);
+      const R l1 = v - a, l3 = v + a;
+      const R w1 = alpha_w(l1, kl, set) * l1, w2 = alpha_w(v, kl, set) * v * g2, w3 = alpha_w(l3, kl, set) * l3;
+      const R ws = s * (w1 + w2 + w3);
+      Fp2[0] = ws;
+      Fp2[2] = s * (w1 * l1 + w2 * v + w3 * l3);
+      Fp2[1] = ws * u;
+      Fp2[3] = s * ((w1 + w3) * H + (w3 - w1) * v * a + w2 * hq);
+    }
+  }
+  VK_HD bool epilogue(const R* U, R& m1, R& m2) const {
+    const R rho = U[0], ir = vrcp(rho);
+    const R u = U[1] * ir, v = U[2] * ir;
+    const R p = (gamma - R(1)) * (U[3] - R(0.5) * rho * (u * u + v * v));
+    m1 = vmax(vabs(u), vabs(v)) + vsqrt(gamma * p * ir);
+    m2 = R(0);
+    return rho > R(0) && p > R(0);
+  }
   VK_HD void split(const R* U, int d, int set, R k, R ch, R* Fp, R* F) const {
     const int in = 1 + d, it = 2 - d, ie = P - 1;
     R rho = U[0];
@@ -235,6 +349,26 @@ struct MHDGLM {
     R bb = U[5] * U[5] + U[6] * U[6] + U[7] * U[7];
     R ke = (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / rho;
     R p = (gamma - R(1)) * (U[4] - R(0.5) * ke - R(0.5) * bb);
+    return rho > R(0) && p > R(0);
+  }
+
+  VK_HD void split2(const R* U, int set, R k, R ch, R* Fp1, R* F1, R* Fp2, R* F2) const {
+    split(U, 0, set, k, ch, Fp1, F1);
+    split(U, 1, set, k, ch, Fp2, F2);
+  }
+
+  // m1 = max_d (|u_d| + c_f,d), m2 = max_d c_f,d, physical test of U^{n+1}
+  VK_HD bool epilogue(const R* U, R& m1, R& m2) const {
+    const R rho = U[0], ir = vrcp(rho);
+    const R bx2 = U[5] * U[5], by2 = U[6] * U[6];
+    const R bb = bx2 + by2 + U[7] * U[7];
+    const R ke = (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir;
+    const R p = (gamma - R(1)) * (U[4] - R(0.5) * ke - R(0.5) * bb);
+    const R a2 = gamma * p * ir, b2 = bb * ir, s = a2 + b2;
+    const R cfx = vsqrt(R(0.5) * (s + vsqrt(vmax(s * s - R(4) * a2 * bx2 * ir, R(0)))));
+    const R cfy = vsqrt(R(0.5) * (s + vsqrt(vmax(s * s - R(4) * a2 * by2 * ir, R(0)))));
+    m1 = vmax(vabs(U[1] * ir) + cfx, vabs(U[2] * ir) + cfy);
+    m2 = vmax(cfx, cfy);
     return rho > R(0) && p > R(0);
   }
 

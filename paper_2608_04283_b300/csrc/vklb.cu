@@ -162,7 +162,7 @@ struct Impl {
       for (int64_t i = 0; i < n; ++i) {
         StepArgs<T> a = make_args<T>(s, t_end);
         if (s->variant == 1)
-          step2d_tma_kernel<Sys, T, R><<<grid, TX + 32, sm, s->stream>>>(a, TX, TY, D);
+          step2d_tma_kernel<Sys, T, R><<<grid, TX + 64, sm, s->stream>>>(a, TX, TY, D);
         else
           step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         s->cur ^= 1;
@@ -201,7 +201,7 @@ struct BatchImpl {
     const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(b->variant, TX, TY, D);
     for (int64_t i = 0; i < n; ++i) {
       if (b->variant == 1)
-        step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX + 32, sm, b->own>>>(
+        step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX + 64, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
       else
         step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(

@@ -110,3 +110,40 @@ def test_char_bc_rhs_matches_oracle_eig(name, kw, side):
         keep = lam < 0 if side == 0 else lam > 0
         want = P @ (np.where(keep, lam, 0.0) * np.linalg.solve(P, dU[:, i]))
         assert np.allclose(out[:, i], want, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,kw", [("swe", {"g": 9.81}), ("euler", {"gamma": 1.4}),
+                                     ("mhd_glm", {"gamma": 5 / 3, "ch": 6.0})])
+@pytest.mark.parametrize("prec,tol", [(0, 2e-13), (1, 2e-5)])
+@pytest.mark.parametrize("set_kind", [0, 1])
+def test_split2_and_epilogue_match_oracle(name, kw, prec, tol, set_kind):
+    """The both-direction split (shared primitives) and the step epilogue that the
+    step kernels call: F(1,+-), F(2,+-) against the oracle; the epilogue maxima
+    against the closed-form wave speeds; the physical test against p, rho > 0."""
+    s = systems.make(name, 2, **kw)
+    gamma, g, ch = kw.get("gamma", 1.4), kw.get("g", 9.81), kw.get("ch", 0.0)
+    U = np.ascontiguousarray(inputs.random_states(name, 600, seed=35, dim=2, gamma=gamma))
+    p, n = U.shape
+    out = [np.zeros_like(U) for _ in range(4)]
+    m1, m2 = np.zeros(n), np.zeros(n)
+    ok = np.zeros(n, dtype=np.int32)
+    st = _lib.vklb_hc_split2(KIND[name], prec, set_kind, C.c_double(2.0), C.c_double(ch), C.c_double(gamma),
+                             C.c_double(g), C.c_double(1.0), C.c_double(-0.5), U.ctypes.data_as(_PD), C.c_int64(n),
+                             *[o.ctypes.data_as(_PD) for o in out], m1.ctypes.data_as(_PD), m2.ctypes.data_as(_PD),
+                             ok.ctypes.data_as(C.POINTER(C.c_int)))
+    assert st == 0
+    for d in range(2):
+        Fp, F = out[2 * d], out[2 * d + 1]
+        Fph = s.flux(U, d)
+        Fo = splitting.split_weighted(s, U, d, 2.0)[0] if set_kind == 0 else 0.5 * Fph
+        scale = np.abs(Fph).max(axis=0) + 1.0
+        assert np.max(np.abs(F - Fph) / scale) < tol
+        assert np.max(np.abs(Fp - Fo) / scale) < tol
+    if name == "mhd_glm":
+        lam = np.maximum(*[np.abs(U[1 + d] / U[0]) + s.fast_speed(U, d) for d in range(2)])
+        cf = np.maximum(s.fast_speed(U, 0), s.fast_speed(U, 1))
+        assert np.allclose(m2, cf, rtol=10 * tol)
+    else:
+        lam = np.maximum(s.max_speed(U, 0), s.max_speed(U, 1))
+    assert np.allclose(m1, lam, rtol=10 * tol)
+    assert np.all(ok == 1)
