@@ -185,10 +185,20 @@ __device__ __forceinline__ void step_bookkeeping(Ctl* ctl, int slot, const StepS
 }
 
 // ------------------------------------------------------------------ D2Q5 step
-template <class Sys, class T, class R>
-__device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by, int TX, int TY,
-                                            unsigned char* smem) {
+// March over the rows of one tile in direction DIR (+1 up, -1 down).  Tiles of
+// even row index march up and odd ones down, so the two tiles that share a
+// boundary read the boundary rows (their own and the ring) at the same time,
+// the second read then hitting L2.  Going up, f^{n+1}_4(y) = f*_4(y - 1) comes
+// from the previous row and f^{n+1}_5(y) = f*_5(y + 1) from the next one; going
+// down the two roles swap.
+template <class Sys, class T, class R, int DIR>
+__device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const StepScalars& sc, int bx, int by,
+                                                int TX, int TY, unsigned char* smem) {
   constexpr int P = Sys::P;
+  constexpr int QB = DIR > 0 ? 3 : 4;            // component carried from the previous row
+  constexpr int QA = DIR > 0 ? 4 : 3;            // component taken from the next row
+  constexpr int MB = DIR > 0 ? C_Q4 : C_Q5;      // ring row behind the march
+  constexpr int MA = DIR > 0 ? C_Q5 : C_Q4;      // ring row ahead of the march
   const Sys sys = make_sys<Sys>(a.sp);
   const int tx = threadIdx.x;
   const int x0 = bx * TX, y0 = by * TY;
@@ -200,34 +210,14 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
   const size_t plane = (size_t)pitch * ny;
   const T* __restrict__ fin = a.f[a.parity];
   T* __restrict__ fout = a.f[a.parity ^ 1];
-  const StepScalars sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
   const int s1 = (a.slot + 1) % 3;
-  if (sc.done) {
-    // t_end already reached: this launch is a no-op that keeps the ping-pong
-    // consistent (f^{n+1} = f^n, same control words).
-    if (act)
-      for (int r = 0; r < h; ++r)
-        for (int i = 0; i < 5 * P; ++i) {
-          size_t o = (size_t)i * plane + (size_t)(y0 + r) * pitch + x;
-          fout[o] = fin[o];
-        }
-    if (bx == 0 && by == 0 && tx == 0) {
-      const int s2 = (a.slot + 2) % 3;
-      a.ctl->t[s1] = a.ctl->t[a.slot];
-      a.ctl->m1[s1] = a.ctl->m1[a.slot];
-      a.ctl->m2[s1] = a.ctl->m2[a.slot];
-      a.ctl->m1[s2] = 0ull;
-      a.ctl->m2[s2] = 0ull;
-    }
-    return;
-  }
-  if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, sc, a.dx, a.fixed_xi, Sys::MHD);
   const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, om = (R)a.omega, kk = (R)a.k;
   const int set = a.set;
+  auto row_of = [&](int r) -> int { return DIR > 0 ? y0 + r : y0 + h - 1 - r; };
 
   R* rb1 = reinterpret_cast<R*>(smem);   // [3][P][TX]  f*_1 of the row
   R* rb2 = rb1 + 3 * P * TX;             // [3][P][TX]  f*_2 of the row
-  R* ringL = rb2 + 3 * P * TX;           // [P][TY]     f*_1 at x0 - 1
+  R* ringL = rb2 + 3 * P * TX;           // [P][TY]     f*_1 at x0 - 1, by tile row
   R* ringR = ringL + P * TY;             // [P][TY]     f*_2 at x0 + w
 
   // x ring: only the component that streams into the tile, from the x split
@@ -248,84 +238,124 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     }
   }
 
-  R f4prev[P], f3c[P], f4c[P];
+  R fbp[P], f3c[P], fbc[P];
 #pragma unroll
-  for (int i = 0; i < P; ++i) f4prev[i] = f3c[i] = f4c[i] = R(0);
+  for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
   if (act) {
     R o[5][P];
-    const int yb = (y0 - 1 + ny) % ny;
-    collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)yb * pitch + x, xinv, c, om, set, kk, ch, o);
+    const int yb = DIR > 0 ? (y0 - 1 + ny) % ny : (y0 + h) % ny;
+    collide_d2q5<Sys, T, R, MB>(sys, fin, plane, (size_t)yb * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
-    for (int i = 0; i < P; ++i) f4prev[i] = o[3][i];
-    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)y0 * pitch + x, xinv, c, om, set, kk, ch, o);
+    for (int i = 0; i < P; ++i) fbp[i] = o[QB][i];
+    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(0) * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       rb1[i * TX + tx] = o[0][i];
       rb2[i * TX + tx] = o[1][i];
       f3c[i] = o[2][i];
-      f4c[i] = o[3][i];
+      fbc[i] = o[QB][i];
     }
   }
 
-  double m1 = 0.0, m2 = 0.0;
+  R m1 = R(0), m2 = R(0);
   bool bad = false;
   for (int r = 0; r < h; ++r) {
-    const int j = y0 + r;
-    R f5n[P], f3n[P], f4n[P];
+    const int j = row_of(r);
+    R fan[P], f3n[P], fbn[P];
     const int nb = (r + 1) % 3, cb = r % 3;
     if (act) {
       R o[5][P];
       if (r + 1 < h) {
-        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)(j + 1) * pitch + x, xinv, c, om, set, kk, ch, o);
+        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(r + 1) * pitch + x, xinv, c, om, set, kk,
+                                        ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
           rb1[(nb * P + i) * TX + tx] = o[0][i];
           rb2[(nb * P + i) * TX + tx] = o[1][i];
           f3n[i] = o[2][i];
-          f4n[i] = o[3][i];
-          f5n[i] = o[4][i];
+          fbn[i] = o[QB][i];
+          fan[i] = o[QA][i];
         }
       } else {
-        const int yt = (y0 + h) % ny;
-        collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)yt * pitch + x, xinv, c, om, set, kk, ch, o);
+        const int ya = DIR > 0 ? (y0 + h) % ny : (y0 - 1 + ny) % ny;
+        collide_d2q5<Sys, T, R, MA>(sys, fin, plane, (size_t)ya * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-          f5n[i] = o[4][i];
-          f3n[i] = f4n[i] = R(0);
+          fan[i] = o[QA][i];
+          f3n[i] = fbn[i] = R(0);
         }
       }
     }
     __syncthreads();
     if (act) {
       const size_t base = (size_t)j * pitch + x;
+      const int rt = j - y0;
       R U[P];
 #pragma unroll
       for (int i = 0; i < P; ++i) {
-        R g1 = tx == 0 ? ringL[i * TY + r] : rb1[(cb * P + i) * TX + tx - 1];
-        R g2 = tx == w - 1 ? ringR[i * TY + r] : rb2[(cb * P + i) * TX + tx + 1];
-        R g3 = f3c[i], g4 = f4prev[i], g5 = f5n[i];
-        Store<T>::st(fout + (size_t)(0 * P + i) * plane + base, g1);
-        Store<T>::st(fout + (size_t)(1 * P + i) * plane + base, g2);
-        Store<T>::st(fout + (size_t)(2 * P + i) * plane + base, g3);
-        Store<T>::st(fout + (size_t)(3 * P + i) * plane + base, g4);
-        Store<T>::st(fout + (size_t)(4 * P + i) * plane + base, g5);
+        R g[5];
+        g[0] = tx == 0 ? ringL[i * TY + rt] : rb1[(cb * P + i) * TX + tx - 1];
+        g[1] = tx == w - 1 ? ringR[i * TY + rt] : rb2[(cb * P + i) * TX + tx + 1];
+        g[2] = f3c[i];
+        g[QB] = fbp[i];
+        g[QA] = fan[i];
         const T* tp = nullptr;
-        U[i] = round_store(g1, tp) + round_store(g2, tp) + round_store(g3, tp) + round_store(g4, tp) +
-               round_store(g5, tp);
+        R acc = R(0);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          Store<T>::st(fout + (size_t)(q * P + i) * plane + base, g[q]);
+          acc += round_store(g[q], tp);
+        }
+        U[i] = acc;
       }
       R e1, e2;
       bad |= !sys.epilogue(U, e1, e2);
-      m1 = fmax(m1, (double)e1);
-      m2 = fmax(m2, (double)e2);
+      m1 = vmax(m1, e1);
+      m2 = vmax(m2, e2);
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-      f4prev[i] = f4c[i];
+      fbp[i] = fbc[i];
       f3c[i] = f3n[i];
-      f4c[i] = f4n[i];
+      fbc[i] = fbn[i];
     }
   }
-  commit_max(m1, m2, bad, a.ctl, s1);
+  commit_max((double)m1, (double)m2, bad, a.ctl, s1);
+}
+
+template <class Sys, class T, class R>
+__device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by, int TX, int TY,
+                                            unsigned char* smem) {
+  constexpr int P = Sys::P;
+  const int tx = threadIdx.x;
+  const int x0 = bx * TX, y0 = by * TY;
+  const StepScalars sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+  if (sc.done) {
+    // t_end already reached: this launch is a no-op that keeps the ping-pong
+    // consistent (f^{n+1} = f^n, same control words).
+    const int w = min(TX, a.nx - x0), h = min(TY, a.ny - y0);
+    const size_t plane = (size_t)a.pitch * a.ny;
+    if (tx < w)
+      for (int r = 0; r < h; ++r)
+        for (int i = 0; i < 5 * P; ++i) {
+          size_t o = (size_t)i * plane + (size_t)(y0 + r) * a.pitch + x0 + tx;
+          a.f[a.parity ^ 1][o] = a.f[a.parity][o];
+        }
+    if (bx == 0 && by == 0 && tx == 0) {
+      const int s1 = (a.slot + 1) % 3, s2 = (a.slot + 2) % 3;
+      a.ctl->t[s1] = a.ctl->t[a.slot];
+      a.ctl->m1[s1] = a.ctl->m1[a.slot];
+      a.ctl->m2[s1] = a.ctl->m2[a.slot];
+      a.ctl->m1[s2] = 0ull;
+      a.ctl->m2[s2] = 0ull;
+    }
+    return;
+  }
+  if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, sc, a.dx, a.fixed_xi, Sys::MHD);
+  if (by & 1)
+    step2d_tile_dir<Sys, T, R, -1>(a, sc, bx, by, TX, TY, smem);
+  else
+    step2d_tile_dir<Sys, T, R, +1>(a, sc, bx, by, TX, TY, smem);
 }
 
 // ------------------------------------------------- D2Q5 step, bulk-copy rows
@@ -554,7 +584,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     issued = min(2 + D, nrows);
   }
 
-  double m1 = 0.0, m2 = 0.0;
+  R m1 = R(0), m2 = R(0);
   bool bad = false;
   for (int r = 0; r < h && !aborted; ++r) {
     const int j = r + 2;                 // stream row computed now (tile row r+1 or the top ring)
@@ -627,8 +657,8 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
       }
       R e1, e2;
       bad |= !sys.epilogue(U, e1, e2);
-      m1 = fmax(m1, (double)e1);
-      m2 = fmax(m2, (double)e2);
+      m1 = vmax(m1, e1);
+      m2 = vmax(m2, e2);
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -646,7 +676,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     __syncthreads();
     return;
   }
-  commit_max(m1, m2, bad, a.ctl, s1);
+  commit_max((double)m1, (double)m2, bad, a.ctl, s1);
 }
 
 template <class Sys, class T, class R>
