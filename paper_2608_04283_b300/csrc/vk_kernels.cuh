@@ -185,20 +185,19 @@ __device__ __forceinline__ void step_bookkeeping(Ctl* ctl, int slot, const StepS
 }
 
 // ------------------------------------------------------------------ D2Q5 step
-// March over the rows of one tile in direction DIR (+1 up, -1 down).  Tiles of
+// March over the rows of one tile, up or down.  Tiles of
 // even row index march up and odd ones down, so the two tiles that share a
 // boundary read the boundary rows (their own and the ring) at the same time,
 // the second read then hitting L2.  Going up, f^{n+1}_4(y) = f*_4(y - 1) comes
 // from the previous row and f^{n+1}_5(y) = f*_5(y + 1) from the next one; going
 // down the two roles swap.
-template <class Sys, class T, class R, int DIR>
+template <class Sys, class T, class R>
 __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const StepScalars& sc, int bx, int by,
                                                 int TX, int TY, unsigned char* smem) {
   constexpr int P = Sys::P;
-  constexpr int QB = DIR > 0 ? 3 : 4;            // component carried from the previous row
-  constexpr int QA = DIR > 0 ? 4 : 3;            // component taken from the next row
-  constexpr int MB = DIR > 0 ? C_Q4 : C_Q5;      // ring row behind the march
-  constexpr int MA = DIR > 0 ? C_Q5 : C_Q4;      // ring row ahead of the march
+  // one body for both directions (a second inlined copy of the larger systems'
+  // arithmetic costs more in instruction-cache misses than the selects below)
+  const bool up = (by & 1) == 0;
   const Sys sys = make_sys<Sys>(a.sp);
   const int tx = threadIdx.x;
   const int x0 = bx * TX, y0 = by * TY;
@@ -213,7 +212,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
   const int s1 = (a.slot + 1) % 3;
   const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, om = (R)a.omega, kk = (R)a.k;
   const int set = a.set;
-  auto row_of = [&](int r) -> int { return DIR > 0 ? y0 + r : y0 + h - 1 - r; };
+  auto row_of = [&](int r) -> int { return up ? y0 + r : y0 + h - 1 - r; };
 
   R* rb1 = reinterpret_cast<R*>(smem);   // [3][P][TX]  f*_1 of the row
   R* rb2 = rb1 + 3 * P * TX;             // [3][P][TX]  f*_2 of the row
@@ -243,17 +242,24 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
   for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
   if (act) {
     R o[5][P];
-    const int yb = DIR > 0 ? (y0 - 1 + ny) % ny : (y0 + h) % ny;
-    collide_d2q5<Sys, T, R, MB>(sys, fin, plane, (size_t)yb * pitch + x, xinv, c, om, set, kk, ch, o);
+    if (up) {
+      collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)((y0 - 1 + ny) % ny) * pitch + x, xinv, c, om, set, kk,
+                                    ch, o);
 #pragma unroll
-    for (int i = 0; i < P; ++i) fbp[i] = o[QB][i];
+      for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
+    } else {
+      collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)((y0 + h) % ny) * pitch + x, xinv, c, om, set, kk, ch,
+                                    o);
+#pragma unroll
+      for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
+    }
     collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(0) * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       rb1[i * TX + tx] = o[0][i];
       rb2[i * TX + tx] = o[1][i];
       f3c[i] = o[2][i];
-      fbc[i] = o[QB][i];
+      fbc[i] = up ? o[3][i] : o[4][i];
     }
   }
 
@@ -273,17 +279,23 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
           rb1[(nb * P + i) * TX + tx] = o[0][i];
           rb2[(nb * P + i) * TX + tx] = o[1][i];
           f3n[i] = o[2][i];
-          fbn[i] = o[QB][i];
-          fan[i] = o[QA][i];
+          fbn[i] = up ? o[3][i] : o[4][i];
+          fan[i] = up ? o[4][i] : o[3][i];
         }
       } else {
-        const int ya = DIR > 0 ? (y0 + h) % ny : (y0 - 1 + ny) % ny;
-        collide_d2q5<Sys, T, R, MA>(sys, fin, plane, (size_t)ya * pitch + x, xinv, c, om, set, kk, ch, o);
+        if (up) {
+          collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)((y0 + h) % ny) * pitch + x, xinv, c, om, set, kk,
+                                        ch, o);
 #pragma unroll
-        for (int i = 0; i < P; ++i) {
-          fan[i] = o[QA][i];
-          f3n[i] = fbn[i] = R(0);
+          for (int i = 0; i < P; ++i) fan[i] = o[4][i];
+        } else {
+          collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)((y0 - 1 + ny) % ny) * pitch + x, xinv, c, om, set,
+                                        kk, ch, o);
+#pragma unroll
+          for (int i = 0; i < P; ++i) fan[i] = o[3][i];
         }
+#pragma unroll
+        for (int i = 0; i < P; ++i) f3n[i] = fbn[i] = R(0);
       }
     }
     __syncthreads();
@@ -297,8 +309,8 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
         g[0] = tx == 0 ? ringL[i * TY + rt] : rb1[(cb * P + i) * TX + tx - 1];
         g[1] = tx == w - 1 ? ringR[i * TY + rt] : rb2[(cb * P + i) * TX + tx + 1];
         g[2] = f3c[i];
-        g[QB] = fbp[i];
-        g[QA] = fan[i];
+        g[3] = up ? fbp[i] : fan[i];
+        g[4] = up ? fan[i] : fbp[i];
         const T* tp = nullptr;
         R acc = R(0);
 #pragma unroll
@@ -352,10 +364,7 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     return;
   }
   if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, sc, a.dx, a.fixed_xi, Sys::MHD);
-  if (by & 1)
-    step2d_tile_dir<Sys, T, R, -1>(a, sc, bx, by, TX, TY, smem);
-  else
-    step2d_tile_dir<Sys, T, R, +1>(a, sc, bx, by, TX, TY, smem);
+  step2d_tile_dir<Sys, T, R>(a, sc, bx, by, TX, TY, smem);
 }
 
 // ------------------------------------------------- D2Q5 step, bulk-copy rows
