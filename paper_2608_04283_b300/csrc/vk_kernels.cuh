@@ -191,13 +191,15 @@ __device__ __forceinline__ void step_bookkeeping(Ctl* ctl, int slot, const StepS
 // the second read then hitting L2.  Going up, f^{n+1}_4(y) = f*_4(y - 1) comes
 // from the previous row and f^{n+1}_5(y) = f*_5(y + 1) from the next one; going
 // down the two roles swap.
-template <class Sys, class T, class R>
+// DIR = +1 / -1 fixes the direction at compile time (two bodies, used for the
+// small systems); DIR = 0 picks it at run time in one body (MHD-GLM, whose
+// arithmetic is large enough that a second copy costs more in instruction-cache
+// misses than the register selects).
+template <class Sys, class T, class R, int DIR>
 __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const StepScalars& sc, int bx, int by,
                                                 int TX, int TY, unsigned char* smem) {
   constexpr int P = Sys::P;
-  // one body for both directions (a second inlined copy of the larger systems'
-  // arithmetic costs more in instruction-cache misses than the selects below)
-  const bool up = (by & 1) == 0;
+  const bool up = DIR > 0 ? true : (DIR < 0 ? false : (by & 1) == 0);
   const Sys sys = make_sys<Sys>(a.sp);
   const int tx = threadIdx.x;
   const int x0 = bx * TX, y0 = by * TY;
@@ -364,7 +366,14 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     return;
   }
   if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, sc, a.dx, a.fixed_xi, Sys::MHD);
-  step2d_tile_dir<Sys, T, R>(a, sc, bx, by, TX, TY, smem);
+  if constexpr (Sys::P <= 4) {
+    if (by & 1)
+      step2d_tile_dir<Sys, T, R, -1>(a, sc, bx, by, TX, TY, smem);
+    else
+      step2d_tile_dir<Sys, T, R, +1>(a, sc, bx, by, TX, TY, smem);
+  } else {
+    step2d_tile_dir<Sys, T, R, 0>(a, sc, bx, by, TX, TY, smem);
+  }
 }
 
 // ------------------------------------------------- D2Q5 step, bulk-copy rows
