@@ -52,7 +52,8 @@ typedef enum {
   VKLB_ERR_CFL = -5,          /* fixed lattice speed below max |lambda| (Eq. 28 violated) */
   VKLB_ERR_TIMEOUT = -6,      /* reserved: a bounded device wait gave up */
   VKLB_ERR_STATE = -7,        /* call out of order (e.g. stepping before vklb_set_state) */
-  VKLB_ERR_UNSUPPORTED = -8   /* combination not built (e.g. D1Q3 with MHD-GLM) */
+  VKLB_ERR_UNSUPPORTED = -8,  /* combination not built (e.g. D1Q3 with MHD-GLM) */
+  VKLB_ERR_LIMIT = -9         /* beyond the fixed scratch of vklb_conservation_totals_noalloc */
 } vklb_status;
 
 /* Hyperbolic system (Sec. 2.1).  gamma: ideal-gas index (Euler, MHD-GLM);
@@ -202,6 +203,25 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out);
 int vklb_batch_set_tiling(vklb_batch* b, int32_t tile_x, int32_t tile_y);
 int vklb_batch_step(vklb_batch* b, int64_t n, int32_t use_graph);
 int vklb_batch_destroy(vklb_batch* b);
+
+/* Conservation totals that allocate nothing (the paper has no counterpart: this
+ * serves callers that cannot call cudaMalloc, e.g. code that only receives
+ * device pointers from another runtime or runs where allocation is forbidden).
+ * f_dev: a distribution buffer in the layout of vklb_device_state, store type
+ * of `precision`, q in {3, 5}, p <= 16 fields (else VKLB_ERR_LIMIT), nx x ny
+ * cells with row pitch `pitch` >= nx.  totals[k] = cell_volume * sum_x sum_q f,
+ * FP64, same reduction order as vklb_conservation_totals; `totals` is a host
+ * pointer (the call synchronises the stream) or, with totals_on_device != 0, a
+ * device pointer (the call returns after enqueueing).  The partial sums live in
+ * one file-scope device array of 16 x 296 + 16 doubles (38 KB) that every GPU
+ * loading the library keeps until the process exits; every slot a call reads is
+ * written earlier in the same call, so nothing needs clearing, but calls that
+ * overlap on the GPU (other streams, other host threads) race on that array.
+ * The first call on a device resolves the array's address (cudaGetSymbolAddress)
+ * and should come before any stream capture.  No cudaMalloc or cudaFree. */
+int vklb_conservation_totals_noalloc(const void* f_dev, int32_t precision, int32_t q, int32_t p, int64_t nx,
+                                     int64_t ny, int64_t pitch, double cell_volume, double* totals,
+                                     int32_t totals_on_device, void* cuda_stream);
 
 /* Number of kernel launches this process has enqueued through the library. */
 int64_t vklb_launch_count(void);

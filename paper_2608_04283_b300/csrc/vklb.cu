@@ -6,6 +6,7 @@
 // synchronises except those documented as synchronising.
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -352,6 +353,7 @@ const char* vklb_strerror(int status) {
     case VKLB_ERR_TIMEOUT: return "bounded device wait gave up";
     case VKLB_ERR_STATE: return "call out of order";
     case VKLB_ERR_UNSUPPORTED: return "unsupported combination";
+    case VKLB_ERR_LIMIT: return "request exceeds the fixed limits of the allocation-free entry point";
   }
   return "unknown status";
 }
@@ -729,6 +731,103 @@ int vklb_batch_destroy(vklb_batch* b) {
   if (b->own) cudaStreamDestroy(b->own);
   delete b;
   return VKLB_OK;
+}
+
+// ------------------------------------------------- allocation-free totals
+// For callers that cannot allocate device memory themselves (for example a host
+// process that only receives device pointers from another runtime, or code
+// running where cudaMalloc is not permitted), conservation totals of a
+// distribution buffer they own, with the partial sums kept in this file-scope
+// device array instead of a cudaMalloc'd buffer.  Every GPU that loads the
+// library holds the array until the process exits.
+}  // extern "C"
+
+namespace {
+constexpr int kNoAllocMaxFields = 16;   // fields a call may reduce
+constexpr int kNoAllocBlocks = kRedBlocks;
+// [field][block] partial sums, then kNoAllocMaxFields final sums
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxFields * kNoAllocBlocks + kNoAllocMaxFields];
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Pass 1 with p and q given at run time: block b sums its fixed chunk of cells
+// per field in FP64 (same order as totals_pass1), writing part[s * gridDim.x + b].
+template <class T>
+__global__ void totals_pass1_rt(const T* __restrict__ f, int p, int q, int nx, int ny, int pitch,
+                                double* __restrict__ part) {
+  __shared__ double red[32];
+  const size_t cells = (size_t)nx * ny, plane = (size_t)pitch * ny;
+  const size_t chunk = (cells + gridDim.x - 1) / gridDim.x;
+  const size_t lo = blockIdx.x * chunk, hi = min(cells, lo + chunk);
+  for (int s = 0; s < p; ++s) {
+    double acc = 0.0;
+    for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const size_t y = i / nx, x = i - y * nx;
+      const size_t o = y * pitch + x;
+      for (int k = 0; k < q; ++k) acc += (double)Store<T>::ld(f + (size_t)(k * p + s) * plane + o);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+      part[(size_t)s * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+int noalloc_launch(const void* f, int p, int q, int nx, int ny, int pitch, double vol, double* scratch, double* out,
+                   cudaStream_t st) {
+  totals_pass1_rt<T><<<kNoAllocBlocks, 256, 0, st>>>((const T*)f, p, q, nx, ny, pitch, scratch);
+  totals_pass2<<<1, 32, 0, st>>>(scratch, kNoAllocBlocks, p, vol, out);
+  g_launches += 2;
+  return cuda_status(cudaGetLastError());
+}
+}  // namespace
+
+extern "C" {
+
+int vklb_conservation_totals_noalloc(const void* f_dev, int32_t precision, int32_t q, int32_t p, int64_t nx,
+                                     int64_t ny, int64_t pitch, double cell_volume, double* totals,
+                                     int32_t totals_on_device, void* cuda_stream) {
+  if (!f_dev || !totals) return VKLB_ERR_ARG;
+  if (precision < VKLB_FP64 || precision > VKLB_BF16_STORE || (q != 3 && q != 5)) return VKLB_ERR_ARG;
+  if (nx < 1 || ny < 1 || pitch < nx || nx > (1 << 30) || ny > (1 << 30) || pitch > (1 << 30)) return VKLB_ERR_ARG;
+  if (p < 1 || p > kNoAllocMaxFields) return VKLB_ERR_LIMIT;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VKLB_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return VKLB_ERR_LIMIT;
+  double* scratch = nullptr;
+  {
+    // first call on this device: resolve the device address of the array
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return VKLB_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = (double*)ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* out = totals_on_device ? totals : scratch + (size_t)kNoAllocMaxFields * kNoAllocBlocks;
+  int rc;
+  if (precision == VKLB_FP64)
+    rc = noalloc_launch<double>(f_dev, p, q, (int)nx, (int)ny, (int)pitch, cell_volume, scratch, out, st);
+  else if (precision == VKLB_FP32)
+    rc = noalloc_launch<float>(f_dev, p, q, (int)nx, (int)ny, (int)pitch, cell_volume, scratch, out, st);
+  else
+    rc = noalloc_launch<__nv_bfloat16>(f_dev, p, q, (int)nx, (int)ny, (int)pitch, cell_volume, scratch, out, st);
+  if (rc) return rc;
+  if (totals_on_device) return VKLB_OK;
+  if ((rc = cuda_status(cudaMemcpyAsync(totals, out, sizeof(double) * p, cudaMemcpyDeviceToHost, st)))) return rc;
+  return cuda_status(cudaStreamSynchronize(st));
 }
 
 }  // extern "C"

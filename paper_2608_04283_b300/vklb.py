@@ -19,8 +19,8 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------ constants
-OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_NONPHYSICAL, ERR_CFL, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8
+OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_NONPHYSICAL, ERR_CFL, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED, ERR_LIMIT = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 ADVECT, SWE, EULER, MHD_GLM = 0, 1, 2, 3
 D1Q3, D2Q5 = 13, 25
 BC_PERIODIC, BC_CHARACTERISTIC = 0, 1
