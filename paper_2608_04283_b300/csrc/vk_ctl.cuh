@@ -22,6 +22,7 @@ enum : int { ERR_NONPHYS = 1, ERR_CFL = 2, ERR_TIMEOUT = 4 };
 
 struct StepScalars {
   double xi;   // lattice speed of this step
+  double xinv; // 1 / xi
   double ch;   // cleaning speed of this step (MHD-GLM)
   bool done;   // t_end reached: nothing to do
 };
@@ -48,6 +49,7 @@ VK_HD StepScalars step_scalars(const Ctl* ctl, int slot, bool mhd, double ch_fac
       s.xi = m * dx / rem;
     }
   }
+  s.xinv = 1.0 / s.xi;
   return s;
 }
 

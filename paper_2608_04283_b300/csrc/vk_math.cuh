@@ -97,7 +97,7 @@ VK_HD R alpha_w(R lam, R k_over_lmax, int set) {
 template <class R>
 VK_HD R one_minus_exp_over(R y) {
   if (y < R(1e-3)) return R(1) - y * (R(0.5) - y * (R(1) / R(6) - y * R(1) / R(24)));
-  return (R(1) - vexp(-y)) / y;
+  return vdiv(R(1) - vexp(-y), y);
 }
 
 // Divided difference (alpha(l1) - alpha(l2)) / (l1 - l2) of the weights.  For the
@@ -107,7 +107,11 @@ VK_HD R one_minus_exp_over(R y) {
 template <class R>
 VK_HD R alpha_dd(R a1, R l1, R a2, R l2, R k_over_lmax, R lmax, int set) {
   if (set == SET_WEIGHTED) {
-    R y = k_over_lmax * (l1 - l2);
+    const R dl = l1 - l2;
+    // well separated speeds: the plain quotient loses no more than a few ulp
+    // relative to alpha's own rounding
+    if (vabs(dl) > R(0.05) * lmax) return (a1 - a2) * vrcp(dl);
+    R y = k_over_lmax * dl;
     if (y >= R(0)) return a1 * (R(1) - a2) * k_over_lmax * one_minus_exp_over(y);
     return a2 * (R(1) - a1) * k_over_lmax * one_minus_exp_over(-y);
   }

@@ -305,14 +305,15 @@ VK_HD void mhd_norm(T a2, T bx2, T bt2, T& af, T& as, T& d) {
   T X, Y;
   if (a2 >= b2) {
     X = T(0.5) * ((a2 - b2) + d);
-    Y = X > T(0) ? a2 * bt2 / X : T(0);
+    Y = X > T(0) ? a2 * bt2 * vrcp(X) : T(0);
   } else {
     Y = T(0.5) * ((b2 - a2) + d);
-    X = Y > T(0) ? a2 * bt2 / Y : T(0);
+    X = Y > T(0) ? a2 * bt2 * vrcp(Y) : T(0);
   }
   if (d > T(0)) {
-    af = vsqrt(vmax(X / d, T(0)));
-    as = vsqrt(vmax(Y / d, T(0)));
+    const T id = vrcp(d);
+    af = vsqrt(vmax(X * id, T(0)));
+    as = vsqrt(vmax(Y * id, T(0)));
   } else {
     af = as = T(0.70710678118654752440);
   }
@@ -428,7 +429,7 @@ struct MHDGLM {
     }
     const R cf2 = R(0.5) * (a2 + bx2 + btt + dcs);
     const R cf = vsqrt(cf2);
-    const R cs = cf2 > R(0) ? vsqrt(a2 * bx2 / cf2) : R(0);
+    const R cs = cf2 > R(0) ? vsqrt(a2 * bx2 * vrcp(cf2)) : R(0);
     const R ca = vsqrt(bx2);
     const R a = vsqrt(a2);
     const R sr = vsqrt(rho);
