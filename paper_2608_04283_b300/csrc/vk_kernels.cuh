@@ -67,16 +67,31 @@ enum CollideMode { C_FULL = 0, C_Q1 = 1, C_Q2 = 2, C_Q4 = 3, C_Q5 = 4 };
 // Collision (Eq. 42) of one D2Q5 cell with the weighted equilibria of Eq. (41):
 //   f1 = c U + F(1,+)/xi, f2 = c U - F(1,-)/xi, f4 = c U + F(2,+)/xi,
 //   f5 = c U - F(2,-)/xi, f3 = U - (f1 + f2 + f4 + f5) (= Eq. 41's rest term).
-template <class Sys, class T, class R, int MODE>
-__device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict__ fin, size_t plane,
-                                             size_t idx, R xinv, R c, R om, int set, R k, R ch,
-                                             R (&out)[5][Sys::P]) {
-  constexpr int P = Sys::P;
-  R f[5][P];
+template <class T, class R, int P>
+__device__ __forceinline__ void load_d2q5(const T* __restrict__ fin, size_t plane, size_t idx, R (&f)[5][P]) {
 #pragma unroll
   for (int q = 0; q < 5; ++q)
 #pragma unroll
     for (int i = 0; i < P; ++i) f[q][i] = Store<T>::ld(fin + (size_t)(q * P + i) * plane + idx);
+}
+
+template <class Sys, class R, int MODE>
+__device__ __forceinline__ void collide_regs(const Sys& sys, const R (&f)[5][Sys::P], R xinv, R c, R om, int set,
+                                             R k, R ch, R (&out)[5][Sys::P]);
+
+template <class Sys, class T, class R, int MODE>
+__device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict__ fin, size_t plane,
+                                             size_t idx, R xinv, R c, R om, int set, R k, R ch,
+                                             R (&out)[5][Sys::P]) {
+  R f[5][Sys::P];
+  load_d2q5<T, R, Sys::P>(fin, plane, idx, f);
+  collide_regs<Sys, R, MODE>(sys, f, xinv, c, om, set, k, ch, out);
+}
+
+template <class Sys, class R, int MODE>
+__device__ __forceinline__ void collide_regs(const Sys& sys, const R (&f)[5][Sys::P], R xinv, R c, R om, int set,
+                                             R k, R ch, R (&out)[5][Sys::P]) {
+  constexpr int P = Sys::P;
   R U[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
@@ -138,10 +153,17 @@ __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
-// Block-wide max of (a, b) and OR of bad; thread 0 commits them to slot s1.
-__device__ __forceinline__ void commit_max(double a, double b, bool bad, Ctl* ctl, int s1) {
-  __shared__ double red[2][32];
+// Block-wide max of (a, b) and OR of bad (in the compute type); thread 0
+// commits them to slot s1 as doubles.
+template <class R>
+__device__ __forceinline__ void commit_max(R a, R b, bool bad, Ctl* ctl, int s1) {
+  __shared__ R red[2][32];
   __shared__ int sbad;
   if (threadIdx.x == 0) sbad = 0;
   __syncthreads();
@@ -155,13 +177,13 @@ __device__ __forceinline__ void commit_max(double a, double b, bool bad, Ctl* ct
   }
   __syncthreads();
   if (wid == 0) {
-    a = lane < nw ? red[0][lane] : 0.0;
-    b = lane < nw ? red[1][lane] : 0.0;
+    a = lane < nw ? red[0][lane] : R(0);
+    b = lane < nw ? red[1][lane] : R(0);
     a = warp_max(a);
     b = warp_max(b);
     if (lane == 0) {
-      atomicMax(&ctl->m1[s1], double_to_bits(a));
-      atomicMax(&ctl->m2[s1], double_to_bits(b));
+      atomicMax(&ctl->m1[s1], double_to_bits((double)a));
+      atomicMax(&ctl->m2[s1], double_to_bits((double)b));
       if (sbad) atomicOr(&ctl->err, ERR_NONPHYS);
     }
   }
@@ -239,23 +261,56 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
     }
   }
 
+  // Rows in march order: k = 0 the ring row behind, k = 1..h the tile rows,
+  // k = h + 1 the ring row ahead.  For the small systems the loads of row k + 1
+  // are issued before row k is collided (two rows in flight per thread).
+  constexpr bool PREF = Sys::P <= 4;
+  auto seq_idx = [&](int k) -> size_t {
+    int yy;
+    if (k == 0)
+      yy = up ? (y0 - 1 + ny) % ny : (y0 + h) % ny;
+    else if (k == h + 1)
+      yy = up ? (y0 + h) % ny : (y0 - 1 + ny) % ny;
+    else
+      yy = row_of(k - 1);
+    return (size_t)yy * pitch + x;
+  };
+  R fA[5][P], fB[5][P];
+  if (PREF && act) {
+    load_d2q5<T, R, P>(fin, plane, seq_idx(0), fA);
+    load_d2q5<T, R, P>(fin, plane, seq_idx(1), fB);
+  }
+
   R fbp[P], f3c[P], fbc[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
   if (act) {
     R o[5][P];
     if (up) {
-      collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)((y0 - 1 + ny) % ny) * pitch + x, xinv, c, om, set, kk,
-                                    ch, o);
+      if (PREF)
+        collide_regs<Sys, R, C_Q4>(sys, fA, xinv, c, om, set, kk, ch, o);
+      else
+        collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, seq_idx(0), xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
     } else {
-      collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)((y0 + h) % ny) * pitch + x, xinv, c, om, set, kk, ch,
-                                    o);
+      if (PREF)
+        collide_regs<Sys, R, C_Q5>(sys, fA, xinv, c, om, set, kk, ch, o);
+      else
+        collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, seq_idx(0), xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
     }
-    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(0) * pitch + x, xinv, c, om, set, kk, ch, o);
+    if (PREF) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int i = 0; i < P; ++i) fA[q][i] = fB[q][i];
+      load_d2q5<T, R, P>(fin, plane, seq_idx(2), fB);
+      collide_regs<Sys, R, C_FULL>(sys, fA, xinv, c, om, set, kk, ch, o);
+    } else {
+      collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, seq_idx(1), xinv, c, om, set, kk, ch, o);
+    }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       rb1[i * TX + tx] = o[0][i];
@@ -272,10 +327,19 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
     R fan[P], f3n[P], fbn[P];
     const int nb = (r + 1) % 3, cb = r % 3;
     if (act) {
+      if (PREF) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+          for (int i = 0; i < P; ++i) fA[q][i] = fB[q][i];
+        if (r + 3 <= h + 1) load_d2q5<T, R, P>(fin, plane, seq_idx(r + 3), fB);
+      }
       R o[5][P];
       if (r + 1 < h) {
-        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(r + 1) * pitch + x, xinv, c, om, set, kk,
-                                        ch, o);
+        if (PREF)
+          collide_regs<Sys, R, C_FULL>(sys, fA, xinv, c, om, set, kk, ch, o);
+        else
+          collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, seq_idx(r + 2), xinv, c, om, set, kk, ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
           rb1[(nb * P + i) * TX + tx] = o[0][i];
@@ -286,13 +350,17 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
         }
       } else {
         if (up) {
-          collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)((y0 + h) % ny) * pitch + x, xinv, c, om, set, kk,
-                                        ch, o);
+          if (PREF)
+            collide_regs<Sys, R, C_Q5>(sys, fA, xinv, c, om, set, kk, ch, o);
+          else
+            collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, seq_idx(h + 1), xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[4][i];
         } else {
-          collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)((y0 - 1 + ny) % ny) * pitch + x, xinv, c, om, set,
-                                        kk, ch, o);
+          if (PREF)
+            collide_regs<Sys, R, C_Q4>(sys, fA, xinv, c, om, set, kk, ch, o);
+          else
+            collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, seq_idx(h + 1), xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[3][i];
         }
@@ -334,7 +402,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
       fbc[i] = fbn[i];
     }
   }
-  commit_max((double)m1, (double)m2, bad, a.ctl, s1);
+  commit_max<R>(m1, m2, bad, a.ctl, s1);
 }
 
 template <class Sys, class T, class R>
@@ -702,7 +770,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     __syncthreads();
     return;
   }
-  commit_max((double)m1, (double)m2, bad, a.ctl, s1);
+  commit_max<R>(m1, m2, bad, a.ctl, s1);
 }
 
 template <class Sys, class T, class R>
@@ -901,7 +969,7 @@ __global__ void init_max_kernel(const double* __restrict__ U, size_t cells, SysP
     }
     bad |= !sys.physical(u);
   }
-  commit_max(m1, m2, bad, ctl, 0);
+  commit_max<double>(m1, m2, bad, ctl, 0);
 }
 
 // f_q = f_q^eq(U) (Eq. 2b) with xi_0, c_h^0 from slot 0.  U is dense [p][ny][nx];
