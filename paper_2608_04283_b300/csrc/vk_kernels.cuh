@@ -67,31 +67,16 @@ enum CollideMode { C_FULL = 0, C_Q1 = 1, C_Q2 = 2, C_Q4 = 3, C_Q5 = 4 };
 // Collision (Eq. 42) of one D2Q5 cell with the weighted equilibria of Eq. (41):
 //   f1 = c U + F(1,+)/xi, f2 = c U - F(1,-)/xi, f4 = c U + F(2,+)/xi,
 //   f5 = c U - F(2,-)/xi, f3 = U - (f1 + f2 + f4 + f5) (= Eq. 41's rest term).
-template <class T, class R, int P>
-__device__ __forceinline__ void load_d2q5(const T* __restrict__ fin, size_t plane, size_t idx, R (&f)[5][P]) {
-#pragma unroll
-  for (int q = 0; q < 5; ++q)
-#pragma unroll
-    for (int i = 0; i < P; ++i) f[q][i] = Store<T>::ld(fin + (size_t)(q * P + i) * plane + idx);
-}
-
-template <class Sys, class R, int MODE>
-__device__ __forceinline__ void collide_regs(const Sys& sys, const R (&f)[5][Sys::P], R xinv, R c, R om, int set,
-                                             R k, R ch, R (&out)[5][Sys::P]);
-
 template <class Sys, class T, class R, int MODE>
 __device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict__ fin, size_t plane,
                                              size_t idx, R xinv, R c, R om, int set, R k, R ch,
                                              R (&out)[5][Sys::P]) {
-  R f[5][Sys::P];
-  load_d2q5<T, R, Sys::P>(fin, plane, idx, f);
-  collide_regs<Sys, R, MODE>(sys, f, xinv, c, om, set, k, ch, out);
-}
-
-template <class Sys, class R, int MODE>
-__device__ __forceinline__ void collide_regs(const Sys& sys, const R (&f)[5][Sys::P], R xinv, R c, R om, int set,
-                                             R k, R ch, R (&out)[5][Sys::P]) {
   constexpr int P = Sys::P;
+  R f[5][P];
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int i = 0; i < P; ++i) f[q][i] = Store<T>::ld(fin + (size_t)(q * P + i) * plane + idx);
   R U[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
@@ -261,56 +246,23 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
     }
   }
 
-  // Rows in march order: k = 0 the ring row behind, k = 1..h the tile rows,
-  // k = h + 1 the ring row ahead.  For the small systems the loads of row k + 1
-  // are issued before row k is collided (two rows in flight per thread).
-  constexpr bool PREF = Sys::P <= 4;
-  auto seq_idx = [&](int k) -> size_t {
-    int yy;
-    if (k == 0)
-      yy = up ? (y0 - 1 + ny) % ny : (y0 + h) % ny;
-    else if (k == h + 1)
-      yy = up ? (y0 + h) % ny : (y0 - 1 + ny) % ny;
-    else
-      yy = row_of(k - 1);
-    return (size_t)yy * pitch + x;
-  };
-  R fA[5][P], fB[5][P];
-  if (PREF && act) {
-    load_d2q5<T, R, P>(fin, plane, seq_idx(0), fA);
-    load_d2q5<T, R, P>(fin, plane, seq_idx(1), fB);
-  }
-
   R fbp[P], f3c[P], fbc[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
   if (act) {
     R o[5][P];
     if (up) {
-      if (PREF)
-        collide_regs<Sys, R, C_Q4>(sys, fA, xinv, c, om, set, kk, ch, o);
-      else
-        collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, seq_idx(0), xinv, c, om, set, kk, ch, o);
+      collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)((y0 - 1 + ny) % ny) * pitch + x, xinv, c, om, set, kk,
+                                    ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
     } else {
-      if (PREF)
-        collide_regs<Sys, R, C_Q5>(sys, fA, xinv, c, om, set, kk, ch, o);
-      else
-        collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, seq_idx(0), xinv, c, om, set, kk, ch, o);
+      collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)((y0 + h) % ny) * pitch + x, xinv, c, om, set, kk, ch,
+                                    o);
 #pragma unroll
       for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
     }
-    if (PREF) {
-#pragma unroll
-      for (int q = 0; q < 5; ++q)
-#pragma unroll
-        for (int i = 0; i < P; ++i) fA[q][i] = fB[q][i];
-      load_d2q5<T, R, P>(fin, plane, seq_idx(2), fB);
-      collide_regs<Sys, R, C_FULL>(sys, fA, xinv, c, om, set, kk, ch, o);
-    } else {
-      collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, seq_idx(1), xinv, c, om, set, kk, ch, o);
-    }
+    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(0) * pitch + x, xinv, c, om, set, kk, ch, o);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       rb1[i * TX + tx] = o[0][i];
@@ -327,19 +279,10 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
     R fan[P], f3n[P], fbn[P];
     const int nb = (r + 1) % 3, cb = r % 3;
     if (act) {
-      if (PREF) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q)
-#pragma unroll
-          for (int i = 0; i < P; ++i) fA[q][i] = fB[q][i];
-        if (r + 3 <= h + 1) load_d2q5<T, R, P>(fin, plane, seq_idx(r + 3), fB);
-      }
       R o[5][P];
       if (r + 1 < h) {
-        if (PREF)
-          collide_regs<Sys, R, C_FULL>(sys, fA, xinv, c, om, set, kk, ch, o);
-        else
-          collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, seq_idx(r + 2), xinv, c, om, set, kk, ch, o);
+        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(r + 1) * pitch + x, xinv, c, om, set, kk,
+                                        ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
           rb1[(nb * P + i) * TX + tx] = o[0][i];
@@ -350,17 +293,13 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
         }
       } else {
         if (up) {
-          if (PREF)
-            collide_regs<Sys, R, C_Q5>(sys, fA, xinv, c, om, set, kk, ch, o);
-          else
-            collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, seq_idx(h + 1), xinv, c, om, set, kk, ch, o);
+          collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)((y0 + h) % ny) * pitch + x, xinv, c, om, set, kk,
+                                        ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[4][i];
         } else {
-          if (PREF)
-            collide_regs<Sys, R, C_Q4>(sys, fA, xinv, c, om, set, kk, ch, o);
-          else
-            collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, seq_idx(h + 1), xinv, c, om, set, kk, ch, o);
+          collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)((y0 - 1 + ny) % ny) * pitch + x, xinv, c, om, set,
+                                        kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[3][i];
         }
