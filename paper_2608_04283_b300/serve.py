@@ -1,0 +1,201 @@
+"""Continuous-batching server for VKLB simulations (the served form).
+
+Requests (system, grid side, step count, initial data) arrive over time.  The
+server admits them first-in first-out while their device memory fits under an
+HBM budget, keeps every admitted simulation's distributions resident on the
+GPU, and advances all active simulations of one system family together with a
+single batched launch per step (``vklb_batch_step``); the three families run on
+their own CUDA streams, so their work overlaps on the device.  A tick advances
+each family by K steps, K = min(tick_steps, fewest steps any member still
+needs), after which finished simulations are read back and freed and waiting
+requests are admitted into the freed memory.  Every request's result is the
+same as when it is served alone: the batched kernel computes each tile of each
+member independently, with the family's fixed tiling.
+
+All arithmetic runs in libvklb.so; this module only schedules.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs
+from . import vklb
+
+FAMILY = {
+    # system: (Sim keyword arguments, domain side)
+    "swe": (dict(omega=1.0, cfl=0.3, g=9.81), 1.0),
+    "euler": (dict(omega=1.0, cfl=0.3, gamma=1.4), 1.0),
+    "mhd_glm": (dict(omega=1.0, cfl=0.3, gamma=5.0 / 3.0, ch_factor=6.0), 2.0 * np.pi),
+}
+FIELDS = {"swe": 3, "euler": 4, "mhd_glm": 9}
+
+
+def device_bytes(system, n, precision="fp32"):
+    """Device memory one simulation holds: two distribution buffers plus the
+    double staging array used by set_state / moments."""
+    s = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
+    pitch = ((n + 31) // 32) * 32
+    p = FIELDS[system]
+    return 2 * 5 * p * pitch * n * s + p * n * n * 8
+
+
+@dataclass
+class Job:
+    req: inputs.Request
+    sim: object = None
+    left: int = 0
+    t_admit: float = 0.0
+    t_done: float = 0.0
+    result: np.ndarray = None
+    status: str = "queued"
+
+
+@dataclass
+class Report:
+    jobs: list = field(default_factory=list)
+    wall_s: float = 0.0
+
+    def summary(self):
+        done = [j for j in self.jobs if j.status == "done"]
+        lat = np.array([j.t_done - j.req.arrival for j in done]) if done else np.zeros(1)
+        wait = np.array([j.t_admit - j.req.arrival for j in done]) if done else np.zeros(1)
+        lups = sum(j.req.n * j.req.n * j.req.steps for j in done)
+        return {"requests": len(self.jobs), "completed": len(done),
+                "failed": sum(j.status == "failed" for j in self.jobs),
+                "wall_s": self.wall_s, "solves_per_s": len(done) / self.wall_s if self.wall_s > 0 else 0.0,
+                "MLUPS": lups / self.wall_s / 1e6 if self.wall_s > 0 else 0.0,
+                "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                "queue_p50_s": float(np.percentile(wait, 50)), "queue_p99_s": float(np.percentile(wait, 99))}
+
+
+class Server:
+    def __init__(self, budget_bytes=120e9, tick_steps=50, precision="fp32", tiles=None, keep_results=False,
+                 clock=None):
+        import torch
+        self.torch = torch
+        self.budget = float(budget_bytes)
+        self.tick = int(tick_steps)
+        self.precision = precision
+        self.tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (64, 16)}
+        self.keep = keep_results
+        self.streams = {k: torch.cuda.Stream() for k in FAMILY}
+        self.clock = clock or time.perf_counter
+
+    def _make(self, req):
+        kw, side = FAMILY[req.system]
+        sim = vklb.Sim(req.system, (req.n, req.n), (0.0, 0.0), (side, side), precision=self.precision,
+                       stream=self.streams[req.system], **kw)
+        sim.set_tiling(*self.tiles[req.system])
+        U0 = np.ascontiguousarray(inputs.request_initial_state(req))
+        sim.set_state(U0)
+        return sim
+
+    def run(self, requests, realtime=True):
+        """Serve ``requests`` (sorted by arrival).  With realtime, arrivals are
+        honoured against the wall clock from the start; otherwise everything is
+        available at once.  Returns a Report."""
+        t0 = self.clock()
+        now = lambda: self.clock() - t0
+        pending = list(requests)
+        jobs = [Job(req=r, left=r.steps) for r in pending]
+        queue, active = [], {k: [] for k in FAMILY}
+        batches = {}
+        used = 0.0
+        peak = 0.0
+        qi = 0
+        while qi < len(jobs) or queue or any(active.values()):
+            t = now()
+            while qi < len(jobs) and (not realtime or jobs[qi].req.arrival <= t):
+                queue.append(jobs[qi])
+                qi += 1
+            # admission: first in, first out, under the memory budget
+            while queue:
+                j = queue[0]
+                need = device_bytes(j.req.system, j.req.n, self.precision)
+                if used + need > self.budget and any(active.values()):
+                    break
+                queue.pop(0)
+                j.sim = self._make(j.req)
+                j.t_admit = now()
+                j.status = "running"
+                j.need = need
+                used += need
+                peak = max(peak, used)
+                active[j.req.system].append(j)
+            if not any(active.values()):
+                if qi < len(jobs):
+                    time.sleep(max(0.0, min(0.01, jobs[qi].req.arrival - now())))
+                continue
+            # one tick: every family advances together on its own stream; a
+            # family's batch is rebuilt only when its membership changed
+            for fam, js in active.items():
+                if not js:
+                    continue
+                key = tuple(j.req.rid for j in js)
+                if batches.get(fam, (None,))[0] != key:
+                    if fam in batches:
+                        batches[fam][1].close()
+                    batches[fam] = (key, vklb.Batch([j.sim for j in js], tile=self.tiles[fam]))
+                k = min(self.tick, min(j.left for j in js))
+                batches[fam][1].step(k, graph=False)
+                for j in js:
+                    j.left -= k
+            for fam, js in active.items():
+                if not js:
+                    continue
+                self.streams[fam].synchronize()
+                if any(j.left == 0 for j in js) and fam in batches:
+                    batches.pop(fam)[1].close()
+                still = []
+                for j in js:
+                    if j.left > 0:
+                        still.append(j)
+                        continue
+                    try:
+                        U = j.sim.moments()
+                        j.status = "done"
+                        if self.keep:
+                            j.result = U
+                    except vklb.VKLBError:
+                        j.status = "failed"
+                    j.t_done = now()
+                    j.sim.close()
+                    j.sim = None
+                    used -= j.need
+                active[fam] = still
+        for key, b in batches.values():
+            b.close()
+        rep = Report(jobs=jobs, wall_s=now())
+        rep.peak_bytes = peak
+        return rep
+
+
+def serve_alone(req, **kw):
+    """The same request served on its own (a batch of one)."""
+    srv = Server(keep_results=True, **kw)
+    r = inputs.Request(rid=req.rid, arrival=0.0, system=req.system, n=req.n, steps=req.steps, phase=req.phase)
+    rep = srv.run([r], realtime=False)
+    return rep.jobs[0].result
+
+
+def run_plain(requests, precision="fp32", tiles=None):
+    """Baseline: the same requests one at a time, one launch per step each."""
+    import torch
+    tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (64, 16)}
+    t0 = time.perf_counter()
+    for r in requests:
+        kw, side = FAMILY[r.system]
+        sim = vklb.Sim(r.system, (r.n, r.n), (0.0, 0.0), (side, side), precision=precision, **kw)
+        sim.set_tiling(*tiles[r.system])
+        sim.set_state(np.ascontiguousarray(inputs.request_initial_state(r)))
+        sim.step(r.steps)
+        sim.moments()
+        sim.close()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    lups = sum(r.n * r.n * r.steps for r in requests)
+    return {"requests": len(requests), "wall_s": wall, "solves_per_s": len(requests) / wall,
+            "MLUPS": lups / wall / 1e6}

@@ -1,0 +1,40 @@
+"""Served form: continuous batching of mixed SWE / Euler / MHD-GLM requests under
+a memory budget.  Each request's result is the same (bitwise) served alone and
+in the mix; the mix completes every request and reports latency percentiles."""
+import numpy as np
+import pytest
+
+from paper_2608_04283_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def srv_mod():
+    from paper_2608_04283_b300 import build
+    build.build()
+    from paper_2608_04283_b300 import serve
+    return serve
+
+
+def test_mix_equals_alone_and_reports_latency(srv_mod):
+    trace = inputs.serving_trace(count=12, rate=400.0, seed=3, nmin=64, nmax=256, nstep=32, smin=20, smax=120)
+    # a small budget forces queueing and admissions into freed memory
+    budget = 3 * srv_mod.device_bytes("mhd_glm", 256)
+    server = srv_mod.Server(budget_bytes=budget, tick_steps=16, keep_results=True)
+    rep = server.run(trace, realtime=True)
+    summ = rep.summary()
+    assert summ["completed"] == len(trace) and summ["failed"] == 0
+    assert summ["latency_p99_s"] >= summ["latency_p50_s"] > 0
+    for job in rep.jobs[::3]:
+        alone = srv_mod.serve_alone(job.req, tick_steps=16)
+        assert np.array_equal(job.result, alone), job.req
+
+
+def test_budget_is_respected(srv_mod):
+    trace = inputs.serving_trace(count=6, rate=1e6, seed=4, nmin=128, nmax=128, nstep=32, smin=10, smax=10)
+    per = max(srv_mod.device_bytes(r.system, r.n) for r in trace)
+    server = srv_mod.Server(budget_bytes=2 * per, tick_steps=5)
+    rep = server.run(trace, realtime=False)
+    assert rep.summary()["completed"] == 6
+    assert rep.peak_bytes <= 2 * per
