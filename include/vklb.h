@@ -150,7 +150,9 @@ int vklb_set_tiling(vklb_sim* sim, int32_t tile_x, int32_t tile_y);
 
 /* Step-kernel variant for D2Q5: 0 = plain coalesced loads, 1 = rows streamed
  * into shared memory by bulk asynchronous copies (TMA) with `stages` rows in
- * flight (2..8).  Both compute the same arithmetic.  Default: 0 (4 stages kept for 1). */
+ * flight (2..8), 2 = plain loads with at most 128 threads per block and a
+ * register cap for 8 resident blocks per SM.  All compute the same arithmetic.
+ * Default: 0 (4 stages kept for 1). */
 int vklb_set_variant(vklb_sim* sim, int32_t variant, int32_t stages);
 
 /* Enqueue n steps of Fig. 5 (no host synchronisation). */

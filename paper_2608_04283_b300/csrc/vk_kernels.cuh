@@ -718,6 +718,14 @@ __global__ void step2d_kernel(StepArgs<T> a, int TX, int TY) {
   step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
 }
 
+// The plain step with at most 128 threads per block and at least 8 resident
+// blocks per SM: the register cap (64) buys occupancy for the small systems.
+template <class Sys, class T, class R>
+__global__ void __launch_bounds__(128, 8) step2d_lb_kernel(StepArgs<T> a, int TX, int TY) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
+}
+
 template <class Sys, class T, class R>
 __global__ void step2d_tma_kernel(StepArgs<T> a, int TX, int TY, int D) {
   extern __shared__ __align__(128) unsigned char smem[];

@@ -157,6 +157,7 @@ struct Impl {
       if (!attr_set) {
         cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
       }
       dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
@@ -164,6 +165,8 @@ struct Impl {
         StepArgs<T> a = make_args<T>(s, t_end);
         if (s->variant == 1)
           step2d_tma_kernel<Sys, T, R><<<grid, TX + 64, sm, s->stream>>>(a, TX, TY, D);
+        else if (s->variant == 2)
+          step2d_lb_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         else
           step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         s->cur ^= 1;
@@ -475,6 +478,7 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
   if (tx == 0) tx = 64;
   if (ty == 0) ty = 16;
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
+  if (s->variant == 2 && tx > 128) return VKLB_ERR_ARG;
   if (s->ops->smem(s->variant, s->P, tx, ty, s->stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->tile_x = tx;
   s->tile_y = ty;
@@ -482,7 +486,8 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
 }
 
 int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
-  if (!s || variant < 0 || variant > 1) return VKLB_ERR_ARG;
+  if (!s || variant < 0 || variant > 2) return VKLB_ERR_ARG;
+  if (variant == 2 && s->tile_x > 128) return VKLB_ERR_ARG;
   if (stages == 0) stages = 4;
   if (stages < 2 || stages > 8) return VKLB_ERR_ARG;
   if (s->dim != 2 && variant == 1) return VKLB_ERR_UNSUPPORTED;
