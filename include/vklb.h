@@ -148,11 +148,12 @@ int vklb_set_state(vklb_sim* sim, const double* U, int32_t on_device);
  * block); 0 keeps the built-in default.  Used by the autotuner. */
 int vklb_set_tiling(vklb_sim* sim, int32_t tile_x, int32_t tile_y);
 
-/* Step-kernel variant for D2Q5: 0 = plain coalesced loads, 1 = rows streamed
- * into shared memory by bulk asynchronous copies (TMA) with `stages` rows in
- * flight (2..8), 2 = plain loads with at most 128 threads per block and a
- * register cap for 8 resident blocks per SM.  All compute the same arithmetic.
- * Default: 0 (4 stages kept for 1). */
+/* Step-kernel variant for D2Q5: 0 = plain coalesced loads, rows exchanged
+ * through shared memory with one block barrier per row; 1 = rows streamed into
+ * shared memory by bulk asynchronous copies (TMA) with `stages` rows in flight
+ * (2..8).  Both compute the same arithmetic.  Default: 0 (4 stages kept for 1).
+ * ERR_ARG for an unknown variant, a stage count outside 2..8 or a tiling whose
+ * shared memory does not fit; ERR_UNSUPPORTED for variant 1 on a 1D grid. */
 int vklb_set_variant(vklb_sim* sim, int32_t variant, int32_t stages);
 
 /* Enqueue n steps of Fig. 5 (no host synchronisation). */

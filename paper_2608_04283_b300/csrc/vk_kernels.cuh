@@ -191,6 +191,26 @@ __device__ __forceinline__ void step_bookkeeping(Ctl* ctl, int slot, const StepS
   }
 }
 
+// The step's constants in the compute type, converted once per block by one
+// thread and shared: FP64 conversions issue at a small fraction of the FP32
+// rate on this part, so per-thread conversions would cost more than the march.
+template <class Sys, class R>
+struct BlockConsts {
+  Sys sys;
+  R xinv, ch, c, om, k;
+};
+template <class Sys, class R, class T>
+__device__ __forceinline__ BlockConsts<Sys, R> block_consts(const StepArgs<T>& a, const StepScalars& sc) {
+  BlockConsts<Sys, R> b;
+  b.sys = make_sys<Sys>(a.sp);
+  b.xinv = (R)sc.xinv;
+  b.ch = (R)sc.ch;
+  b.c = (R)a.c;
+  b.om = (R)a.omega;
+  b.k = (R)a.k;
+  return b;
+}
+
 // ------------------------------------------------------------------ D2Q5 step
 // March over the rows of one tile, up or down.  Tiles of
 // even row index march up and odd ones down, so the two tiles that share a
@@ -203,11 +223,11 @@ __device__ __forceinline__ void step_bookkeeping(Ctl* ctl, int slot, const StepS
 // arithmetic is large enough that a second copy costs more in instruction-cache
 // misses than the register selects).
 template <class Sys, class T, class R, int DIR>
-__device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const StepScalars& sc, int bx, int by,
-                                                int TX, int TY, unsigned char* smem) {
+__device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const BlockConsts<Sys, R>& bc, int bx,
+                                                int by, int TX, int TY, unsigned char* smem) {
   constexpr int P = Sys::P;
   const bool up = DIR > 0 ? true : (DIR < 0 ? false : (by & 1) == 0);
-  const Sys sys = make_sys<Sys>(a.sp);
+  const Sys sys = bc.sys;
   const int tx = threadIdx.x;
   const int x0 = bx * TX, y0 = by * TY;
   const int nx = a.nx, ny = a.ny;
@@ -219,7 +239,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Step
   const T* __restrict__ fin = a.f[a.parity];
   T* __restrict__ fout = a.f[a.parity ^ 1];
   const int s1 = (a.slot + 1) % 3;
-  const R xinv = (R)sc.xinv, ch = (R)sc.ch, c = (R)a.c, om = (R)a.omega, kk = (R)a.k;
+  const R xinv = bc.xinv, ch = bc.ch, c = bc.c, om = bc.om, kk = bc.k;
   const int set = a.set;
   auto row_of = [&](int r) -> int { return up ? y0 + r : y0 + h - 1 - r; };
 
@@ -353,10 +373,13 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
   // the step's scalars in FP64 by one thread per block (FP64 is slow on this
   // part), shared with the others
   __shared__ StepScalars s_sc;
-  if (tx == 0) s_sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+  __shared__ BlockConsts<Sys, R> s_bc;
+  if (tx == 0) {
+    s_sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+    s_bc = block_consts<Sys, R>(a, s_sc);
+  }
   __syncthreads();
-  const StepScalars sc = s_sc;
-  if (sc.done) {
+  if (s_sc.done) {
     // t_end already reached: this launch is a no-op that keeps the ping-pong
     // consistent (f^{n+1} = f^n, same control words).
     const int w = min(TX, a.nx - x0), h = min(TY, a.ny - y0);
@@ -377,14 +400,14 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     }
     return;
   }
-  if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, sc, a.dx, a.fixed_xi, Sys::MHD);
+  if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, s_sc, a.dx, a.fixed_xi, Sys::MHD);
   if constexpr (Sys::P <= 4) {
     if (by & 1)
-      step2d_tile_dir<Sys, T, R, -1>(a, sc, bx, by, TX, TY, smem);
+      step2d_tile_dir<Sys, T, R, -1>(a, s_bc, bx, by, TX, TY, smem);
     else
-      step2d_tile_dir<Sys, T, R, +1>(a, sc, bx, by, TX, TY, smem);
+      step2d_tile_dir<Sys, T, R, +1>(a, s_bc, bx, by, TX, TY, smem);
   } else {
-    step2d_tile_dir<Sys, T, R, 0>(a, sc, bx, by, TX, TY, smem);
+    step2d_tile_dir<Sys, T, R, 0>(a, s_bc, bx, by, TX, TY, smem);
   }
 }
 
@@ -445,8 +468,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 template <class T>
 struct TmaLayout {
-  int TX, TY, D, SW;        // tile, stages, stage row width in elements
-  size_t stage_elems;       // elements of one stage
+  int TX, TY, D;
+  size_t stage_elems;       // elements of one stage (5 p planes x TX)
   size_t off_stage, off_rb, off_ring, bytes;
   template <class R, int P>
   VK_HD static TmaLayout make(int TX, int TY, int D) {
@@ -454,46 +477,48 @@ struct TmaLayout {
     L.TX = TX;
     L.TY = TY;
     L.D = D;
-    L.SW = TX + 2 * (16 / (int)sizeof(T));
-    L.stage_elems = (size_t)5 * P * L.SW;
+    L.stage_elems = (size_t)5 * P * TX;
     L.off_stage = 128;
     L.off_rb = L.off_stage + (size_t)D * L.stage_elems * sizeof(T);
     L.off_rb = (L.off_rb + 15) & ~(size_t)15;
     L.off_ring = L.off_rb + (size_t)6 * P * TX * sizeof(R);
-    L.bytes = L.off_ring + (size_t)6 * P * sizeof(R) + 16;
+    L.bytes = L.off_ring + (size_t)2 * P * TY * sizeof(R) + 16;
     return L;
   }
 };
 
+// March with rows streamed into shared memory.  The x-ring cells of every row
+// are collided up front from global memory (as in the plain march); the
+// producer warp only issues the row copies, right after each row barrier, so it
+// never holds the barrier back.  Tiles march up or down by tile-row parity.
 template <class Sys, class T, class R>
 __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, int by, int TX, int TY, int D,
                                                 unsigned char* smem) {
   constexpr int P = Sys::P;
   constexpr int NPL = 5 * P;
-  constexpr int CH = 16 / (int)sizeof(T);
   const TmaLayout<T> L = TmaLayout<T>::template make<R, P>(TX, TY, D);
-  const int SW = L.SW;
-  const Sys sys = make_sys<Sys>(a.sp);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const bool consumer = tid < TX;
-  const int pw = consumer ? -1 : (tid - TX) >> 5;   // producer warps: 0 streams rows + left ring, 1 right ring
-  const bool producer = pw == 0;
-  const bool ringer = pw >= 0 && lane == 0;
+  const bool producer = !consumer;
   const int x0 = bx * TX, y0 = by * TY;
   const int nx = a.nx, ny = a.ny, pitch = a.pitch;
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);
   const int x = x0 + tid;
   const bool act = consumer && tid < w;
+  const bool up = (by & 1) == 0;
   const size_t plane = (size_t)pitch * ny;
   const T* __restrict__ fin = a.f[a.parity];
   T* __restrict__ fout = a.f[a.parity ^ 1];
   __shared__ StepScalars s_sc;
-  if (tid == 0) s_sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+  __shared__ BlockConsts<Sys, R> s_bc;
+  if (tid == 0) {
+    s_sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+    s_bc = block_consts<Sys, R>(a, s_sc);
+  }
   __syncthreads();
-  const StepScalars sc = s_sc;
   const int s1 = (a.slot + 1) % 3;
-  if (sc.done) {
+  if (s_sc.done) {
     if (act)
       for (int r = 0; r < h; ++r)
         for (int i = 0; i < NPL; ++i) {
@@ -510,48 +535,35 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     }
     return;
   }
-  if (bx == 0 && by == 0 && tid == 0) step_bookkeeping(a.ctl, a.slot, sc, a.dx, a.fixed_xi, Sys::MHD);
-  const R xinv = (R)sc.xinv, ch = (R)sc.ch, c = (R)a.c, om = (R)a.omega, kk = (R)a.k;
+  if (bx == 0 && by == 0 && tid == 0) step_bookkeeping(a.ctl, a.slot, s_sc, a.dx, a.fixed_xi, Sys::MHD);
+  const Sys sys = s_bc.sys;
+  const R xinv = s_bc.xinv, ch = s_bc.ch, c = s_bc.c, om = s_bc.om, kk = s_bc.k;
   const int set = a.set;
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   T* stages = reinterpret_cast<T*>(smem + L.off_stage);
   R* rb1 = reinterpret_cast<R*>(smem + L.off_rb);   // [3][P][TX]
   R* rb2 = rb1 + 3 * P * TX;                       // [3][P][TX]
-  R* ringL = reinterpret_cast<R*>(smem + L.off_ring);  // [3][P]
-  R* ringR = ringL + 3 * P;                            // [3][P]
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_ring + 6 * P * sizeof(R));
+  R* ringL = reinterpret_cast<R*>(smem + L.off_ring);  // [P][TY]
+  R* ringR = ringL + P * TY;                           // [P][TY]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_ring + 2 * P * TY * sizeof(R));
 
-  const int nrows = h + 2;   // y ring below, h tile rows, y ring above
-  const int xl = (x0 - 1 + nx) % nx, xr = (x0 + w) % nx;
-  const int xlc = (xl / CH) * CH, xrc = (xr / CH) * CH;
-  const int colL = TX + (xl - xlc), colR = TX + CH + (xr - xrc);
+  const int nrows = h + 2;   // ring row behind, h tile rows in march order, ring row ahead
   const uint32_t main_bytes = (uint32_t)((((size_t)w * sizeof(T)) + 15) & ~(size_t)15);
-
   auto row_y = [&](int j) -> int {
-    if (j == 0) return (y0 - 1 + ny) % ny;
-    if (j == nrows - 1) return (y0 + h) % ny;
-    return y0 + j - 1;
+    if (j == 0) return up ? (y0 - 1 + ny) % ny : (y0 + h) % ny;
+    if (j == nrows - 1) return up ? (y0 + h) % ny : (y0 - 1 + ny) % ny;
+    return up ? y0 + j - 1 : y0 + h - j;
   };
-  // producer warp: stream row j into stage j % D
+  // producer warp: stream row j into stage j % D (one copy per plane)
   auto issue = [&](int j) {
     const int s = j % D;
     T* st = stages + (size_t)s * L.stage_elems;
-    const bool interior = j >= 1 && j <= h;
-    const uint32_t bytes = (uint32_t)NPL * (main_bytes + (interior ? 32u : 0u));
-    const T* src = fin + (size_t)row_y(j) * pitch;
+    const T* src = fin + (size_t)row_y(j) * pitch + x0;
     fence_proxy_async_smem();
-    if (lane == 0) mbar_arrive_expect_tx(&bars[s], bytes);
+    if (lane == 0) mbar_arrive_expect_tx(&bars[s], (uint32_t)NPL * main_bytes);
     __syncwarp();
-    for (int i = lane; i < NPL; i += 32) {
-      const T* ps = src + (size_t)i * plane;
-      T* pd = st + (size_t)i * SW;
-      bulk_g2s(pd, ps + x0, main_bytes, &bars[s]);
-      if (interior) {
-        bulk_g2s(pd + TX, ps + xlc, 16u, &bars[s]);
-        bulk_g2s(pd + TX + CH, ps + xrc, 16u, &bars[s]);
-      }
-    }
+    for (int i = lane; i < NPL; i += 32) bulk_g2s(st + (size_t)i * TX, src + (size_t)i * plane, main_bytes, &bars[s]);
   };
   auto stage_of = [&](int j) -> const T* { return stages + (size_t)(j % D) * L.stage_elems; };
 
@@ -561,48 +573,56 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     *abort_flag = 0;
   }
   __syncthreads();
-  int issued = 0;
-  if (producer) {
+  if (producer)
     for (int j = 0; j < min(D, nrows); ++j) issue(j);
-  }
-  issued = min(D, nrows);
+  int issued = min(D, nrows);
 
-  R f4prev[P], f3c[P], f4c[P];
+  // x ring: only the component that streams into the tile, from the x split
+  for (int t = tid; t < 2 * h && consumer; t += TX) {
+    const int side = t >= h;
+    const int r = side ? t - h : t;
+    const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
+    const size_t idx = (size_t)(y0 + r) * pitch + xr;
+    R o[5][P];
+    if (!side) {
+      collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
 #pragma unroll
-  for (int i = 0; i < P; ++i) f4prev[i] = f3c[i] = f4c[i] = R(0);
+      for (int i = 0; i < P; ++i) ringL[i * TY + r] = o[0][i];
+    } else {
+      collide_d2q5<Sys, T, R, C_Q2>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+      for (int i = 0; i < P; ++i) ringR[i * TY + r] = o[1][i];
+    }
+  }
+
+  R fbp[P], f3c[P], fbc[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
   bool ok = true;
   if (consumer) {
     ok = mbar_wait_bounded(&bars[0], 0u);
     if (ok && act) {
       R o[5][P];
-      collide_d2q5<Sys, T, R, C_Q4>(sys, stage_of(0), (size_t)SW, (size_t)tid, xinv, c, om, set, kk, ch, o);
+      if (up) {
+        collide_d2q5<Sys, T, R, C_Q4>(sys, stage_of(0), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
 #pragma unroll
-      for (int i = 0; i < P; ++i) f4prev[i] = o[3][i];
+        for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
+      } else {
+        collide_d2q5<Sys, T, R, C_Q5>(sys, stage_of(0), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+        for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
+      }
     }
     ok = ok && mbar_wait_bounded(&bars[1 % D], (uint32_t)((1 / D) & 1));
     if (ok && act) {
       R o[5][P];
-      collide_d2q5<Sys, T, R, C_FULL>(sys, stage_of(1), (size_t)SW, (size_t)tid, xinv, c, om, set, kk, ch, o);
+      collide_d2q5<Sys, T, R, C_FULL>(sys, stage_of(1), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) {
         rb1[i * TX + tid] = o[0][i];
         rb2[i * TX + tid] = o[1][i];
         f3c[i] = o[2][i];
-        f4c[i] = o[3][i];
-      }
-    }
-  } else if (ringer) {
-    ok = mbar_wait_bounded(&bars[1 % D], (uint32_t)((1 / D) & 1));
-    if (ok) {
-      R o[5][P];
-      if (pw == 0) {
-        collide_d2q5<Sys, T, R, C_Q1>(sys, stage_of(1), (size_t)SW, (size_t)colL, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-        for (int i = 0; i < P; ++i) ringL[i] = o[0][i];
-      } else {
-        collide_d2q5<Sys, T, R, C_Q2>(sys, stage_of(1), (size_t)SW, (size_t)colR, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-        for (int i = 0; i < P; ++i) ringR[i] = o[1][i];
+        fbc[i] = up ? o[3][i] : o[4][i];
       }
     }
   }
@@ -620,45 +640,34 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
   R m1 = R(0), m2 = R(0);
   bool bad = false;
   for (int r = 0; r < h && !aborted; ++r) {
-    const int j = r + 2;                 // stream row computed now (tile row r+1 or the top ring)
+    const int j = r + 2;                 // stream row collided now
     const bool full = r + 1 < h;
     const int nb = (r + 1) % 3, cb = r % 3;
-    R f5n[P], f3n[P], f4n[P];
+    R fan[P], f3n[P], fbn[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) f5n[i] = f3n[i] = f4n[i] = R(0);
-    const uint32_t par = (uint32_t)((j / D) & 1);
+    for (int i = 0; i < P; ++i) fan[i] = f3n[i] = fbn[i] = R(0);
     if (consumer) {
-      ok = mbar_wait_bounded(&bars[j % D], par);
+      ok = mbar_wait_bounded(&bars[j % D], (uint32_t)((j / D) & 1));
       if (ok && act) {
         R o[5][P];
         if (full) {
-          collide_d2q5<Sys, T, R, C_FULL>(sys, stage_of(j), (size_t)SW, (size_t)tid, xinv, c, om, set, kk, ch, o);
+          collide_d2q5<Sys, T, R, C_FULL>(sys, stage_of(j), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) {
             rb1[(nb * P + i) * TX + tid] = o[0][i];
             rb2[(nb * P + i) * TX + tid] = o[1][i];
             f3n[i] = o[2][i];
-            f4n[i] = o[3][i];
-            f5n[i] = o[4][i];
+            fbn[i] = up ? o[3][i] : o[4][i];
+            fan[i] = up ? o[4][i] : o[3][i];
           }
+        } else if (up) {
+          collide_d2q5<Sys, T, R, C_Q5>(sys, stage_of(j), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+          for (int i = 0; i < P; ++i) fan[i] = o[4][i];
         } else {
-          collide_d2q5<Sys, T, R, C_Q5>(sys, stage_of(j), (size_t)SW, (size_t)tid, xinv, c, om, set, kk, ch, o);
+          collide_d2q5<Sys, T, R, C_Q4>(sys, stage_of(j), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
 #pragma unroll
-          for (int i = 0; i < P; ++i) f5n[i] = o[4][i];
-        }
-      }
-    } else if (ringer && full) {
-      ok = mbar_wait_bounded(&bars[j % D], par);
-      if (ok) {
-        R o[5][P];
-        if (pw == 0) {
-          collide_d2q5<Sys, T, R, C_Q1>(sys, stage_of(j), (size_t)SW, (size_t)colL, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-          for (int i = 0; i < P; ++i) ringL[nb * P + i] = o[0][i];
-        } else {
-          collide_d2q5<Sys, T, R, C_Q2>(sys, stage_of(j), (size_t)SW, (size_t)colR, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-          for (int i = 0; i < P; ++i) ringR[nb * P + i] = o[1][i];
+          for (int i = 0; i < P; ++i) fan[i] = o[3][i];
         }
       }
     }
@@ -672,21 +681,26 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
       issued = j + D + 1;
     }
     if (act) {
-      const size_t base = (size_t)(y0 + r) * pitch + x;
+      const int yo = row_y(r + 1);
+      const int rt = yo - y0;
+      const size_t base = (size_t)yo * pitch + x;
       R U[P];
 #pragma unroll
       for (int i = 0; i < P; ++i) {
-        R g1 = tid == 0 ? ringL[cb * P + i] : rb1[(cb * P + i) * TX + tid - 1];
-        R g2 = tid == w - 1 ? ringR[cb * P + i] : rb2[(cb * P + i) * TX + tid + 1];
-        R g3 = f3c[i], g4 = f4prev[i], g5 = f5n[i];
-        Store<T>::st(fout + (size_t)(0 * P + i) * plane + base, g1);
-        Store<T>::st(fout + (size_t)(1 * P + i) * plane + base, g2);
-        Store<T>::st(fout + (size_t)(2 * P + i) * plane + base, g3);
-        Store<T>::st(fout + (size_t)(3 * P + i) * plane + base, g4);
-        Store<T>::st(fout + (size_t)(4 * P + i) * plane + base, g5);
+        R g[5];
+        g[0] = tid == 0 ? ringL[i * TY + rt] : rb1[(cb * P + i) * TX + tid - 1];
+        g[1] = tid == w - 1 ? ringR[i * TY + rt] : rb2[(cb * P + i) * TX + tid + 1];
+        g[2] = f3c[i];
+        g[3] = up ? fbp[i] : fan[i];
+        g[4] = up ? fan[i] : fbp[i];
         const T* tp = nullptr;
-        U[i] = round_store(g1, tp) + round_store(g2, tp) + round_store(g3, tp) + round_store(g4, tp) +
-               round_store(g5, tp);
+        R acc = R(0);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          Store<T>::st(fout + (size_t)(q * P + i) * plane + base, g[q]);
+          acc += round_store(g[q], tp);
+        }
+        U[i] = acc;
       }
       R e1, e2;
       bad |= !sys.epilogue(U, e1, e2);
@@ -695,9 +709,9 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-      f4prev[i] = f4c[i];
+      fbp[i] = fbc[i];
       f3c[i] = f3n[i];
-      f4c[i] = f4n[i];
+      fbc[i] = fbn[i];
     }
   }
   if (aborted) {
@@ -714,15 +728,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
 
 template <class Sys, class T, class R>
 __global__ void step2d_kernel(StepArgs<T> a, int TX, int TY) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
-}
-
-// The plain step with at most 128 threads per block and at least 8 resident
-// blocks per SM: the register cap (64) buys occupancy for the small systems.
-template <class Sys, class T, class R>
-__global__ void __launch_bounds__(128, 8) step2d_lb_kernel(StepArgs<T> a, int TX, int TY) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
 }
 
@@ -747,7 +753,7 @@ __global__ void step2d_batch_kernel(const StepArgs<T>* __restrict__ desc, const 
   StepArgs<T> a = desc[wk.sim];
   a.parity = (a.parity + step_off) & 1;
   a.slot = (a.slot + step_off) % 3;
-  if (VARIANT == 1)
+  if constexpr (VARIANT == 1)
     step2d_tile_tma<Sys, T, R>(a, wk.bx, wk.by, TX, TY, D, smem);
   else
     step2d_tile<Sys, T, R>(a, wk.bx, wk.by, TX, TY, smem);

@@ -157,16 +157,13 @@ struct Impl {
       if (!attr_set) {
         cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
       }
       dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
       for (int64_t i = 0; i < n; ++i) {
         StepArgs<T> a = make_args<T>(s, t_end);
         if (s->variant == 1)
-          step2d_tma_kernel<Sys, T, R><<<grid, TX + 64, sm, s->stream>>>(a, TX, TY, D);
-        else if (s->variant == 2)
-          step2d_lb_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
+          step2d_tma_kernel<Sys, T, R><<<grid, TX + 32, sm, s->stream>>>(a, TX, TY, D);
         else
           step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         s->cur ^= 1;
@@ -205,7 +202,7 @@ struct BatchImpl {
     const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(b->variant, TX, TY, D);
     for (int64_t i = 0; i < n; ++i) {
       if (b->variant == 1)
-        step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX + 64, sm, b->own>>>(
+        step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX + 32, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
       else
         step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(
@@ -444,6 +441,14 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? VKLB_ERR_NOMEM : VKLB_ERR_CUDA;
   }
+  // zero both buffers once: the row padding (pitch > nx) is never written by
+  // the kernels, and a checkpoint blob must not carry stale device memory
+  if ((e = cudaMemsetAsync(s->f[0], 0, fbytes, s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(s->f[1], 0, fbytes, s->stream)) != cudaSuccess) {
+    free_sim(s);
+    cudaGetLastError();
+    return VKLB_ERR_CUDA;
+  }
   *out = s;
   return VKLB_OK;
 }
@@ -478,7 +483,6 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
   if (tx == 0) tx = 64;
   if (ty == 0) ty = 16;
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
-  if (s->variant == 2 && tx > 128) return VKLB_ERR_ARG;
   if (s->ops->smem(s->variant, s->P, tx, ty, s->stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->tile_x = tx;
   s->tile_y = ty;
@@ -486,11 +490,10 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
 }
 
 int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
-  if (!s || variant < 0 || variant > 2) return VKLB_ERR_ARG;
-  if (variant == 2 && s->tile_x > 128) return VKLB_ERR_ARG;
+  if (!s || variant < 0 || variant > 1) return VKLB_ERR_ARG;
   if (stages == 0) stages = 4;
   if (stages < 2 || stages > 8) return VKLB_ERR_ARG;
-  if (s->dim != 2 && variant == 1) return VKLB_ERR_UNSUPPORTED;
+  if (s->dim != 2 && variant != 0) return VKLB_ERR_UNSUPPORTED;
   if (s->ops->smem(variant, s->P, s->tile_x, s->tile_y, stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->variant = variant;
   s->stages = stages;
