@@ -125,6 +125,9 @@ typedef struct {
   int32_t kernels_per_step;  /* kernel launches one vklb_step(1) makes */
   int32_t variant;           /* step kernel: 0 plain loads, 1 bulk-copy (TMA) row pipeline */
   int64_t pitch;             /* elements per row of a device distribution plane (>= nx) */
+  int32_t blocks_per_sm;     /* 2D: resident blocks per SM of the step kernel at this launch shape
+                                (CUDA occupancy calculator); 1D: 0 */
+  int32_t sms;               /* SMs of the current device */
 } vklb_info_t;
 
 /* Create a simulation.  dt > 0 fixes xi = dx / dt for every step; dt <= 0
@@ -145,7 +148,14 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid,
 int vklb_set_state(vklb_sim* sim, const double* U, int32_t on_device);
 
 /* Launch shape of the step kernel (tile_x cells along x by tile_y rows per
- * block); 0 keeps the built-in default.  Used by the autotuner. */
+ * block): tile_x a multiple of 32 in 32..256, tile_y in 1..256; 0 takes the
+ * built-in default (128, then the wave-fit height; also the shape a new 2D
+ * simulation starts with).  tile_y = -1 (2D only) picks the height that
+ * makes the grid fill whole waves of resident blocks (SM count x blocks per SM
+ * of the kernel this tile_x and variant launch, from the CUDA occupancy
+ * calculator, on the current device), in as few waves as keep tile_y <= 256.
+ * The resolved shape is reported by vklb_info.  ERR_ARG for a shape outside
+ * these ranges or whose shared memory does not fit.  Used by the autotuner. */
 int vklb_set_tiling(vklb_sim* sim, int32_t tile_x, int32_t tile_y);
 
 /* Step-kernel variant for D2Q5: 0 = plain coalesced loads, rows exchanged
@@ -203,6 +213,10 @@ const char* vklb_strerror(int status);
  * alone.  vklb_batch_step(n) enqueues n steps on the stream of the first
  * simulation; use_graph != 0 captures them in a CUDA graph and replays it. */
 int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out);
+/* Same ranges as vklb_set_tiling.  tile_y = -1: the members' grids differ, so
+ * the height (1..64) maximises (fill of the last wave of the work-list) x
+ * (tile_y / (tile_y + 2)), the share of a tile's rows that are not the
+ * recomputed ring. */
 int vklb_batch_set_tiling(vklb_batch* b, int32_t tile_x, int32_t tile_y);
 int vklb_batch_step(vklb_batch* b, int64_t n, int32_t use_graph);
 int vklb_batch_destroy(vklb_batch* b);

@@ -20,7 +20,9 @@ from . import inputs
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE = os.path.join(HERE, "tuning.json")
-TILES = [(32, 8), (32, 16), (64, 4), (64, 8), (64, 16), (64, 32), (128, 4), (128, 8), (128, 16), (256, 4), (256, 8)]
+# (tx, -1): the height that fills whole waves of resident blocks
+TILES = [(32, 8), (32, 16), (64, 4), (64, 8), (64, 16), (64, 32), (128, 4), (128, 8), (128, 16), (128, 32),
+         (128, 64), (256, 4), (256, 8), (64, -1), (128, -1), (256, -1)]
 VARIANTS = [(0, 0), (1, 2), (1, 3)]
 
 
@@ -43,8 +45,9 @@ def tune(system, precision, n, steps=30, warmup=5, tiles=TILES, variants=VARIANT
     for var in variants:
         for tile in tiles:
             try:
+                sim.set_tiling(32, 8)      # a shape every variant accepts
                 sim.set_variant(*var)
-                sim.set_tiling(*tile)
+                sim.set_tiling(*tile)      # the wave-fit height depends on the variant
             except vklb.VKLBError:
                 continue
             sim.set_state(U0d)
@@ -55,7 +58,8 @@ def tune(system, precision, n, steps=30, warmup=5, tiles=TILES, variants=VARIANT
             e1.record(stream)
             e1.synchronize()
             sim.sync()
-            results.append({"variant": list(var), "tile": list(tile), "ms": e0.elapsed_time(e1) / steps})
+            results.append({"variant": list(var), "tile": list(tile), "ms": e0.elapsed_time(e1) / steps,
+                            "resolved": [sim.info.tile_x, sim.info.tile_y], "blocks_per_sm": sim.info.blocks_per_sm})
     sim.close()
     results.sort(key=lambda r: r["ms"])
     return results

@@ -732,6 +732,25 @@ __global__ void step2d_kernel(StepArgs<T> a, int TX, int TY) {
   step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
 }
 
+// Register bound of the plain step: blocks of at most 128 threads with at least
+// `min_blocks` of them resident per SM (0 = no bound).  FP32 MHD-GLM needs about
+// 157 registers a thread unbounded (3 blocks of 4 warps per SM); capped at 128
+// (4 blocks) it spills a few hundred bytes to L1 and still runs faster.
+template <class Sys, class R>
+struct StepBound {
+  static constexpr int min_blocks = 0;
+};
+template <>
+struct StepBound<MHDGLM<float>, float> {
+  static constexpr int min_blocks = 4;
+};
+
+template <class Sys, class T, class R, int MINB>
+__global__ void __launch_bounds__(128, MINB) step2d_lb_kernel(StepArgs<T> a, int TX, int TY) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
+}
+
 template <class Sys, class T, class R>
 __global__ void step2d_tma_kernel(StepArgs<T> a, int TX, int TY, int D) {
   extern __shared__ __align__(128) unsigned char smem[];

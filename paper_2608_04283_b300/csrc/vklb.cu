@@ -56,6 +56,8 @@ struct Ops {
   int (*totals)(vklb_sim*, double*);
   int (*batch)(vklb_batch*, int64_t, int);
   size_t (*smem)(int variant, int p, int tx, int ty, int stages);
+  int (*occupancy)(int variant, int tx, int ty, int stages);
+  int (*batch_occupancy)(int variant, int tx, int ty, int stages);
   size_t real_bytes;
   size_t args_bytes;
 };
@@ -153,17 +155,14 @@ struct Impl {
     } else {
       const int TX = s->tile_x, TY = s->tile_y, D = s->stages;
       const size_t sm = smem_bytes_v(s->variant, TX, TY, D);
-      static bool attr_set = false;
-      if (!attr_set) {
-        cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-      }
+      set_attributes();
       dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
       for (int64_t i = 0; i < n; ++i) {
         StepArgs<T> a = make_args<T>(s, t_end);
         if (s->variant == 1)
           step2d_tma_kernel<Sys, T, R><<<grid, TX + 32, sm, s->stream>>>(a, TX, TY, D);
+        else if (bounded(TX))
+          step2d_lb_kernel<Sys, T, R, kMinBlocks><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         else
           step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         s->cur ^= 1;
@@ -171,6 +170,46 @@ struct Impl {
       }
       g_launches += n;
       return cuda_status(cudaGetLastError());
+    }
+  }
+
+  // the plain step takes the register-bounded instantiation when it has one
+  // and the block fits its 128-thread bound
+  static constexpr int kMinBlocks = StepBound<Sys, R>::min_blocks > 0 ? StepBound<Sys, R>::min_blocks : 1;
+  static bool bounded(int tx) { return StepBound<Sys, R>::min_blocks > 0 && tx <= 128; }
+
+  static void set_attributes() {
+    if constexpr (DIM == 2) {
+      static bool done = false;
+      if (done) return;
+      cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+      cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      done = true;
+    }
+  }
+
+  // resident blocks per SM of the step kernel a sim with this launch shape runs
+  static int occupancy(int variant, int tx, int ty, int d) {
+    if constexpr (DIM != 2) {
+      return 0;
+    } else {
+      set_attributes();
+      const size_t sm = smem_bytes_v(variant, tx, ty, d);
+      int nb = 0;
+      cudaError_t e;
+      if (variant == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_tma_kernel<Sys, T, R>, tx + 32, sm);
+      else if (bounded(tx))
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_lb_kernel<Sys, T, R, kMinBlocks>, tx, sm);
+      else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_kernel<Sys, T, R>, tx, sm);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return nb;
     }
   }
 
@@ -208,6 +247,25 @@ struct BatchImpl {
         step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
     }
+    }
+  }
+  // resident blocks per SM of the batched step kernel at this launch shape
+  static int occupancy(int variant, int tx, int ty, int d) {
+    if constexpr (DIM != 2) {
+      return 0;
+    } else {
+      const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(variant, tx, ty, d);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      int nb = 0;
+      cudaError_t e = variant == 1
+                          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx + 32, sm)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 0>, tx, sm);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return nb;
     }
   }
   static int step(vklb_batch* b, int64_t n, int use_graph) {
@@ -274,6 +332,7 @@ const Ops* ops_of() {
   static const Ops o = {&Impl<Sys, T, R, DIM>::init,    &Impl<Sys, T, R, DIM>::step,
                         &Impl<Sys, T, R, DIM>::moments, &Impl<Sys, T, R, DIM>::totals,
                         &BatchImpl<Sys, T, R, DIM>::step, &smem_of<Sys, T, R, DIM>,
+                        &Impl<Sys, T, R, DIM>::occupancy, &BatchImpl<Sys, T, R, DIM>::occupancy,
                         sizeof(R),                        sizeof(StepArgs<T>)};
   return &o;
 }
@@ -359,6 +418,34 @@ const char* vklb_strerror(int status) {
 }
 
 int64_t vklb_launch_count(void) { return g_launches.load(); }
+
+// Tile height that makes the grid fill whole waves of resident blocks: with
+// `slots` = SMs x resident blocks per SM and gx tiles across, the first k for
+// which ceil(ny / (k * floor(slots / gx))) <= 256 rows.
+static int wave_fit_rows(vklb_sim* s, int tx, int* ty_out) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return VKLB_ERR_CUDA;
+  }
+  const int64_t gx = (s->nx + tx - 1) / tx;
+  int ty = 16;
+  for (int pass = 0; pass < 2; ++pass) {   // occupancy depends on ty through the ring buffers
+    const int nb = s->ops->occupancy(s->variant, tx, ty, s->stages);
+    if (nb < 1) return VKLB_ERR_ARG;
+    int64_t rows = (int64_t)nb * sms / gx;
+    if (rows < 1) rows = 1;
+    for (int64_t k = 1;; ++k) {
+      const int64_t t = (s->ny + k * rows - 1) / (k * rows);
+      if (t <= 256) {
+        ty = (int)(t < 1 ? 1 : t);
+        break;
+      }
+    }
+  }
+  *ty_out = ty;
+  return VKLB_OK;
+}
 
 int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, const vklb_bc* bc,
                 const vklb_weight* weight, double dt, int32_t precision, void* cuda_stream, vklb_sim** out) {
@@ -449,6 +536,13 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
     cudaGetLastError();
     return VKLB_ERR_CUDA;
   }
+  if (dim == 2) {   // default launch shape: 128-cell rows, height fitted to whole waves
+    int ty = 16;
+    if (wave_fit_rows(s, 128, &ty) == VKLB_OK) {
+      s->tile_x = 128;
+      s->tile_y = ty;
+    }
+  }
   *out = s;
   return VKLB_OK;
 }
@@ -480,8 +574,12 @@ int vklb_set_state(vklb_sim* s, const double* U, int32_t on_device) {
 
 int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
   if (!s) return VKLB_ERR_ARG;
-  if (tx == 0) tx = 64;
-  if (ty == 0) ty = 16;
+  if (tx == 0) tx = 128;
+  if (ty == 0) ty = -1;
+  if (ty == -1 && s->dim == 2 && tx >= 32 && tx <= 256 && tx % 32 == 0) {
+    int st = wave_fit_rows(s, tx, &ty);
+    if (st) return st;
+  }
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
   if (s->ops->smem(s->variant, s->P, tx, ty, s->stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->tile_x = tx;
@@ -595,6 +693,11 @@ int vklb_info(const vklb_sim* s, vklb_info_t* info) {
   info->tile_y = s->tile_y;
   info->kernels_per_step = 1;
   info->variant = s->variant;
+  info->blocks_per_sm = s->dim == 2 ? s->ops->occupancy(s->variant, s->tile_x, s->tile_y, s->stages) : 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    cudaGetLastError();
+  info->sms = sms;
   return VKLB_OK;
 }
 
@@ -710,10 +813,44 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
   return VKLB_OK;
 }
 
+// Batch tile height for tile_y = -1: the members' grids differ, so no height
+// makes the work-list a whole number of waves in general.  Over ty = 1..64 take
+// the best (fill of the last wave) x (tile rows / (tile rows + the 2 ring rows
+// each tile recomputes)), the larger ty on ties.
+static int batch_fit_rows(vklb_batch* b, int tx, int* ty_out) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return VKLB_ERR_CUDA;
+  }
+  double best = -1.0;
+  int best_ty = 8;
+  for (int ty = 1; ty <= 64; ++ty) {
+    const int nb = b->ops->batch_occupancy(b->variant, tx, ty, b->stages);
+    if (nb < 1) continue;
+    const double slots = (double)nb * sms;
+    double blocks = 0.0;
+    for (const vklb_sim* s : b->sims) blocks += (double)((s->nx + tx - 1) / tx) * (double)((s->ny + ty - 1) / ty);
+    const double waves = std::ceil(blocks / slots);
+    const double score = blocks / (waves * slots) * ((double)ty / (ty + 2));
+    if (score >= best) {
+      best = score;
+      best_ty = ty;
+    }
+  }
+  if (best < 0.0) return VKLB_ERR_ARG;
+  *ty_out = best_ty;
+  return VKLB_OK;
+}
+
 int vklb_batch_set_tiling(vklb_batch* b, int32_t tx, int32_t ty) {
   if (!b) return VKLB_ERR_ARG;
   if (tx == 0) tx = 64;
   if (ty == 0) ty = 16;
+  if (ty == -1 && tx >= 32 && tx <= 256 && tx % 32 == 0) {
+    int st = batch_fit_rows(b, tx, &ty);
+    if (st) return st;
+  }
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
   if (b->ops->smem(b->variant, b->sims[0]->P, tx, ty, b->stages) > 200 * 1024) return VKLB_ERR_ARG;
   b->tile_x = tx;

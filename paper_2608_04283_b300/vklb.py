@@ -54,7 +54,8 @@ class Info(C.Structure):
     _fields_ = [("p", C.c_int32), ("q", C.c_int32), ("precision", C.c_int32), ("store_bytes", C.c_int32),
                 ("cells", C.c_int64), ("bytes_per_lup", C.c_int64), ("state_bytes", C.c_int64),
                 ("dx", C.c_double), ("tile_x", C.c_int32), ("tile_y", C.c_int32),
-                ("kernels_per_step", C.c_int32), ("variant", C.c_int32), ("pitch", C.c_int64)]
+                ("kernels_per_step", C.c_int32), ("variant", C.c_int32), ("pitch", C.c_int64),
+                ("blocks_per_sm", C.c_int32), ("sms", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -165,6 +166,8 @@ class Sim:
         _check(_lib.vklb_set_state(self._h, U.ctypes.data_as(_P), 0), "vklb_set_state")
 
     def set_tiling(self, tx, ty):
+        """Step-kernel tile: tx cells by ty rows per block; ty = -1 fits the
+        grid to whole waves of resident blocks (resolved height in info.tile_y)."""
         _check(_lib.vklb_set_tiling(self._h, int(tx), int(ty)), "vklb_set_tiling")
         _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
 
