@@ -415,7 +415,8 @@ def secondary(torch, vklb, wl, prec, flush_buf, steps):
 def batched_swe(torch, vklb, count=256, steps=500):
     """Batched form: 256 seeded SWE instances (sides 64..1024, Gaussian humps),
     500 steps each, one launch per step over all instances (CUDA graph), against
-    the same instances launched one at a time.  Reports solves/s."""
+    the same instances launched one at a time, each at its own wave-fit tiling.
+    Reports solves/s."""
     specs = inputs.swe_humps_batch(count, seed=0)
     tile = tiling_for("swe", "fp32", (256, 256)) or (64, 16)
     stream = torch.cuda.Stream()
@@ -450,14 +451,18 @@ def batched_swe(torch, vklb, count=256, steps=500):
     torch.cuda.synchronize()
     tp = time.perf_counter() - t0
     plain_out = [sims[i].moments() for i in (0, count // 2, count - 1)]
-    same = all(np.array_equal(a, c) for a, c in zip(batch_out, plain_out))
+    # each instance alone takes its own wave-fit height, the batch one height
+    # fitted to its whole work-list: the tilings differ, so the two agree to
+    # FP32 rounding (the batch of one is bitwise equal to the batch of many,
+    # which the GPU tests check)
+    diff = max(float(np.abs(a - c).sum() / np.abs(c).sum()) for a, c in zip(batch_out, plain_out))
     b.close()
     for s in sims:
         s.close()
     return {"instances": count, "steps": steps, "cells_total": cells, "tile": list(tile),
             "batched_solves_per_s": count / tb, "plain_solves_per_s": count / tp,
             "batched_MLUPS": cells * steps / tb / 1e6, "plain_MLUPS": cells * steps / tp / 1e6,
-            "speedup": tp / tb, "batched_equals_plain_bitwise": bool(same),
+            "speedup": tp / tb, "batched_vs_plain_rel_l1": diff,
             "note": "wall clock incl. launch; batched = one launch per step over all instances in one CUDA graph"}
 
 
