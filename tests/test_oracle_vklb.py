@@ -278,3 +278,27 @@ def test_run_to_lands_on_t_end():
     sim.run_to(0.1)
     assert sim.t == 0.1
     assert 200 < sim.steps < 260
+
+
+def test_one_step_is_local_given_global_xi():
+    """One step at a cell depends only on its 5-point neighbourhood (Eqs. 42-43)
+    and on the global xi (Eq. 29): an oracle run on the 5 x 5 periodic patch with
+    xi fixed at the full grid's xi_0 reproduces the full grid's step at the
+    patch centre.  (The full-size GPU parity test samples cells this way.)"""
+    n = 16
+    L = 10.0
+    U0 = inputs.isentropic_vortex(n, lo=0.0, hi=L)
+    sysm = systems.Euler(1.4, 2)
+    full = vklb.Sim(sysm, (n, n), (0.0, 0.0), (L, L), omega=2.0, nu=0.3)
+    full.set_state(U0)
+    xi0 = full.xi
+    full.step()
+    Uf = full.moments()
+    dx = L / n
+    for x, y in [(0, 0), (15, 3), (7, 8), (8, 15)]:
+        xs = np.arange(x - 2, x + 3) % n
+        ys = np.arange(y - 2, y + 3) % n
+        ref = vklb.Sim(sysm, (5, 5), (0.0, 0.0), (5 * dx, 5 * dx), omega=2.0, nu=0.3, dt=dx / xi0)
+        ref.set_state(U0[:, ys][:, :, xs])
+        ref.step()
+        np.testing.assert_allclose(ref.moments()[:, 2, 2], Uf[:, y, x], rtol=1e-13, atol=0)
