@@ -1,0 +1,117 @@
+"""Parity at the benchmark's full size and launch shape: the 1024^2 Euler
+isentropic vortex (omega 2, CFL 0.3, c 0.05, k 2) with the tiling bench.py
+times (128 x 8, one wave of 1024 tiles), in FP32 and FP64.
+
+The oracle cannot step 10^6 cells in seconds, but one step of the update at a
+cell depends only on its 5-point neighbourhood and on the global lattice speed
+xi_0 = max|lambda(U_0)| / nu (Eq. 29).  So xi_0 is taken from the oracle's
+global maximum over the full grid, and each sampled cell is checked against an
+oracle run on the 5 x 5 periodic patch around it with xi fixed at xi_0: its
+centre after one step is exactly the full-grid result (pinned on the CPU by
+test_one_step_is_local_given_global_xi).  The samples include the edges of the
+128 x 8 tiles and of the periodic grid, where the kernel's recomputed ring
+cells and index wrap act.  A property that holds at any size (Thm 4.3's
+conservation on a periodic grid) is checked on the whole grid.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import systems, vklb as ovklb
+from paper_2608_04283_b300 import inputs
+from parity_util import max_rel
+
+pytestmark = pytest.mark.gpu
+
+N = 1024
+L = 10.0
+GAMMA = 1.4
+KW = dict(omega=2.0, cfl=0.3, c=0.05, k=2.0, gamma=GAMMA)
+
+
+@pytest.fixture(scope="module")
+def vk():
+    from paper_2608_04283_b300 import build
+    build.build()
+    from paper_2608_04283_b300 import vklb
+    return vklb
+
+
+@pytest.fixture(scope="module")
+def U0():
+    return np.ascontiguousarray(inputs.isentropic_vortex(N))
+
+
+def _bench_tile():
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    return bench.tiling_for("euler", "fp32", (N, N))
+
+
+def _samples():
+    rng = np.random.default_rng(20)
+    edges = [0, 1, 127, 128, 129, 511, 512, N - 2, N - 1]
+    rows = [0, 1, 7, 8, 9, 15, 16, 511, 512, N - 8, N - 1]
+    pts = [(x, y) for x in edges[::2] for y in rows[::2]]
+    pts += [(int(x), int(y)) for x, y in rng.integers(0, N, size=(24, 2))]
+    pts += [(N // 2 + d, N // 2) for d in (-3, 0, 3)]     # through the vortex core
+    return pts
+
+
+def _oracle_at(U0, pts, xi0):
+    dx = L / N
+    sysm = systems.Euler(GAMMA, 2)
+    out = np.empty((U0.shape[0], len(pts)))
+    for i, (x, y) in enumerate(pts):
+        xs = np.arange(x - 2, x + 3) % N
+        ys = np.arange(y - 2, y + 3) % N
+        patch = U0[:, ys][:, :, xs]
+        ref = ovklb.Sim(sysm, (5, 5), (0.0, 0.0), (5 * dx, 5 * dx), omega=KW["omega"], nu=KW["cfl"], c=KW["c"],
+                        k=KW["k"], dt=dx / xi0)
+        ref.set_state(patch)
+        ref.step()
+        out[:, i] = ref.moments()[:, 2, 2]
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-11)])
+def test_fullsize_one_step_sampled(vk, U0, precision, tol):
+    tile = _bench_tile()
+    assert tile == (128, 8)
+    sim = vk.Sim("euler", (N, N), (0.0, 0.0), (L, L), precision=precision, **KW)
+    sim.set_tiling(*tile)
+    assert (sim.info.tile_x, sim.info.tile_y) == (128, 8)
+    sim.set_state(U0)
+    sim.step(1)
+    got = sim.moments()
+    t, nsteps, _ = sim.time()
+    sim.close()
+
+    full = ovklb.Sim(systems.Euler(GAMMA, 2), (N, N), (0.0, 0.0), (L, L), omega=KW["omega"], nu=KW["cfl"])
+    xi0 = full.max_lambda(U0) / KW["cfl"]                   # Eq. (29) over the full grid
+    dx = L / N
+    assert nsteps == 1
+    assert abs(t - dx / xi0) <= (1e-6 if precision == "fp32" else 1e-13) * (dx / xi0)
+
+    pts = _samples()
+    want = _oracle_at(U0, pts, xi0)
+    have = np.stack([got[:, y, x] for x, y in pts], axis=1)
+    err = max_rel(have, want)
+    assert err.max() <= tol, err
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-6), ("fp64", 1e-13)])
+def test_fullsize_conservation(vk, U0, precision, tol):
+    """Thm 4.3: on the periodic grid the totals of rho, m and E do not change;
+    20 steps at the bench's launch shape, FP64 totals of the stored f."""
+    sim = vk.Sim("euler", (N, N), (0.0, 0.0), (L, L), precision=precision, **KW)
+    sim.set_tiling(*_bench_tile())
+    sim.set_state(U0)
+    t0 = sim.totals()
+    sim.step(20)
+    t1 = sim.totals()
+    sim.close()
+    scale = np.abs(t0).max()
+    assert np.abs(t1 - t0).max() <= tol * scale, (t0, t1)
