@@ -413,16 +413,14 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
 
 // ------------------------------------------------- D2Q5 step, bulk-copy rows
 // Same arithmetic as step2d_tile, but the rows of f^n reach the block through
-// shared memory: an extra producer warp issues 1D bulk asynchronous copies
-// (cp.async.bulk, the TMA engine) of every distribution plane's row segment
-// [x0, x0 + TX) plus the two 16-byte chunks holding the x-ring cells, D rows
-// ahead, each stage completing on its own mbarrier.  The per-row block barrier
-// that already exchanges f*_1 / f*_2 between neighbours also tells the producer
-// that a stage has been consumed.  The producer warp's lanes 0 and 1 collide the
-// two x-ring cells of each row (the consumers never diverge for the ring).
-// Every mbarrier wait is bounded; a wait that gives up sets ERR_TIMEOUT and the
-// block leaves the tile after all threads agree, waiting (bounded) for its
-// copies still in flight.
+// shared memory by 1D bulk asynchronous copies (cp.async.bulk, the TMA engine),
+// one per distribution plane's row segment [x0, x0 + TX), D rows ahead, each
+// stage completing on its own mbarrier.  There is one block barrier per row, as
+// in the plain march: before it, thread 0 waits for the next row's copies, so
+// the barrier also publishes that row to the block; after it, the lanes of warp
+// 0 refill the stage just consumed.  Every mbarrier wait is bounded; a wait that
+// gives up sets ERR_TIMEOUT and the block leaves the tile after all threads
+// agree, waiting (bounded) for its copies still in flight.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -481,16 +479,18 @@ struct TmaLayout {
     L.off_stage = 128;
     L.off_rb = L.off_stage + (size_t)D * L.stage_elems * sizeof(T);
     L.off_rb = (L.off_rb + 15) & ~(size_t)15;
-    L.off_ring = L.off_rb + (size_t)6 * P * TX * sizeof(R);
+    L.off_ring = L.off_rb + (size_t)4 * P * TX * sizeof(R);
     L.bytes = L.off_ring + (size_t)2 * P * TY * sizeof(R) + 16;
     return L;
   }
 };
 
-// March with rows streamed into shared memory.  The x-ring cells of every row
-// are collided up front from global memory (as in the plain march); the
-// producer warp only issues the row copies, right after each row barrier, so it
-// never holds the barrier back.  Tiles march up or down by tile-row parity.
+// The march over stream rows 0 .. h+1 (ring row behind, the h tile rows in
+// march order, ring row ahead).  Iteration j collides row j from its stage and
+// then writes stream row j-1, whose f*_1 / f*_2 exchange buffer the previous
+// barrier published; so two exchange buffers suffice.  The x-ring cells are
+// collided up front from global memory.  Tiles march up or down by tile-row
+// parity.
 template <class Sys, class T, class R>
 __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, int by, int TX, int TY, int D,
                                                 unsigned char* smem) {
@@ -499,13 +499,12 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
   const TmaLayout<T> L = TmaLayout<T>::template make<R, P>(TX, TY, D);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const bool consumer = tid < TX;
-  const bool producer = !consumer;
+  const bool issuer = tid < 32;
   const int x0 = bx * TX, y0 = by * TY;
   const int nx = a.nx, ny = a.ny, pitch = a.pitch;
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);
   const int x = x0 + tid;
-  const bool act = consumer && tid < w;
+  const bool act = tid < w;
   const bool up = (by & 1) == 0;
   const size_t plane = (size_t)pitch * ny;
   const T* __restrict__ fin = a.f[a.parity];
@@ -542,20 +541,20 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   T* stages = reinterpret_cast<T*>(smem + L.off_stage);
-  R* rb1 = reinterpret_cast<R*>(smem + L.off_rb);   // [3][P][TX]
-  R* rb2 = rb1 + 3 * P * TX;                       // [3][P][TX]
-  R* ringL = reinterpret_cast<R*>(smem + L.off_ring);  // [P][TY]
-  R* ringR = ringL + P * TY;                           // [P][TY]
+  R* rb1 = reinterpret_cast<R*>(smem + L.off_rb);   // [2][P][TX]  f*_1 of the row
+  R* rb2 = rb1 + 2 * P * TX;                       // [2][P][TX]  f*_2 of the row
+  R* ringL = reinterpret_cast<R*>(smem + L.off_ring);  // [P][TY]  f*_1 at x0 - 1
+  R* ringR = ringL + P * TY;                           // [P][TY]  f*_2 at x0 + w
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_ring + 2 * P * TY * sizeof(R));
 
-  const int nrows = h + 2;   // ring row behind, h tile rows in march order, ring row ahead
+  const int nrows = h + 2;
   const uint32_t main_bytes = (uint32_t)((((size_t)w * sizeof(T)) + 15) & ~(size_t)15);
   auto row_y = [&](int j) -> int {
     if (j == 0) return up ? (y0 - 1 + ny) % ny : (y0 + h) % ny;
     if (j == nrows - 1) return up ? (y0 + h) % ny : (y0 - 1 + ny) % ny;
     return up ? y0 + j - 1 : y0 + h - j;
   };
-  // producer warp: stream row j into stage j % D (one copy per plane)
+  // warp 0: stream row j into stage j % D, one copy per plane
   auto issue = [&](int j) {
     const int s = j % D;
     T* st = stages + (size_t)s * L.stage_elems;
@@ -565,7 +564,6 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     __syncwarp();
     for (int i = lane; i < NPL; i += 32) bulk_g2s(st + (size_t)i * TX, src + (size_t)i * plane, main_bytes, &bars[s]);
   };
-  auto stage_of = [&](int j) -> const T* { return stages + (size_t)(j % D) * L.stage_elems; };
 
   if (tid == 0) {
     for (int s = 0; s < D; ++s) mbar_init(&bars[s], 1);
@@ -573,152 +571,110 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     *abort_flag = 0;
   }
   __syncthreads();
-  if (producer)
+  if (issuer)
     for (int j = 0; j < min(D, nrows); ++j) issue(j);
   int issued = min(D, nrows);
 
   // x ring: only the component that streams into the tile, from the x split
-  for (int t = tid; t < 2 * h && consumer; t += TX) {
+  for (int t = tid; t < 2 * h; t += TX) {
     const int side = t >= h;
     const int r = side ? t - h : t;
     const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
     const size_t idx = (size_t)(y0 + r) * pitch + xr;
     R o[5][P];
-    if (!side) {
-      collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
+    collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
 #pragma unroll
-      for (int i = 0; i < P; ++i) ringL[i * TY + r] = o[0][i];
-    } else {
-      collide_d2q5<Sys, T, R, C_Q2>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-      for (int i = 0; i < P; ++i) ringR[i * TY + r] = o[1][i];
+    for (int i = 0; i < P; ++i) {
+      if (side)
+        ringR[i * TY + r] = o[1][i];
+      else
+        ringL[i * TY + r] = o[0][i];
     }
   }
+  if (tid == 0 && !mbar_wait_bounded(&bars[0], 0u)) *abort_flag = 1;
+  __syncthreads();   // row 0 and the ring published
+  bool aborted = *abort_flag != 0;
+  int waiting = 0;   // first row whose copies may still be in flight
 
   R fbp[P], f3c[P], fbc[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
-  bool ok = true;
-  if (consumer) {
-    ok = mbar_wait_bounded(&bars[0], 0u);
-    if (ok && act) {
-      R o[5][P];
-      if (up) {
-        collide_d2q5<Sys, T, R, C_Q4>(sys, stage_of(0), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-        for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
-      } else {
-        collide_d2q5<Sys, T, R, C_Q5>(sys, stage_of(0), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-        for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
-      }
-    }
-    ok = ok && mbar_wait_bounded(&bars[1 % D], (uint32_t)((1 / D) & 1));
-    if (ok && act) {
-      R o[5][P];
-      collide_d2q5<Sys, T, R, C_FULL>(sys, stage_of(1), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        rb1[i * TX + tid] = o[0][i];
-        rb2[i * TX + tid] = o[1][i];
-        f3c[i] = o[2][i];
-        fbc[i] = up ? o[3][i] : o[4][i];
-      }
-    }
-  }
-  if (!ok) *abort_flag = 1;
-  __syncthreads();
-  bool aborted = *abort_flag != 0;
-  int pending_from = 0;    // first stream row not yet consumed by every thread
-  if (!aborted) {
-    pending_from = 2;
-    for (int j = issued; j < min(2 + D, nrows); ++j)
-      if (producer) issue(j);
-    issued = min(2 + D, nrows);
-  }
-
   R m1 = R(0), m2 = R(0);
   bool bad = false;
-  for (int r = 0; r < h && !aborted; ++r) {
-    const int j = r + 2;                 // stream row collided now
-    const bool full = r + 1 < h;
-    const int nb = (r + 1) % 3, cb = r % 3;
-    R fan[P], f3n[P], fbn[P];
-#pragma unroll
-    for (int i = 0; i < P; ++i) fan[i] = f3n[i] = fbn[i] = R(0);
-    if (consumer) {
-      ok = mbar_wait_bounded(&bars[j % D], (uint32_t)((j / D) & 1));
-      if (ok && act) {
-        R o[5][P];
-        if (full) {
-          collide_d2q5<Sys, T, R, C_FULL>(sys, stage_of(j), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            rb1[(nb * P + i) * TX + tid] = o[0][i];
-            rb2[(nb * P + i) * TX + tid] = o[1][i];
-            f3n[i] = o[2][i];
-            fbn[i] = up ? o[3][i] : o[4][i];
-            fan[i] = up ? o[4][i] : o[3][i];
-          }
-        } else if (up) {
-          collide_d2q5<Sys, T, R, C_Q5>(sys, stage_of(j), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-          for (int i = 0; i < P; ++i) fan[i] = o[4][i];
-        } else {
-          collide_d2q5<Sys, T, R, C_Q4>(sys, stage_of(j), (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-          for (int i = 0; i < P; ++i) fan[i] = o[3][i];
-        }
-      }
-    }
-    if (!ok) *abort_flag = 1;
-    __syncthreads();
-    aborted = *abort_flag != 0;
-    if (aborted) break;
-    pending_from = j + 1;
-    if (j + D < nrows) {
-      if (producer) issue(j + D);
-      issued = j + D + 1;
-    }
+  for (int j = 0; j < nrows && !aborted; ++j) {
+    const T* st = stages + (size_t)(j % D) * L.stage_elems;
     if (act) {
-      const int yo = row_y(r + 1);
-      const int rt = yo - y0;
-      const size_t base = (size_t)yo * pitch + x;
-      R U[P];
+      R o[5][P];
+      if (j == 0) {
+        if (up)
+          collide_d2q5<Sys, T, R, C_Q4>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+        else
+          collide_d2q5<Sys, T, R, C_Q5>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+      } else if (j <= h) {
+        collide_d2q5<Sys, T, R, C_FULL>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+        const int nb = (j - 1) & 1;
 #pragma unroll
-      for (int i = 0; i < P; ++i) {
-        R g[5];
-        g[0] = tid == 0 ? ringL[i * TY + rt] : rb1[(cb * P + i) * TX + tid - 1];
-        g[1] = tid == w - 1 ? ringR[i * TY + rt] : rb2[(cb * P + i) * TX + tid + 1];
-        g[2] = f3c[i];
-        g[3] = up ? fbp[i] : fan[i];
-        g[4] = up ? fan[i] : fbp[i];
-        const T* tp = nullptr;
-        R acc = R(0);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          Store<T>::st(fout + (size_t)(q * P + i) * plane + base, g[q]);
-          acc += round_store(g[q], tp);
+        for (int i = 0; i < P; ++i) {
+          rb1[(nb * P + i) * TX + tid] = o[0][i];
+          rb2[(nb * P + i) * TX + tid] = o[1][i];
         }
-        U[i] = acc;
+      } else if (up) {
+        collide_d2q5<Sys, T, R, C_Q5>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+      } else {
+        collide_d2q5<Sys, T, R, C_Q4>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
       }
-      R e1, e2;
-      bad |= !sys.epilogue(U, e1, e2);
-      m1 = vmax(m1, e1);
-      m2 = vmax(m2, e2);
-    }
+      if (j >= 2) {   // stream row j - 1 (a tile row) is complete
+        const int yo = row_y(j - 1);
+        const int rt = yo - y0;
+        const int cb = (j - 2) & 1;
+        const size_t base = (size_t)yo * pitch + x;
+        R U[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-      fbp[i] = fbc[i];
-      f3c[i] = f3n[i];
-      fbc[i] = fbn[i];
+        for (int i = 0; i < P; ++i) {
+          R g[5];
+          g[0] = tid == 0 ? ringL[i * TY + rt] : rb1[(cb * P + i) * TX + tid - 1];
+          g[1] = tid == w - 1 ? ringR[i * TY + rt] : rb2[(cb * P + i) * TX + tid + 1];
+          g[2] = f3c[i];
+          g[3] = up ? fbp[i] : o[3][i];
+          g[4] = up ? o[4][i] : fbp[i];
+          const T* tp = nullptr;
+          R acc = R(0);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            Store<T>::st(fout + (size_t)(q * P + i) * plane + base, g[q]);
+            acc += round_store(g[q], tp);
+          }
+          U[i] = acc;
+        }
+        R e1, e2;
+        bad |= !sys.epilogue(U, e1, e2);
+        m1 = vmax(m1, e1);
+        m2 = vmax(m2, e2);
+      }
+      if (j <= h) {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          fbp[i] = fbc[i];
+          fbc[i] = up ? o[3][i] : o[4][i];
+          if (j > 0) f3c[i] = o[2][i];   // (row 0 is a ring row: its collision has no f*_3)
+        }
+      }
+    }
+    if (tid == 0 && j + 1 < nrows && !mbar_wait_bounded(&bars[(j + 1) % D], (uint32_t)(((j + 1) / D) & 1)))
+      *abort_flag = 1;
+    __syncthreads();   // row j consumed; row j + 1 and the exchange buffer of row j published
+    aborted = *abort_flag != 0;
+    waiting = j + 1;
+    if (!aborted && j + D < nrows) {
+      if (issuer) issue(j + D);
+      issued = j + D + 1;
     }
   }
   if (aborted) {
     // a wait gave up: report it and let the copies still in flight land first
-    if (tid == 0) atomicOr(&a.ctl->err, ERR_TIMEOUT);
-    if (producer && lane == 0) {
-      for (int j = pending_from; j < issued; ++j) mbar_wait_bounded(&bars[j % D], (uint32_t)((j / D) & 1));
+    if (tid == 0) {
+      atomicOr(&a.ctl->err, ERR_TIMEOUT);
+      for (int j = waiting; j < issued; ++j) mbar_wait_bounded(&bars[j % D], (uint32_t)((j / D) & 1));
     }
     __syncthreads();
     return;

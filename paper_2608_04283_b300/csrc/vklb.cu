@@ -160,7 +160,7 @@ struct Impl {
       for (int64_t i = 0; i < n; ++i) {
         StepArgs<T> a = make_args<T>(s, t_end);
         if (s->variant == 1)
-          step2d_tma_kernel<Sys, T, R><<<grid, TX + 32, sm, s->stream>>>(a, TX, TY, D);
+          step2d_tma_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY, D);
         else if (bounded(TX))
           step2d_lb_kernel<Sys, T, R, kMinBlocks><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         else
@@ -200,7 +200,7 @@ struct Impl {
       int nb = 0;
       cudaError_t e;
       if (variant == 1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_tma_kernel<Sys, T, R>, tx + 32, sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_tma_kernel<Sys, T, R>, tx, sm);
       else if (bounded(tx))
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_lb_kernel<Sys, T, R, kMinBlocks>, tx, sm);
       else
@@ -241,7 +241,7 @@ struct BatchImpl {
     const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(b->variant, TX, TY, D);
     for (int64_t i = 0; i < n; ++i) {
       if (b->variant == 1)
-        step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX + 32, sm, b->own>>>(
+        step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
       else
         step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(
@@ -259,7 +259,7 @@ struct BatchImpl {
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       int nb = 0;
       cudaError_t e = variant == 1
-                          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx + 32, sm)
+                          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx, sm)
                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 0>, tx, sm);
       if (e != cudaSuccess) {
         cudaGetLastError();
