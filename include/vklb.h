@@ -124,7 +124,7 @@ typedef struct {
   int32_t tile_x, tile_y;    /* launch shape of the step kernel */
   int32_t kernels_per_step;  /* kernel launches one vklb_step(1) makes */
   int32_t variant;           /* step kernel: 0 plain loads, 1 bulk-copy (TMA) row pipeline */
-  int64_t pitch;             /* elements per row of a device distribution plane (>= nx) */
+  int64_t pitch;             /* cells per padded row of the device layout (>= nx; 2D: a multiple of 32) */
   int32_t blocks_per_sm;     /* 2D: resident blocks per SM of the step kernel at this launch shape
                                 (CUDA occupancy calculator); 1D: 0 */
   int32_t sms;               /* SMs of the current device */
@@ -191,9 +191,12 @@ int vklb_time(vklb_sim* sim, double* t, int64_t* steps, double* xi);
 
 int vklb_info(const vklb_sim* sim, vklb_info_t* info);
 
-/* Device pointer of the current distribution buffer, laid out
- * f[(q * p + k) * ny * pitch + y * pitch + x] in the store type of the
- * precision (pitch from vklb_info).  Borrowed; valid until the next vklb_step. */
+/* Device pointer of the current distribution buffer in the store type of the
+ * precision, pitch from vklb_info.  D1Q3: component planes,
+ * f[(q * p + k) * pitch + x].  D2Q5: 32-cell bricks, component j = q * p + k of
+ * cell (x, y) at f[((y * (pitch / 32) + x / 32) * 5 * p + j) * 32 + x % 32] (a
+ * row of bricks holds all components of 32 neighbouring cells contiguously).
+ * Borrowed; valid until the next vklb_step. */
 int vklb_device_state(const vklb_sim* sim, void** f_dev);
 
 /* Checkpoint / resume: the blob holds the distributions and the control words
@@ -226,7 +229,7 @@ int vklb_batch_destroy(vklb_batch* b);
  * device pointers from another runtime or runs where allocation is forbidden).
  * f_dev: a distribution buffer in the layout of vklb_device_state, store type
  * of `precision`, q in {3, 5}, p <= 16 fields (else VKLB_ERR_LIMIT), nx x ny
- * cells with row pitch `pitch` >= nx.  totals[k] = cell_volume * sum_x sum_q f,
+ * cells with row pitch `pitch` >= nx (a multiple of 32 for q = 5).  totals[k] = cell_volume * sum_x sum_q f,
  * FP64, same reduction order as vklb_conservation_totals; `totals` is a host
  * pointer (the call synchronises the stream) or, with totals_on_device != 0, a
  * device pointer (the call returns after enqueueing).  The partial sums live in

@@ -52,7 +52,7 @@ struct StepArgs {
   T* f[2];         // ping-pong distribution buffers
   int parity;      // f[parity] holds f^n
   int nx, ny;
-  int pitch;       // elements per row of a distribution plane (>= nx; plane = pitch * ny)
+  int pitch;       // cells per padded row (a multiple of 32 in 2D: pitch / 32 bricks per row)
   double dx, c, omega, k, inv_nu, fixed_xi, t_end, ch_factor;
   int set;
   int bc_lo, bc_hi;  // 1D: 0 periodic, 1 characteristic
@@ -60,6 +60,23 @@ struct StepArgs {
   int slot;        // n % 3
   SysParams sp;
 };
+
+// 2D distribution layout: 32-cell bricks.  Component k = q p + i of cell (x, y)
+// is f[((y nxb + x / 32) 5p + k) 32 + x % 32], nxb = pitch / 32: a warp's access
+// to one component of 32 neighbouring cells is one contiguous 32-element run,
+// the 5p components of a brick follow each other (component stride kBrick, a
+// compile-time immediate offset), and a tile row of whole bricks is one
+// contiguous range.  1D grids keep component planes f[k nx + x].
+constexpr int kBrick = 32;
+VK_HD size_t brick_base(int x, int y, int nxb, int npl) {
+  return ((((size_t)y * nxb + (x >> 5)) * npl) << 5) + (x & 31);
+}
+// Offset of component 0 of cell (x, y) and the stride between components, for
+// either lattice (Q = 5: bricks; Q = 3: planes of pitch x ny).
+VK_HD size_t cell_base(int Q, int P, int x, int y, int pitch) {
+  return Q == 5 ? brick_base(x, y, pitch / kBrick, Q * P) : (size_t)y * pitch + x;
+}
+VK_HD size_t comp_stride(int Q, int pitch, int ny) { return Q == 5 ? (size_t)kBrick : (size_t)pitch * ny; }
 
 // Which post-collision components a cell must produce.
 enum CollideMode { C_FULL = 0, C_Q1 = 1, C_Q2 = 2, C_Q4 = 3, C_Q5 = 4 };
@@ -234,8 +251,9 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);
   const int x = x0 + tx;
   const bool act = tx < w;
-  const int pitch = a.pitch;
-  const size_t plane = (size_t)pitch * ny;
+  constexpr int NPL = 5 * P;
+  constexpr size_t plane = kBrick;   // component stride in the brick layout
+  const int nxb = a.pitch / kBrick;
   const T* __restrict__ fin = a.f[a.parity];
   T* __restrict__ fout = a.f[a.parity ^ 1];
   const int s1 = (a.slot + 1) % 3;
@@ -253,7 +271,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     const int side = t >= h;
     const int r = side ? t - h : t;
     const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
-    const size_t idx = (size_t)(y0 + r) * pitch + xr;
+    const size_t idx = brick_base(xr, y0 + r, nxb, NPL);
     R o[5][P];
     if (!side) {
       collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
@@ -272,17 +290,18 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   if (act) {
     R o[5][P];
     if (up) {
-      collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)((y0 - 1 + ny) % ny) * pitch + x, xinv, c, om, set, kk,
-                                    ch, o);
+      collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, brick_base(x, (y0 - 1 + ny) % ny, nxb, NPL), xinv, c, om, set,
+                                    kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
     } else {
-      collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)((y0 + h) % ny) * pitch + x, xinv, c, om, set, kk, ch,
-                                    o);
+      collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, brick_base(x, (y0 + h) % ny, nxb, NPL), xinv, c, om, set, kk,
+                                    ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
     }
-    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(0) * pitch + x, xinv, c, om, set, kk, ch, o);
+    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, brick_base(x, row_of(0), nxb, NPL), xinv, c, om, set, kk, ch,
+                                    o);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       rb1[i * TX + tx] = o[0][i];
@@ -301,8 +320,8 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     if (act) {
       R o[5][P];
       if (r + 1 < h) {
-        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, (size_t)row_of(r + 1) * pitch + x, xinv, c, om, set, kk,
-                                        ch, o);
+        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, brick_base(x, row_of(r + 1), nxb, NPL), xinv, c, om, set,
+                                        kk, ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
           rb1[(nb * P + i) * TX + tx] = o[0][i];
@@ -313,13 +332,13 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
         }
       } else {
         if (up) {
-          collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, (size_t)((y0 + h) % ny) * pitch + x, xinv, c, om, set, kk,
-                                        ch, o);
+          collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, brick_base(x, (y0 + h) % ny, nxb, NPL), xinv, c, om, set,
+                                        kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[4][i];
         } else {
-          collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, (size_t)((y0 - 1 + ny) % ny) * pitch + x, xinv, c, om, set,
-                                        kk, ch, o);
+          collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, brick_base(x, (y0 - 1 + ny) % ny, nxb, NPL), xinv, c, om,
+                                        set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[3][i];
         }
@@ -329,7 +348,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     }
     __syncthreads();
     if (act) {
-      const size_t base = (size_t)j * pitch + x;
+      const size_t base = brick_base(x, j, nxb, NPL);
       const int rt = j - y0;
       R U[P];
 #pragma unroll
@@ -383,11 +402,10 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     // t_end already reached: this launch is a no-op that keeps the ping-pong
     // consistent (f^{n+1} = f^n, same control words).
     const int w = min(TX, a.nx - x0), h = min(TY, a.ny - y0);
-    const size_t plane = (size_t)a.pitch * a.ny;
     if (tx < w)
       for (int r = 0; r < h; ++r)
         for (int i = 0; i < 5 * P; ++i) {
-          size_t o = (size_t)i * plane + (size_t)(y0 + r) * a.pitch + x0 + tx;
+          const size_t o = brick_base(x0 + tx, y0 + r, a.pitch / kBrick, 5 * P) + (size_t)i * kBrick;
           a.f[a.parity ^ 1][o] = a.f[a.parity][o];
         }
     if (bx == 0 && by == 0 && tx == 0) {
@@ -413,9 +431,9 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
 
 // ------------------------------------------------- D2Q5 step, bulk-copy rows
 // Same arithmetic as step2d_tile, but the rows of f^n reach the block through
-// shared memory by 1D bulk asynchronous copies (cp.async.bulk, the TMA engine),
-// one per distribution plane's row segment [x0, x0 + TX), D rows ahead, each
-// stage completing on its own mbarrier.  There is one block barrier per row, as
+// shared memory by 1D bulk asynchronous copies (cp.async.bulk, the TMA engine):
+// in the brick layout a tile row is one contiguous range, so one copy per row,
+// D rows ahead, each stage completing on its own mbarrier.  There is one block barrier per row, as
 // in the plain march: before it, thread 0 waits for the next row's copies, so
 // the barrier also publishes that row to the block; after it, the lanes of warp
 // 0 refill the stage just consumed.  Every mbarrier wait is bounded; a wait that
@@ -467,7 +485,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 template <class T>
 struct TmaLayout {
   int TX, TY, D;
-  size_t stage_elems;       // elements of one stage (5 p planes x TX)
+  size_t stage_elems;       // elements of one stage (TX / 32 bricks of 5p x 32)
   size_t off_stage, off_rb, off_ring, bytes;
   template <class R, int P>
   VK_HD static TmaLayout make(int TX, int TY, int D) {
@@ -498,15 +516,14 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
   constexpr int NPL = 5 * P;
   const TmaLayout<T> L = TmaLayout<T>::template make<R, P>(TX, TY, D);
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const bool issuer = tid < 32;
   const int x0 = bx * TX, y0 = by * TY;
-  const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+  const int nx = a.nx, ny = a.ny;
+  const int nxb = a.pitch / kBrick;
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);
   const int x = x0 + tid;
   const bool act = tid < w;
   const bool up = (by & 1) == 0;
-  const size_t plane = (size_t)pitch * ny;
+  constexpr size_t plane = kBrick;   // component stride in the brick layout
   const T* __restrict__ fin = a.f[a.parity];
   T* __restrict__ fout = a.f[a.parity ^ 1];
   __shared__ StepScalars s_sc;
@@ -521,7 +538,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     if (act)
       for (int r = 0; r < h; ++r)
         for (int i = 0; i < NPL; ++i) {
-          size_t o = (size_t)i * plane + (size_t)(y0 + r) * pitch + x;
+          const size_t o = brick_base(x, y0 + r, nxb, NPL) + (size_t)i * kBrick;
           fout[o] = fin[o];
         }
     if (bx == 0 && by == 0 && tid == 0) {
@@ -548,21 +565,19 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_ring + 2 * P * TY * sizeof(R));
 
   const int nrows = h + 2;
-  const uint32_t main_bytes = (uint32_t)((((size_t)w * sizeof(T)) + 15) & ~(size_t)15);
+  // whole bricks of the tile row: (w + 31) / 32 of 5p x 32 elements
+  const uint32_t row_bytes = (uint32_t)((size_t)((w + kBrick - 1) / kBrick) * NPL * kBrick * sizeof(T));
   auto row_y = [&](int j) -> int {
     if (j == 0) return up ? (y0 - 1 + ny) % ny : (y0 + h) % ny;
     if (j == nrows - 1) return up ? (y0 + h) % ny : (y0 - 1 + ny) % ny;
     return up ? y0 + j - 1 : y0 + h - j;
   };
-  // warp 0: stream row j into stage j % D, one copy per plane
+  // thread 0: stream row j into stage j % D, one copy
   auto issue = [&](int j) {
     const int s = j % D;
-    T* st = stages + (size_t)s * L.stage_elems;
-    const T* src = fin + (size_t)row_y(j) * pitch + x0;
     fence_proxy_async_smem();
-    if (lane == 0) mbar_arrive_expect_tx(&bars[s], (uint32_t)NPL * main_bytes);
-    __syncwarp();
-    for (int i = lane; i < NPL; i += 32) bulk_g2s(st + (size_t)i * TX, src + (size_t)i * plane, main_bytes, &bars[s]);
+    mbar_arrive_expect_tx(&bars[s], row_bytes);
+    bulk_g2s(stages + (size_t)s * L.stage_elems, fin + brick_base(x0, row_y(j), nxb, NPL), row_bytes, &bars[s]);
   };
 
   if (tid == 0) {
@@ -571,7 +586,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     *abort_flag = 0;
   }
   __syncthreads();
-  if (issuer)
+  if (tid == 0)
     for (int j = 0; j < min(D, nrows); ++j) issue(j);
   int issued = min(D, nrows);
 
@@ -580,7 +595,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     const int side = t >= h;
     const int r = side ? t - h : t;
     const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
-    const size_t idx = (size_t)(y0 + r) * pitch + xr;
+    const size_t idx = brick_base(xr, y0 + r, nxb, NPL);
     R o[5][P];
     collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
 #pragma unroll
@@ -601,17 +616,18 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
   for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
   R m1 = R(0), m2 = R(0);
   bool bad = false;
+  const size_t sidx = (size_t)(tid >> 5) * NPL * kBrick + (tid & 31);   // this column in a stage
   for (int j = 0; j < nrows && !aborted; ++j) {
     const T* st = stages + (size_t)(j % D) * L.stage_elems;
     if (act) {
       R o[5][P];
       if (j == 0) {
         if (up)
-          collide_d2q5<Sys, T, R, C_Q4>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+          collide_d2q5<Sys, T, R, C_Q4>(sys, st, plane, sidx, xinv, c, om, set, kk, ch, o);
         else
-          collide_d2q5<Sys, T, R, C_Q5>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+          collide_d2q5<Sys, T, R, C_Q5>(sys, st, plane, sidx, xinv, c, om, set, kk, ch, o);
       } else if (j <= h) {
-        collide_d2q5<Sys, T, R, C_FULL>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+        collide_d2q5<Sys, T, R, C_FULL>(sys, st, plane, sidx, xinv, c, om, set, kk, ch, o);
         const int nb = (j - 1) & 1;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
@@ -619,15 +635,15 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
           rb2[(nb * P + i) * TX + tid] = o[1][i];
         }
       } else if (up) {
-        collide_d2q5<Sys, T, R, C_Q5>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+        collide_d2q5<Sys, T, R, C_Q5>(sys, st, plane, sidx, xinv, c, om, set, kk, ch, o);
       } else {
-        collide_d2q5<Sys, T, R, C_Q4>(sys, st, (size_t)TX, (size_t)tid, xinv, c, om, set, kk, ch, o);
+        collide_d2q5<Sys, T, R, C_Q4>(sys, st, plane, sidx, xinv, c, om, set, kk, ch, o);
       }
       if (j >= 2) {   // stream row j - 1 (a tile row) is complete
         const int yo = row_y(j - 1);
         const int rt = yo - y0;
         const int cb = (j - 2) & 1;
-        const size_t base = (size_t)yo * pitch + x;
+        const size_t base = brick_base(x, yo, nxb, NPL);
         R U[P];
 #pragma unroll
         for (int i = 0; i < P; ++i) {
@@ -666,7 +682,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     aborted = *abort_flag != 0;
     waiting = j + 1;
     if (!aborted && j + D < nrows) {
-      if (issuer) issue(j + D);
+      if (tid == 0) issue(j + D);
       issued = j + D + 1;
     }
   }
@@ -901,7 +917,7 @@ __global__ void init_max_kernel(const double* __restrict__ U, size_t cells, SysP
 }
 
 // f_q = f_q^eq(U) (Eq. 2b) with xi_0, c_h^0 from slot 0.  U is dense [p][ny][nx];
-// f is pitched [q][p][ny][pitch].
+// f in the lattice's layout (cell_base / comp_stride).
 template <class Sys, class T, class R, int DIM>
 __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, StepArgs<T> a) {
   constexpr int P = Sys::P;
@@ -909,10 +925,11 @@ __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, Step
   const StepScalars sc = step_scalars(a.ctl, 0, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, -1.0, a.dx);
   const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, kk = (R)a.k;
   T* f = a.f[a.parity];
-  const size_t plane = (size_t)a.pitch * a.ny;
+  constexpr int Q = DIM == 1 ? 3 : 5;
+  const size_t plane = comp_stride(Q, a.pitch, a.ny);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
     const size_t y = i / a.nx, x = i - y * a.nx;
-    const size_t o = y * a.pitch + x;
+    const size_t o = cell_base(Q, P, (int)x, (int)y, a.pitch);
     R u[P];
 #pragma unroll
     for (int s = 0; s < P; ++s) u[s] = (R)U[s * cells + i];
@@ -946,13 +963,13 @@ __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, Step
   }
 }
 
-// U_k = sum_q f_q,k (Eq. 3), as double, dense [p][ny][nx] from pitched f.
+// U_k = sum_q f_q,k (Eq. 3), as double, dense [p][ny][nx] from f in the lattice's layout.
 template <class T, int P, int Q>
 __global__ void moments_kernel(const T* __restrict__ f, int nx, int ny, int pitch, double* __restrict__ U) {
-  const size_t cells = (size_t)nx * ny, plane = (size_t)pitch * ny;
+  const size_t cells = (size_t)nx * ny, plane = comp_stride(Q, pitch, ny);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
     const size_t y = i / nx, x = i - y * nx;
-    const size_t o = y * pitch + x;
+    const size_t o = cell_base(Q, P, (int)x, (int)y, pitch);
 #pragma unroll
     for (int s = 0; s < P; ++s) {
       double acc = 0.0;
@@ -968,14 +985,14 @@ __global__ void moments_kernel(const T* __restrict__ f, int nx, int ny, int pitc
 template <class T, int P, int Q>
 __global__ void totals_pass1(const T* __restrict__ f, int nx, int ny, int pitch, double* __restrict__ part) {
   __shared__ double red[32];
-  const size_t cells = (size_t)nx * ny, plane = (size_t)pitch * ny;
+  const size_t cells = (size_t)nx * ny, plane = comp_stride(Q, pitch, ny);
   const size_t chunk = (cells + gridDim.x - 1) / gridDim.x;
   const size_t lo = blockIdx.x * chunk, hi = min(cells, lo + chunk);
   for (int s = 0; s < P; ++s) {
     double acc = 0.0;
     for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       const size_t y = i / nx, x = i - y * nx;
-      const size_t o = y * pitch + x;
+      const size_t o = cell_base(Q, P, (int)x, (int)y, pitch);
 #pragma unroll
       for (int q = 0; q < Q; ++q) acc += (double)Store<T>::ld(f + (size_t)(q * P + s) * plane + o);
     }

@@ -492,9 +492,9 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->nx = nx;
   s->ny = ny;
   s->cells = nx * ny;
-  // 2D rows are padded to 32 elements so that every row of a distribution
-  // plane starts on a 64-byte (bf16) / 128-byte (fp32) / 256-byte (fp64)
-  // boundary, as the bulk copies of the step kernel need.
+  // 2D rows are padded to whole 32-cell bricks (the D2Q5 layout, see
+  // brick_base): every brick starts on a 64-byte (bf16) / 128-byte (fp32) /
+  // 256-byte (fp64) boundary, as coalescing and the bulk copies need.
   s->pitch = dim == 2 ? ((nx + 31) / 32) * 32 : nx;
   s->dx = dx;
   s->ch_factor = sys->ch_factor;
@@ -902,14 +902,14 @@ template <class T>
 __global__ void totals_pass1_rt(const T* __restrict__ f, int p, int q, int nx, int ny, int pitch,
                                 double* __restrict__ part) {
   __shared__ double red[32];
-  const size_t cells = (size_t)nx * ny, plane = (size_t)pitch * ny;
+  const size_t cells = (size_t)nx * ny, plane = comp_stride(q, pitch, ny);
   const size_t chunk = (cells + gridDim.x - 1) / gridDim.x;
   const size_t lo = blockIdx.x * chunk, hi = min(cells, lo + chunk);
   for (int s = 0; s < p; ++s) {
     double acc = 0.0;
     for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       const size_t y = i / nx, x = i - y * nx;
-      const size_t o = y * pitch + x;
+      const size_t o = cell_base(q, p, (int)x, (int)y, pitch);
       for (int k = 0; k < q; ++k) acc += (double)Store<T>::ld(f + (size_t)(k * p + s) * plane + o);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -942,6 +942,7 @@ int vklb_conservation_totals_noalloc(const void* f_dev, int32_t precision, int32
   if (!f_dev || !totals) return VKLB_ERR_ARG;
   if (precision < VKLB_FP64 || precision > VKLB_BF16_STORE || (q != 3 && q != 5)) return VKLB_ERR_ARG;
   if (nx < 1 || ny < 1 || pitch < nx || nx > (1 << 30) || ny > (1 << 30) || pitch > (1 << 30)) return VKLB_ERR_ARG;
+  if (q == 5 && pitch % 32 != 0) return VKLB_ERR_ARG;   // whole bricks per row
   if (p < 1 || p > kNoAllocMaxFields) return VKLB_ERR_LIMIT;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return VKLB_ERR_CUDA;
