@@ -71,9 +71,38 @@ def tiling_for(system, precision, n):
     return tuple(ent[best])
 
 
-def step_kernel_name(system, prec, tile_x):
-    """The step kernel the library launches: FP32-compute MHD-GLM with blocks of
-    at most 128 threads takes the register-bounded instantiation."""
+def launch_shape(system, precision, n):
+    """(tile, (variant, stages)) the autotuner measured best for the nearest grid
+    side, or None for the library's defaults."""
+    tile = tiling_for(system, precision, n)
+    if tile is None:
+        return None
+    tab = json.load(open(os.path.join(ROOT, "paper_2608_04283_b300", "tuning.json")))
+    var = (0, 0)
+    vt = {k: v for k, v in tab.get("_variants", {}).items() if k.startswith(f"{system}/{precision}/")}
+    if vt:
+        side = max(n)
+        best = min(vt.keys(), key=lambda k: abs(int(k.rsplit("/", 1)[1]) - side))
+        if int(best.rsplit("/", 1)[1]) == int(min(tab[f"{system}/{precision}"].keys(), key=lambda k: abs(int(k) - side))):
+            var = tuple(vt[best])
+    return tile, var
+
+
+def configure(sim, shape):
+    if shape is None:
+        return
+    tile, var = shape
+    sim.set_tiling(32, 8)          # a shape every variant accepts
+    sim.set_variant(*var)
+    sim.set_tiling(*tile)          # the wave-fit height depends on the variant
+
+
+def step_kernel_name(system, prec, tile_x, variant):
+    """The step kernel the library launches: the bulk-copy variant, or the plain
+    one, which FP32-compute MHD-GLM with blocks of at most 128 threads takes in
+    its register-bounded instantiation."""
+    if variant == 1:
+        return "step2d_tma_kernel"
     return "step2d_lb_kernel" if system == "mhd_glm" and prec != "fp64" and tile_x <= 128 else "step2d_kernel"
 
 
@@ -259,9 +288,8 @@ def run_ours(args, wl):
     prec = args.precision
     stream = torch.cuda.Stream()
     sim = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, stream=stream, **wl["kw"])
-    tile = tiling_for(wl["system"], prec, wl["n"])
-    if tile:
-        sim.set_tiling(*tile)
+    tile = launch_shape(wl["system"], prec, wl["n"])
+    configure(sim, tile)
     U0 = wl["ic"]()
     U0_dev = torch.from_numpy(U0).cuda()
     flush_buf = L2Flush(torch)
@@ -288,11 +316,12 @@ def run_ours(args, wl):
     mean_ms = total_ms / args.steps
     achieved = bpl * cells / (mean_ms * 1e-3) / 1e9
     peaks, peak_src = measured_peaks()
-    key = f"step2d/{wl['system']}/{prec}/{wl['n'][0]}x{wl['n'][1]}/{sim.info.tile_x}x{sim.info.tile_y}"
+    kname = step_kernel_name(wl["system"], prec, sim.info.tile_x, sim.info.variant)
+    key = f"{kname}/{wl['system']}/{prec}/{wl['n'][0]}x{wl['n'][1]}/{sim.info.tile_x}x{sim.info.tile_y}"
     traffic = traffic_record(key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_src + " (burst)",
-                "algorithmic_bytes_per_lup": bpl, "kernel": step_kernel_name(wl["system"], prec, sim.info.tile_x)}
+                "algorithmic_bytes_per_lup": bpl, "kernel": kname}
 
     extras = {}
     acc = None
@@ -317,6 +346,7 @@ def run_ours(args, wl):
                 "data": "synthetic",
                 "config": {"workload": args.workload, "description": wl["name"], "cells": cells,
                            "precision": prec, "tile": [sim.info.tile_x, sim.info.tile_y],
+                           "variant": sim.info.variant,
                            "l2": "flushed before every timed step: 256 MiB write, then 256 MiB read of another buffer",
                            "reinit_every": REINIT_EVERY, "parallelism": "replicas" if world > 1 else "single"},
                 "hbm_gbs": achieved, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -341,8 +371,8 @@ def accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps):
     res = []
     for p in (prec, "fp64"):
         s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=p, **wl["kw"])
-        if tile and p == prec:
-            s.set_tiling(*tile)
+        if p == prec:
+            configure(s, tile)
         s.set_state(U0)
         s.step(steps)
         res.append(s.moments())
@@ -374,8 +404,7 @@ def end_to_end(torch, vklb, wl, prec, tile, steps, U0):
     host_in[...] = U0
     host_out = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True).numpy()
     s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, **wl["kw"])
-    if tile:
-        s.set_tiling(*tile)
+    configure(s, tile)
     s.set_state(host_in)
     s.step(2)
     s.moments(out=host_out)
@@ -396,9 +425,7 @@ def end_to_end(torch, vklb, wl, prec, tile, steps, U0):
 def secondary(torch, vklb, wl, prec, flush_buf, steps):
     stream = torch.cuda.Stream()
     s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, stream=stream, **wl["kw"])
-    tile = tiling_for(wl["system"], prec, wl["n"])
-    if tile:
-        s.set_tiling(*tile)
+    configure(s, launch_shape(wl["system"], prec, wl["n"]))
     U0 = torch.from_numpy(wl["ic"]()).cuda()
     durs = timed_steps(torch, s, stream, U0, steps, 5, flush_buf)
     cells = wl["n"][0] * wl["n"][1]
@@ -409,7 +436,7 @@ def secondary(torch, vklb, wl, prec, flush_buf, steps):
     s.close()
     return {"workload": wl["name"], "MLUPS": cells / (mean_ms * 1e-3) / 1e6, "ms_per_step": mean_ms,
             "hbm_gbs": gbs, "frac_of_peak": gbs / peaks["hbm_gbs"], "bytes_per_lup": bpl,
-            "tile": [s.info.tile_x, s.info.tile_y], "steps": steps}
+            "tile": [s.info.tile_x, s.info.tile_y], "variant": s.info.variant, "steps": steps}
 
 
 def batched_swe(torch, vklb, count=256, steps=500):

@@ -23,7 +23,7 @@ TABLE = os.path.join(HERE, "tuning.json")
 # (tx, -1): the height that fills whole waves of resident blocks
 TILES = [(32, 8), (32, 16), (64, 4), (64, 8), (64, 16), (64, 32), (128, 4), (128, 8), (128, 16), (128, 32),
          (128, 64), (256, 4), (256, 8), (64, -1), (128, -1), (256, -1)]
-VARIANTS = [(0, 0), (1, 2), (1, 3)]
+VARIANTS = [(0, 0), (1, 2), (1, 3), (1, 4)]
 
 
 def _state(system, n):
@@ -69,8 +69,11 @@ def write(system, precision, n, best):
     tab = json.load(open(TABLE))
     ent = tab.setdefault(f"{system}/{precision}", {})
     ent[str(n)] = best["tile"]
+    var = tab.setdefault("_variants", {})
     if best["variant"][0] != 0:
-        tab.setdefault("_variants", {})[f"{system}/{precision}/{n}"] = best["variant"]
+        var[f"{system}/{precision}/{n}"] = best["variant"]
+    else:
+        var.pop(f"{system}/{precision}/{n}", None)
     json.dump(tab, open(TABLE, "w"), indent=1)
 
 

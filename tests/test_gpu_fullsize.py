@@ -1,6 +1,6 @@
 """Parity at the benchmark's full size and launch shape: the 1024^2 Euler
-isentropic vortex (omega 2, CFL 0.3, c 0.05, k 2) with the tiling bench.py
-times (128 x 8, one wave of 1024 tiles), in FP32 and FP64.
+isentropic vortex (omega 2, CFL 0.3, c 0.05, k 2) in the launch shape bench.py
+times (the autotuned tile and kernel variant), in FP32 and FP64.
 
 The oracle cannot step 10^6 cells in seconds, but one step of the update at a
 cell depends only on its 5-point neighbourhood and on the global lattice speed
@@ -8,9 +8,9 @@ xi_0 = max|lambda(U_0)| / nu (Eq. 29).  So xi_0 is taken from the oracle's
 global maximum over the full grid, and each sampled cell is checked against an
 oracle run on the 5 x 5 periodic patch around it with xi fixed at xi_0: its
 centre after one step is exactly the full-grid result (pinned on the CPU by
-test_one_step_is_local_given_global_xi).  The samples include the edges of the
-128 x 8 tiles and of the periodic grid, where the kernel's recomputed ring
-cells and index wrap act.  A property that holds at any size (Thm 4.3's
+test_one_step_is_local_given_global_xi).  The samples include the edges of
+128-, 256- and 32-cell bricks and tiles, and of the periodic grid, where the
+kernel's recomputed ring cells and index wrap act.  A property that holds at any size (Thm 4.3's
 conservation on a periodic grid) is checked on the whole grid.
 """
 import os
@@ -44,15 +44,15 @@ def U0():
     return np.ascontiguousarray(inputs.isentropic_vortex(N))
 
 
-def _bench_tile():
+def _bench():
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
-    return bench.tiling_for("euler", "fp32", (N, N))
+    return bench
 
 
 def _samples():
     rng = np.random.default_rng(20)
-    edges = [0, 1, 127, 128, 129, 511, 512, N - 2, N - 1]
+    edges = [0, 1, 31, 32, 127, 128, 129, 255, 256, 511, 512, N - 2, N - 1]
     rows = [0, 1, 7, 8, 9, 15, 16, 511, 512, N - 8, N - 1]
     pts = [(x, y) for x in edges[::2] for y in rows[::2]]
     pts += [(int(x), int(y)) for x, y in rng.integers(0, N, size=(24, 2))]
@@ -78,11 +78,10 @@ def _oracle_at(U0, pts, xi0):
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-11)])
 def test_fullsize_one_step_sampled(vk, U0, precision, tol):
-    tile = _bench_tile()
-    assert tile == (128, 8)
+    bench = _bench()
+    shape = bench.launch_shape("euler", "fp32", (N, N))
     sim = vk.Sim("euler", (N, N), (0.0, 0.0), (L, L), precision=precision, **KW)
-    sim.set_tiling(*tile)
-    assert (sim.info.tile_x, sim.info.tile_y) == (128, 8)
+    bench.configure(sim, shape)
     sim.set_state(U0)
     sim.step(1)
     got = sim.moments()
@@ -107,7 +106,8 @@ def test_fullsize_conservation(vk, U0, precision, tol):
     """Thm 4.3: on the periodic grid the totals of rho, m and E do not change;
     20 steps at the bench's launch shape, FP64 totals of the stored f."""
     sim = vk.Sim("euler", (N, N), (0.0, 0.0), (L, L), precision=precision, **KW)
-    sim.set_tiling(*_bench_tile())
+    bench = _bench()
+    bench.configure(sim, bench.launch_shape("euler", "fp32", (N, N)))
     sim.set_state(U0)
     t0 = sim.totals()
     sim.step(20)
