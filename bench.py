@@ -169,6 +169,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_throughput(torch, local_ms, cells, steps, world, device):
+    """Whole-job MLUPS of `world` independent replicas (weak scaling: every rank
+    steps its own copy of the workload): the slowest rank's timed region, taken
+    by a MAX all-reduce, bounds the job.  Returns (MLUPS, max ms)."""
+    ms = float(local_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * cells * steps / (ms * 1e-3) / 1e6, ms
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -308,11 +320,7 @@ def run_ours(args, wl):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = float(durs.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * cells * args.steps / (total_ms * 1e-3) / 1e6
+    value, total_ms = replica_throughput(torch, total_ms, cells, args.steps, world, "cuda")
     mean_ms = total_ms / args.steps
     achieved = bpl * cells / (mean_ms * 1e-3) / 1e9
     peaks, peak_src = measured_peaks()
