@@ -128,6 +128,7 @@ typedef struct {
   int32_t blocks_per_sm;     /* 2D: resident blocks per SM of the step kernel at this launch shape
                                 (CUDA occupancy calculator); 1D: 0 */
   int32_t sms;               /* SMs of the current device */
+  int32_t form;              /* 0: distributions are the state; 1: moments (vklb_set_form) */
 } vklb_info_t;
 
 /* Create a simulation.  dt > 0 fixes xi = dx / dt for every step; dt <= 0
@@ -166,6 +167,23 @@ int vklb_set_tiling(vklb_sim* sim, int32_t tile_x, int32_t tile_y);
  * shared memory does not fit; ERR_UNSUPPORTED for variant 1 on a 1D grid. */
 int vklb_set_variant(vklb_sim* sim, int32_t variant, int32_t stages);
 
+/* State form.  0 (default): the 5p distributions of Eq. (38)-(43) are the
+ * state.  1 (D2Q5, omega == 1 only): the p moments U are the state.  At
+ * omega = 1 the collision (Eq. 42) leaves f* = f^eq(U) (Eq. 41), so the step
+ * is the finite-volume update of Thm 4.3, U^{n+1}(x) = sum_q f^eq_q(U^n(x - v_q)),
+ * and storing U moves 2p instead of 10p values a cell.  Both forms run the same
+ * march and the same arithmetic from U (form 0 relaxes to f^eq exactly at
+ * omega = 1), so form 1's U after every step equals the sum
+ * ((((f1 + f2) + f3) + f4) + f5) of form 0's stored distributions up to
+ * rounding (the compiler may fuse multiply-adds differently in the two
+ * kernels), not bit for bit.  The
+ * initial U is that sum of f^eq(U_0).  Reallocates the device buffers (p components a cell for form
+ * 1) and resets the launch shape to the default; the state must be set again
+ * (VKLB_ERR_STATE until then).  Errors: VKLB_ERR_ARG for omega != 1 or an
+ * unknown form; VKLB_ERR_UNSUPPORTED on a 1D grid or with the bulk-copy variant
+ * (which form 1 does not use); VKLB_ERR_NOMEM. */
+int vklb_set_form(vklb_sim* sim, int32_t form);
+
 /* Enqueue n steps of Fig. 5 (no host synchronisation). */
 int vklb_step(vklb_sim* sim, int64_t n);
 
@@ -196,11 +214,15 @@ int vklb_info(const vklb_sim* sim, vklb_info_t* info);
  * f[(q * p + k) * pitch + x].  D2Q5: 32-cell bricks, component j = q * p + k of
  * cell (x, y) at f[((y * (pitch / 32) + x / 32) * 5 * p + j) * 32 + x % 32] (a
  * row of bricks holds all components of 32 neighbouring cells contiguously).
+ * In the moment form (vklb_set_form) the buffer holds U instead, field k of
+ * cell (x, y) at f[((y * (pitch / 32) + x / 32) * p + k) * 32 + x % 32].
  * Borrowed; valid until the next vklb_step. */
 int vklb_device_state(const vklb_sim* sim, void** f_dev);
 
-/* Checkpoint / resume: the blob holds the distributions and the control words
- * (t, steps, xi, c_h).  vklb_state_bytes gives its size; get synchronises. */
+/* Checkpoint / resume: the blob holds the device state (distributions, or U in
+ * the moment form) and the control words (t, steps, xi, c_h).  A blob loads
+ * only into a simulation of the same system, grid, precision and form.
+ * vklb_state_bytes gives its size; get synchronises. */
 int vklb_state_bytes(const vklb_sim* sim, size_t* bytes);
 int vklb_get_state(vklb_sim* sim, void* blob, size_t bytes);
 int vklb_put_state(vklb_sim* sim, const void* blob, size_t bytes);
@@ -227,7 +249,7 @@ int vklb_batch_destroy(vklb_batch* b);
 /* Conservation totals that allocate nothing (the paper has no counterpart: this
  * serves callers that cannot call cudaMalloc, e.g. code that only receives
  * device pointers from another runtime or runs where allocation is forbidden).
- * f_dev: a distribution buffer in the layout of vklb_device_state, store type
+ * f_dev: a distribution buffer (form 0) in the layout of vklb_device_state, store type
  * of `precision`, q in {3, 5}, p <= 16 fields (else VKLB_ERR_LIMIT), nx x ny
  * cells with row pitch `pitch` >= nx (a multiple of 32 for q = 5).  totals[k] = cell_volume * sum_x sum_q f,
  * FP64, same reduction order as vklb_conservation_totals; `totals` is a host

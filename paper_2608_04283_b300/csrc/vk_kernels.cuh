@@ -71,19 +71,65 @@ constexpr int kBrick = 32;
 VK_HD size_t brick_base(int x, int y, int nxb, int npl) {
   return ((((size_t)y * nxb + (x >> 5)) * npl) << 5) + (x & 31);
 }
-// Offset of component 0 of cell (x, y) and the stride between components, for
-// either lattice (Q = 5: bricks; Q = 3: planes of pitch x ny).
+// Offset of component 0 of cell (x, y) and the stride between components of a
+// state with Q components a field: Q = 3 (D1Q3) planes of pitch x ny; Q = 5
+// (D2Q5 distributions) and Q = 1 (D2Q5 moment form) 32-cell bricks of Q p.
 VK_HD size_t cell_base(int Q, int P, int x, int y, int pitch) {
-  return Q == 5 ? brick_base(x, y, pitch / kBrick, Q * P) : (size_t)y * pitch + x;
+  return Q != 3 ? brick_base(x, y, pitch / kBrick, Q * P) : (size_t)y * pitch + x;
 }
-VK_HD size_t comp_stride(int Q, int pitch, int ny) { return Q == 5 ? (size_t)kBrick : (size_t)pitch * ny; }
+VK_HD size_t comp_stride(int Q, int pitch, int ny) { return Q != 3 ? (size_t)kBrick : (size_t)pitch * ny; }
 
 // Which post-collision components a cell must produce.
 enum CollideMode { C_FULL = 0, C_Q1 = 1, C_Q2 = 2, C_Q4 = 3, C_Q5 = 4 };
 
-// Collision (Eq. 42) of one D2Q5 cell with the weighted equilibria of Eq. (41):
-//   f1 = c U + F(1,+)/xi, f2 = c U - F(1,-)/xi, f4 = c U + F(2,+)/xi,
-//   f5 = c U - F(2,-)/xi, f3 = U - (f1 + f2 + f4 + f5) (= Eq. 41's rest term).
+// Weighted equilibria of Eq. (41) from U, the components MODE needs:
+//   e1 = c U + F(1,+)/xi, e2 = c U - F(1,-)/xi, e4 = c U + F(2,+)/xi,
+//   e5 = c U - F(2,-)/xi, e3 = U - (e1 + e2 + e4 + e5) (= Eq. 41's rest term).
+template <class Sys, class R, int MODE>
+__device__ __forceinline__ void equilibria_d2q5(const Sys& sys, const R (&U)[Sys::P], R xinv, R c, int set, R k,
+                                                R ch, R (&e)[5][Sys::P]) {
+  constexpr int P = Sys::P;
+  if (MODE == C_FULL) {
+    R Fp1[P], F1[P], Fp2[P], F2[P];
+    sys.split2(U, set, k, ch, Fp1, F1, Fp2, F2);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      const R cu = c * U[i];
+      e[0][i] = cu + Fp1[i] * xinv;
+      e[1][i] = cu - (F1[i] - Fp1[i]) * xinv;
+      e[3][i] = cu + Fp2[i] * xinv;
+      e[4][i] = cu - (F2[i] - Fp2[i]) * xinv;
+      e[2][i] = U[i] - ((e[0][i] + e[1][i]) + e[3][i] + e[4][i]);
+    }
+    return;
+  }
+  R Fp[P], F[P];
+  if (MODE == C_Q1 || MODE == C_Q2) {
+    sys.split(U, 0, set, k, ch, Fp, F);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      e[0][i] = c * U[i] + Fp[i] * xinv;
+      e[1][i] = c * U[i] - (F[i] - Fp[i]) * xinv;
+    }
+  } else {
+    sys.split(U, 1, set, k, ch, Fp, F);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      e[3][i] = c * U[i] + Fp[i] * xinv;
+      e[4][i] = c * U[i] - (F[i] - Fp[i]) * xinv;
+    }
+  }
+}
+
+// BGK relaxation, Eq. (42); at omega = 1 the post-collision state is the
+// equilibrium itself, taken exactly (as the moment form below takes it).
+template <class R>
+__device__ __forceinline__ R relax(R f, R e, R om) {
+  return om == R(1) ? e : f + om * (e - f);
+}
+
+// Collision (Eq. 42) of one D2Q5 cell: load f, U = sum_q f_q (Eq. 3), the
+// equilibria, relax.
 template <class Sys, class T, class R, int MODE>
 __device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict__ fin, size_t plane,
                                              size_t idx, R xinv, R c, R om, int set, R k, R ch,
@@ -97,49 +143,18 @@ __device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict
   R U[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
-  if (MODE == C_FULL) {
-    R Fp1[P], F1[P], Fp2[P], F2[P];
-    sys.split2(U, set, k, ch, Fp1, F1, Fp2, F2);
+  R e[5][P];
+  equilibria_d2q5<Sys, R, MODE>(sys, U, xinv, c, set, k, ch, e);
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-      const R cu = c * U[i];
-      const R e1 = cu + Fp1[i] * xinv;
-      const R e2 = cu - (F1[i] - Fp1[i]) * xinv;
-      const R e4 = cu + Fp2[i] * xinv;
-      const R e5 = cu - (F2[i] - Fp2[i]) * xinv;
-      const R e3 = U[i] - ((e1 + e2) + e4 + e5);
-      out[0][i] = f[0][i] + om * (e1 - f[0][i]);
-      out[1][i] = f[1][i] + om * (e2 - f[1][i]);
-      out[2][i] = f[2][i] + om * (e3 - f[2][i]);
-      out[3][i] = f[3][i] + om * (e4 - f[3][i]);
-      out[4][i] = f[4][i] + om * (e5 - f[4][i]);
+  for (int i = 0; i < P; ++i) {
+    if (MODE == C_FULL || MODE == C_Q1 || MODE == C_Q2) {
+      out[0][i] = relax(f[0][i], e[0][i], om);
+      out[1][i] = relax(f[1][i], e[1][i], om);
     }
-    return;
-  }
-  R Fp[P], F[P];
-  if (MODE == C_Q1 || MODE == C_Q2) {
-    sys.split(U, 0, set, k, ch, Fp, F);
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      R e1 = c * U[i] + Fp[i] * xinv;
-      R e2 = c * U[i] - (F[i] - Fp[i]) * xinv;
-      out[0][i] = f[0][i] + om * (e1 - f[0][i]);
-      out[1][i] = f[1][i] + om * (e2 - f[1][i]);
-      if (MODE == C_FULL) out[2][i] = e1 + e2;  // partial sum of the rest term
-    }
-  }
-  if (MODE == C_FULL || MODE == C_Q4 || MODE == C_Q5) {
-    sys.split(U, 1, set, k, ch, Fp, F);
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      R e4 = c * U[i] + Fp[i] * xinv;
-      R e5 = c * U[i] - (F[i] - Fp[i]) * xinv;
-      out[3][i] = f[3][i] + om * (e4 - f[3][i]);
-      out[4][i] = f[4][i] + om * (e5 - f[4][i]);
-      if (MODE == C_FULL) {
-        R e3 = U[i] - (out[2][i] + e4 + e5);
-        out[2][i] = f[2][i] + om * (e3 - f[2][i]);
-      }
+    if (MODE == C_FULL) out[2][i] = relax(f[2][i], e[2][i], om);
+    if (MODE == C_FULL || MODE == C_Q4 || MODE == C_Q5) {
+      out[3][i] = relax(f[3][i], e[3][i], om);
+      out[4][i] = relax(f[4][i], e[4][i], om);
     }
   }
 }
@@ -228,6 +243,33 @@ __device__ __forceinline__ BlockConsts<Sys, R> block_consts(const StepArgs<T>& a
   return b;
 }
 
+// State forms of a D2Q5 simulation.  FORM 0 keeps the distributions f (5p
+// components a cell); FORM 1, for omega = 1 only, keeps the moments U (p a
+// cell): at omega = 1 the post-collision state is f^eq(U) (Eq. 42), so f after
+// streaming is a function of the neighbours' U and a step is the finite-volume
+// update of Thm 4.3, U^{n+1}(x) = sum_q f^eq_q(U^n(x - v_q)) (Eqs. 41, 43).
+// Both march the same way; only the load and the store differ.
+template <class Sys, int FORM>
+struct StateForm {
+  static constexpr int NS = FORM == 0 ? 5 * Sys::P : Sys::P;   // stored components a cell
+};
+
+// Post-collision components of cell (x, y) that MODE needs.
+template <class Sys, class T, class R, int MODE, int FORM>
+__device__ __forceinline__ void cell_post(const Sys& sys, const T* __restrict__ fin, int x, int y, int nxb, R xinv,
+                                          R c, R om, int set, R k, R ch, R (&o)[5][Sys::P]) {
+  constexpr int P = Sys::P;
+  const size_t b = brick_base(x, y, nxb, StateForm<Sys, FORM>::NS);
+  if constexpr (FORM == 0) {
+    collide_d2q5<Sys, T, R, MODE>(sys, fin, kBrick, b, xinv, c, om, set, k, ch, o);
+  } else {
+    R U[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) U[i] = Store<T>::ld(fin + b + (size_t)i * kBrick);
+    equilibria_d2q5<Sys, R, MODE>(sys, U, xinv, c, set, k, ch, o);
+  }
+}
+
 // ------------------------------------------------------------------ D2Q5 step
 // March over the rows of one tile, up or down.  Tiles of
 // even row index march up and odd ones down, so the two tiles that share a
@@ -239,7 +281,7 @@ __device__ __forceinline__ BlockConsts<Sys, R> block_consts(const StepArgs<T>& a
 // small systems); DIR = 0 picks it at run time in one body (MHD-GLM, whose
 // arithmetic is large enough that a second copy costs more in instruction-cache
 // misses than the register selects).
-template <class Sys, class T, class R, int DIR>
+template <class Sys, class T, class R, int DIR, int FORM>
 __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const BlockConsts<Sys, R>& bc, int bx,
                                                 int by, int TX, int TY, unsigned char* smem) {
   constexpr int P = Sys::P;
@@ -251,8 +293,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   const int w = min(TX, nx - x0), h = min(TY, ny - y0);
   const int x = x0 + tx;
   const bool act = tx < w;
-  constexpr int NPL = 5 * P;
-  constexpr size_t plane = kBrick;   // component stride in the brick layout
+  constexpr int NS = StateForm<Sys, FORM>::NS;
   const int nxb = a.pitch / kBrick;
   const T* __restrict__ fin = a.f[a.parity];
   T* __restrict__ fout = a.f[a.parity ^ 1];
@@ -271,14 +312,13 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     const int side = t >= h;
     const int r = side ? t - h : t;
     const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
-    const size_t idx = brick_base(xr, y0 + r, nxb, NPL);
     R o[5][P];
     if (!side) {
-      collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
+      cell_post<Sys, T, R, C_Q1, FORM>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) ringL[i * TY + r] = o[0][i];
     } else {
-      collide_d2q5<Sys, T, R, C_Q2>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
+      cell_post<Sys, T, R, C_Q2, FORM>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) ringR[i * TY + r] = o[1][i];
     }
@@ -290,18 +330,15 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   if (act) {
     R o[5][P];
     if (up) {
-      collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, brick_base(x, (y0 - 1 + ny) % ny, nxb, NPL), xinv, c, om, set,
-                                    kk, ch, o);
+      cell_post<Sys, T, R, C_Q4, FORM>(sys, fin, x, (y0 - 1 + ny) % ny, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
     } else {
-      collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, brick_base(x, (y0 + h) % ny, nxb, NPL), xinv, c, om, set, kk,
-                                    ch, o);
+      cell_post<Sys, T, R, C_Q5, FORM>(sys, fin, x, (y0 + h) % ny, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
     }
-    collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, brick_base(x, row_of(0), nxb, NPL), xinv, c, om, set, kk, ch,
-                                    o);
+    cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, row_of(0), nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       rb1[i * TX + tx] = o[0][i];
@@ -320,8 +357,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     if (act) {
       R o[5][P];
       if (r + 1 < h) {
-        collide_d2q5<Sys, T, R, C_FULL>(sys, fin, plane, brick_base(x, row_of(r + 1), nxb, NPL), xinv, c, om, set,
-                                        kk, ch, o);
+        cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, row_of(r + 1), nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
           rb1[(nb * P + i) * TX + tx] = o[0][i];
@@ -332,13 +368,11 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
         }
       } else {
         if (up) {
-          collide_d2q5<Sys, T, R, C_Q5>(sys, fin, plane, brick_base(x, (y0 + h) % ny, nxb, NPL), xinv, c, om, set,
-                                        kk, ch, o);
+          cell_post<Sys, T, R, C_Q5, FORM>(sys, fin, x, (y0 + h) % ny, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[4][i];
         } else {
-          collide_d2q5<Sys, T, R, C_Q4>(sys, fin, plane, brick_base(x, (y0 - 1 + ny) % ny, nxb, NPL), xinv, c, om,
-                                        set, kk, ch, o);
+          cell_post<Sys, T, R, C_Q4, FORM>(sys, fin, x, (y0 - 1 + ny) % ny, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[3][i];
         }
@@ -348,7 +382,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     }
     __syncthreads();
     if (act) {
-      const size_t base = brick_base(x, j, nxb, NPL);
+      const size_t base = brick_base(x, j, nxb, NS);
       const int rt = j - y0;
       R U[P];
 #pragma unroll
@@ -360,13 +394,20 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
         g[3] = up ? fbp[i] : fan[i];
         g[4] = up ? fan[i] : fbp[i];
         const T* tp = nullptr;
-        R acc = R(0);
+        if constexpr (FORM == 0) {
+          R acc = R(0);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          Store<T>::st(fout + (size_t)(q * P + i) * plane + base, g[q]);
-          acc += round_store(g[q], tp);
+          for (int q = 0; q < 5; ++q) {
+            Store<T>::st(fout + (size_t)(q * P + i) * kBrick + base, g[q]);
+            acc += round_store(g[q], tp);
+          }
+          U[i] = acc;
+        } else {
+          // Eq. (3), summed in the order of the distribution form's next collision
+          const R u = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];
+          Store<T>::st(fout + (size_t)i * kBrick + base, u);
+          U[i] = round_store(u, tp);
         }
-        U[i] = acc;
       }
       R e1, e2;
       bad |= !sys.epilogue(U, e1, e2);
@@ -383,10 +424,10 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   commit_max<R>(m1, m2, bad, a.ctl, s1);
 }
 
-template <class Sys, class T, class R>
+template <class Sys, class T, class R, int FORM = 0>
 __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by, int TX, int TY,
                                             unsigned char* smem) {
-  constexpr int P = Sys::P;
+  constexpr int NS = StateForm<Sys, FORM>::NS;
   const int tx = threadIdx.x;
   const int x0 = bx * TX, y0 = by * TY;
   // the step's scalars in FP64 by one thread per block (FP64 is slow on this
@@ -404,8 +445,8 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     const int w = min(TX, a.nx - x0), h = min(TY, a.ny - y0);
     if (tx < w)
       for (int r = 0; r < h; ++r)
-        for (int i = 0; i < 5 * P; ++i) {
-          const size_t o = brick_base(x0 + tx, y0 + r, a.pitch / kBrick, 5 * P) + (size_t)i * kBrick;
+        for (int i = 0; i < NS; ++i) {
+          const size_t o = brick_base(x0 + tx, y0 + r, a.pitch / kBrick, NS) + (size_t)i * kBrick;
           a.f[a.parity ^ 1][o] = a.f[a.parity][o];
         }
     if (bx == 0 && by == 0 && tx == 0) {
@@ -421,11 +462,11 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
   if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, s_sc, a.dx, a.fixed_xi, Sys::MHD);
   if constexpr (Sys::P <= 4) {
     if (by & 1)
-      step2d_tile_dir<Sys, T, R, -1>(a, s_bc, bx, by, TX, TY, smem);
+      step2d_tile_dir<Sys, T, R, -1, FORM>(a, s_bc, bx, by, TX, TY, smem);
     else
-      step2d_tile_dir<Sys, T, R, +1>(a, s_bc, bx, by, TX, TY, smem);
+      step2d_tile_dir<Sys, T, R, +1, FORM>(a, s_bc, bx, by, TX, TY, smem);
   } else {
-    step2d_tile_dir<Sys, T, R, 0>(a, s_bc, bx, by, TX, TY, smem);
+    step2d_tile_dir<Sys, T, R, 0, FORM>(a, s_bc, bx, by, TX, TY, smem);
   }
 }
 
@@ -704,6 +745,13 @@ __global__ void step2d_kernel(StepArgs<T> a, int TX, int TY) {
   step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
 }
 
+// The moment form (omega = 1): U in, U out, p components a cell.
+template <class Sys, class T, class R>
+__global__ void step2d_u_kernel(StepArgs<T> a, int TX, int TY) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  step2d_tile<Sys, T, R, 1>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
+}
+
 // Register bound of the plain step: blocks of at most 128 threads with at least
 // `min_blocks` of them resident per SM (0 = no bound).  FP32 MHD-GLM needs about
 // 157 registers a thread unbounded (3 blocks of 4 warps per SM); capped at 128
@@ -717,10 +765,10 @@ struct StepBound<MHDGLM<float>, float> {
   static constexpr int min_blocks = 4;
 };
 
-template <class Sys, class T, class R, int MINB>
+template <class Sys, class T, class R, int MINB, int FORM = 0>
 __global__ void __launch_bounds__(128, MINB) step2d_lb_kernel(StepArgs<T> a, int TX, int TY) {
   extern __shared__ __align__(128) unsigned char smem[];
-  step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
+  step2d_tile<Sys, T, R, FORM>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
 }
 
 template <class Sys, class T, class R>
@@ -746,6 +794,8 @@ __global__ void step2d_batch_kernel(const StepArgs<T>* __restrict__ desc, const 
   a.slot = (a.slot + step_off) % 3;
   if constexpr (VARIANT == 1)
     step2d_tile_tma<Sys, T, R>(a, wk.bx, wk.by, TX, TY, D, smem);
+  else if constexpr (VARIANT == 2)
+    step2d_tile<Sys, T, R, 1>(a, wk.bx, wk.by, TX, TY, smem);   // moment form
   else
     step2d_tile<Sys, T, R>(a, wk.bx, wk.by, TX, TY, smem);
 }
@@ -918,14 +968,14 @@ __global__ void init_max_kernel(const double* __restrict__ U, size_t cells, SysP
 
 // f_q = f_q^eq(U) (Eq. 2b) with xi_0, c_h^0 from slot 0.  U is dense [p][ny][nx];
 // f in the lattice's layout (cell_base / comp_stride).
-template <class Sys, class T, class R, int DIM>
+template <class Sys, class T, class R, int DIM, int FORM = 0>
 __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, StepArgs<T> a) {
   constexpr int P = Sys::P;
   const Sys sys = make_sys<Sys>(a.sp);
   const StepScalars sc = step_scalars(a.ctl, 0, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, -1.0, a.dx);
   const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, kk = (R)a.k;
   T* f = a.f[a.parity];
-  constexpr int Q = DIM == 1 ? 3 : 5;
+  constexpr int Q = DIM == 1 ? 3 : (FORM == 0 ? 5 : 1);
   const size_t plane = comp_stride(Q, a.pitch, a.ny);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cells; i += (size_t)gridDim.x * blockDim.x) {
     const size_t y = i / a.nx, x = i - y * a.nx;
@@ -955,10 +1005,23 @@ __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, Step
         e[4][s] = c * u[s] - (F[s] - Fp[s]) * xinv;
         e[2][s] = u[s] - (e[0][s] + e[1][s] + e[3][s] + e[4][s]);
       }
+      if constexpr (FORM == 0) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q)
+        for (int q = 0; q < 5; ++q)
 #pragma unroll
-        for (int s = 0; s < P; ++s) Store<T>::st(f + (size_t)(q * P + s) * plane + o, e[q][s]);
+          for (int s = 0; s < P; ++s) Store<T>::st(f + (size_t)(q * P + s) * plane + o, e[q][s]);
+      } else {
+        // the moments of those distributions, summed in the order of the
+        // distribution form's first collision
+        const T* tp = nullptr;
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+          const R u = (((round_store(e[0][s], tp) + round_store(e[1][s], tp)) + round_store(e[2][s], tp)) +
+                       round_store(e[3][s], tp)) +
+                      round_store(e[4][s], tp);
+          Store<T>::st(f + (size_t)s * plane + o, u);
+        }
+      }
     }
   }
 }

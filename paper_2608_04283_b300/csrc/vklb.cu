@@ -45,6 +45,8 @@ struct vklb_sim {
   double* stage;           // [p][cells] double staging for set_state / moments
   int tile_x, tile_y;
   int variant, stages;     // step kernel: 0 plain, 1 bulk-copy row pipeline with `stages` rows in flight
+  int form;                // 0 distributions f, 1 moments U (omega = 1, D2Q5)
+  int QS;                  // stored components a field: Q (form 0) or 1 (form 1)
   bool ready;
   const Ops* ops;
 };
@@ -80,6 +82,10 @@ struct vklb_batch {
 };
 
 namespace {
+
+// Kernel selector: 0 plain distribution step, 1 bulk-copy distribution step,
+// 2 moment-form step.
+int kernel_variant(const vklb_sim* s) { return s->form == 1 ? 2 : s->variant; }
 
 template <class T>
 StepArgs<T> make_args(const vklb_sim* s, double t_end) {
@@ -124,7 +130,14 @@ struct Impl {
     a.parity = s->cur;
     const int blk = 256;
     init_max_kernel<Sys, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, s->sp, s->ctl);
-    init_feq_kernel<Sys, T, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, a);
+    if constexpr (DIM == 2) {
+      if (s->form == 1)
+        init_feq_kernel<Sys, T, R, DIM, 1><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, a);
+      else
+        init_feq_kernel<Sys, T, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, a);
+    } else {
+      init_feq_kernel<Sys, T, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, a);
+    }
     g_launches += 2;
     return cuda_status(cudaGetLastError());
   }
@@ -154,13 +167,18 @@ struct Impl {
       return VKLB_OK;
     } else {
       const int TX = s->tile_x, TY = s->tile_y, D = s->stages;
-      const size_t sm = smem_bytes_v(s->variant, TX, TY, D);
+      const int kv = kernel_variant(s);
+      const size_t sm = smem_bytes_v(kv, TX, TY, D);
       set_attributes();
       dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
       for (int64_t i = 0; i < n; ++i) {
         StepArgs<T> a = make_args<T>(s, t_end);
-        if (s->variant == 1)
+        if (kv == 1)
           step2d_tma_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY, D);
+        else if (kv == 2 && bounded(TX))
+          step2d_lb_kernel<Sys, T, R, kMinBlocks, 1><<<grid, TX, sm, s->stream>>>(a, TX, TY);
+        else if (kv == 2)
+          step2d_u_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         else if (bounded(TX))
           step2d_lb_kernel<Sys, T, R, kMinBlocks><<<grid, TX, sm, s->stream>>>(a, TX, TY);
         else
@@ -186,6 +204,9 @@ struct Impl {
       cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            200 * 1024);
       cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_u_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
       done = true;
     }
   }
@@ -201,6 +222,10 @@ struct Impl {
       cudaError_t e;
       if (variant == 1)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_tma_kernel<Sys, T, R>, tx, sm);
+      else if (variant == 2 && bounded(tx))
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_lb_kernel<Sys, T, R, kMinBlocks, 1>, tx, sm);
+      else if (variant == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_u_kernel<Sys, T, R>, tx, sm);
       else if (bounded(tx))
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_lb_kernel<Sys, T, R, kMinBlocks>, tx, sm);
       else
@@ -215,15 +240,23 @@ struct Impl {
 
   static int moments(vklb_sim* s, double* dU) {
     const int blk = 256;
-    moments_kernel<T, P, Q><<<grid_for(s->cells, blk), blk, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx,
-                                                                            (int)s->ny, (int)s->pitch, dU);
+    if (s->form == 1)
+      moments_kernel<T, P, 1><<<grid_for(s->cells, blk), blk, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx,
+                                                                              (int)s->ny, (int)s->pitch, dU);
+    else
+      moments_kernel<T, P, Q><<<grid_for(s->cells, blk), blk, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx,
+                                                                              (int)s->ny, (int)s->pitch, dU);
     g_launches += 1;
     return cuda_status(cudaGetLastError());
   }
 
   static int totals(vklb_sim* s, double* host) {
-    totals_pass1<T, P, Q><<<kRedBlocks, 256, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx, (int)s->ny,
-                                                             (int)s->pitch, s->part);
+    if (s->form == 1)
+      totals_pass1<T, P, 1><<<kRedBlocks, 256, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx, (int)s->ny,
+                                                               (int)s->pitch, s->part);
+    else
+      totals_pass1<T, P, Q><<<kRedBlocks, 256, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx, (int)s->ny,
+                                                               (int)s->pitch, s->part);
     double scale = DIM == 1 ? s->dx : s->dx * s->dx;
     totals_pass2<<<1, 32, 0, s->stream>>>(s->part, kRedBlocks, P, scale, s->dvec);
     g_launches += 2;
@@ -243,6 +276,9 @@ struct BatchImpl {
       if (b->variant == 1)
         step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+      else if (b->variant == 2)
+        step2d_batch_kernel<Sys, T, R, 2><<<b->nwork, TX, sm, b->own>>>(
+            (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
       else
         step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
@@ -257,10 +293,12 @@ struct BatchImpl {
       const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(variant, tx, ty, d);
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       int nb = 0;
-      cudaError_t e = variant == 1
-                          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx, sm)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 0>, tx, sm);
+      cudaError_t e =
+          variant == 1   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx, sm)
+          : variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 2>, tx, sm)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 0>, tx, sm);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -276,6 +314,7 @@ struct BatchImpl {
     if (!attr_set) {
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr_set = true;
     }
     StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
@@ -431,7 +470,7 @@ static int wave_fit_rows(vklb_sim* s, int tx, int* ty_out) {
   const int64_t gx = (s->nx + tx - 1) / tx;
   int ty = 16;
   for (int pass = 0; pass < 2; ++pass) {   // occupancy depends on ty through the ring buffers
-    const int nb = s->ops->occupancy(s->variant, tx, ty, s->stages);
+    const int nb = s->ops->occupancy(kernel_variant(s), tx, ty, s->stages);
     if (nb < 1) return VKLB_ERR_ARG;
     int64_t rows = (int64_t)nb * sms / gx;
     if (rows < 1) rows = 1;
@@ -516,6 +555,8 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->tile_y = 16;
   s->variant = 0;   // plain loads measure faster than the bulk-copy pipeline on B300 so far
   s->stages = 4;
+  s->form = 0;
+  s->QS = s->Q;
   s->ops = ops;
   const size_t fbytes = (size_t)s->Q * s->P * (size_t)s->pitch * s->ny * s->store_bytes;
   cudaError_t e = cudaSuccess;
@@ -581,7 +622,7 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
     if (st) return st;
   }
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
-  if (s->ops->smem(s->variant, s->P, tx, ty, s->stages) > 200 * 1024) return VKLB_ERR_ARG;
+  if (s->ops->smem(kernel_variant(s), s->P, tx, ty, s->stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->tile_x = tx;
   s->tile_y = ty;
   return VKLB_OK;
@@ -592,9 +633,48 @@ int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
   if (stages == 0) stages = 4;
   if (stages < 2 || stages > 8) return VKLB_ERR_ARG;
   if (s->dim != 2 && variant != 0) return VKLB_ERR_UNSUPPORTED;
+  if (s->form == 1 && variant != 0) return VKLB_ERR_UNSUPPORTED;
   if (s->ops->smem(variant, s->P, s->tile_x, s->tile_y, stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->variant = variant;
   s->stages = stages;
+  return VKLB_OK;
+}
+
+int vklb_set_form(vklb_sim* s, int32_t form) {
+  if (!s || (form != 0 && form != 1)) return VKLB_ERR_ARG;
+  if (form == s->form) return VKLB_OK;
+  if (form == 1 && s->dim != 2) return VKLB_ERR_UNSUPPORTED;
+  if (form == 1 && s->omega != 1.0) return VKLB_ERR_ARG;   // f* = f^eq(U) holds at omega = 1 only
+  if (form == 1 && s->variant != 0) return VKLB_ERR_UNSUPPORTED;
+  int st = cuda_status(cudaStreamSynchronize(s->stream));
+  if (st) return st;
+  const int qs = form == 1 ? 1 : s->Q;
+  const size_t fbytes = (size_t)qs * s->P * (size_t)s->pitch * s->ny * s->store_bytes;
+  void* nf[2] = {nullptr, nullptr};
+  cudaError_t e = cudaMalloc(&nf[0], fbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&nf[1], fbytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nf[0], 0, fbytes, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(nf[1], 0, fbytes, s->stream);
+  if (e != cudaSuccess) {
+    cudaFree(nf[0]);
+    cudaFree(nf[1]);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? VKLB_ERR_NOMEM : VKLB_ERR_CUDA;
+  }
+  cudaFree(s->f[0]);
+  cudaFree(s->f[1]);
+  s->f[0] = nf[0];
+  s->f[1] = nf[1];
+  s->form = form;
+  s->QS = qs;
+  s->cur = 0;
+  s->launched = 0;
+  s->ready = false;   // the state must be set again
+  int ty = 16;        // the default launch shape, refitted for this form's kernel
+  if (wave_fit_rows(s, 128, &ty) == VKLB_OK) {
+    s->tile_x = 128;
+    s->tile_y = ty;
+  }
   return VKLB_OK;
 }
 
@@ -685,15 +765,16 @@ int vklb_info(const vklb_sim* s, vklb_info_t* info) {
   info->precision = s->prec;
   info->store_bytes = s->store_bytes;
   info->cells = s->cells;
-  info->bytes_per_lup = 2LL * s->Q * s->P * s->store_bytes;
-  info->state_bytes = (int64_t)s->Q * s->P * s->pitch * s->ny * s->store_bytes;
+  info->bytes_per_lup = 2LL * s->QS * s->P * s->store_bytes;
+  info->state_bytes = (int64_t)s->QS * s->P * s->pitch * s->ny * s->store_bytes;
   info->pitch = s->pitch;
   info->dx = s->dx;
   info->tile_x = s->tile_x;
   info->tile_y = s->tile_y;
   info->kernels_per_step = 1;
   info->variant = s->variant;
-  info->blocks_per_sm = s->dim == 2 ? s->ops->occupancy(s->variant, s->tile_x, s->tile_y, s->stages) : 0;
+  info->blocks_per_sm = s->dim == 2 ? s->ops->occupancy(kernel_variant(s), s->tile_x, s->tile_y, s->stages) : 0;
+  info->form = s->form;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     cudaGetLastError();
@@ -709,7 +790,7 @@ int vklb_device_state(const vklb_sim* s, void** f_dev) {
 
 int vklb_state_bytes(const vklb_sim* s, size_t* bytes) {
   if (!s || !bytes) return VKLB_ERR_ARG;
-  *bytes = sizeof(BlobHeader) + sizeof(Ctl) + (size_t)s->Q * s->P * s->pitch * s->ny * s->store_bytes;
+  *bytes = sizeof(BlobHeader) + sizeof(Ctl) + (size_t)s->QS * s->P * s->pitch * s->ny * s->store_bytes;
   return VKLB_OK;
 }
 
@@ -717,13 +798,13 @@ int vklb_get_state(vklb_sim* s, void* blob, size_t bytes) {
   size_t need = 0;
   if (!s || !blob || vklb_state_bytes(s, &need) || bytes < need) return VKLB_ERR_ARG;
   if (!s->ready) return VKLB_ERR_STATE;
-  BlobHeader hdr = {kMagic, (uint32_t)s->kind, (uint32_t)s->P, (uint32_t)s->Q, (uint32_t)s->prec,
+  BlobHeader hdr = {kMagic, (uint32_t)s->kind, (uint32_t)s->P, (uint32_t)s->QS, (uint32_t)s->prec,
                     (uint32_t)(s->launched % 3), s->nx, s->ny, s->launched};
   memcpy(blob, &hdr, sizeof(hdr));
   char* p = (char*)blob + sizeof(hdr);
   int st = cuda_status(cudaMemcpyAsync(p, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
   if (st) return st;
-  const size_t fb = (size_t)s->Q * s->P * s->pitch * s->ny * s->store_bytes;
+  const size_t fb = (size_t)s->QS * s->P * s->pitch * s->ny * s->store_bytes;
   if ((st = cuda_status(cudaMemcpyAsync(p + sizeof(Ctl), s->f[s->cur], fb, cudaMemcpyDeviceToHost, s->stream)))) return st;
   if ((st = cuda_status(cudaStreamSynchronize(s->stream)))) return st;
   Ctl h;
@@ -736,7 +817,7 @@ int vklb_put_state(vklb_sim* s, const void* blob, size_t bytes) {
   if (!s || !blob || vklb_state_bytes(s, &need) || bytes < need) return VKLB_ERR_ARG;
   BlobHeader hdr;
   memcpy(&hdr, blob, sizeof(hdr));
-  if (hdr.magic != kMagic || (int)hdr.kind != s->kind || (int)hdr.P != s->P || (int)hdr.Q != s->Q ||
+  if (hdr.magic != kMagic || (int)hdr.kind != s->kind || (int)hdr.P != s->P || (int)hdr.Q != s->QS ||
       (int)hdr.prec != s->prec || hdr.nx != s->nx || hdr.ny != s->ny)
     return VKLB_ERR_ARG;
   const char* p = (const char*)blob + sizeof(hdr);
@@ -744,7 +825,7 @@ int vklb_put_state(vklb_sim* s, const void* blob, size_t bytes) {
   if (st) return st;
   s->cur = 0;
   s->launched = hdr.launched;
-  const size_t fb = (size_t)s->Q * s->P * s->pitch * s->ny * s->store_bytes;
+  const size_t fb = (size_t)s->QS * s->P * s->pitch * s->ny * s->store_bytes;
   if ((st = cuda_status(cudaMemcpyAsync(s->f[0], p + sizeof(Ctl), fb, cudaMemcpyHostToDevice, s->stream)))) return st;
   if ((st = cuda_status(cudaStreamSynchronize(s->stream)))) return st;
   s->ready = true;
@@ -781,7 +862,8 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
   for (int i = 0; i < n; ++i) {
     const vklb_sim* s = sims[i];
     if (!s || !s->ready) return VKLB_ERR_STATE;
-    if (s->ops != s0->ops || s->set != s0->set || s->variant != s0->variant || s->stages != s0->stages)
+    if (s->ops != s0->ops || s->set != s0->set || s->variant != s0->variant || s->stages != s0->stages ||
+        s->form != s0->form)
       return VKLB_ERR_ARG;
   }
   vklb_batch* b = new (std::nothrow) vklb_batch();
@@ -789,7 +871,7 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
   b->sims.assign(sims, sims + n);
   b->tile_x = s0->tile_x;
   b->tile_y = s0->tile_y;
-  b->variant = s0->variant;
+  b->variant = kernel_variant(s0);   // 2: the moment form
   b->stages = s0->stages;
   b->stream = s0->stream;
   b->ops = s0->ops;

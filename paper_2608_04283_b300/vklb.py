@@ -55,7 +55,7 @@ class Info(C.Structure):
                 ("cells", C.c_int64), ("bytes_per_lup", C.c_int64), ("state_bytes", C.c_int64),
                 ("dx", C.c_double), ("tile_x", C.c_int32), ("tile_y", C.c_int32),
                 ("kernels_per_step", C.c_int32), ("variant", C.c_int32), ("pitch", C.c_int64),
-                ("blocks_per_sm", C.c_int32), ("sms", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("sms", C.c_int32), ("form", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -66,6 +66,7 @@ _SIGS = {
     "vklb_set_state": (C.c_int, [_P, _P, C.c_int32]),
     "vklb_set_tiling": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "vklb_set_variant": (C.c_int, [_P, C.c_int32, C.c_int32]),
+    "vklb_set_form": (C.c_int, [_P, C.c_int32]),
     "vklb_step": (C.c_int, [_P, C.c_int64]),
     "vklb_step_to": (C.c_int, [_P, C.c_double]),
     "vklb_sync": (C.c_int, [_P]),
@@ -120,11 +121,12 @@ def _stream_handle(stream):
 
 class Sim:
     """One simulation (see vklb_create).  ``system`` in advection / swe / euler /
-    mhd_glm; ``n`` = (nx,) or (nx, ny); ``lo``/``hi`` domain corners."""
+    mhd_glm; ``n`` = (nx,) or (nx, ny); ``lo``/``hi`` domain corners; ``form``
+    "moments" keeps U instead of f as the state (D2Q5, omega = 1; vklb_set_form)."""
 
     def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted", c=0.05, k=2.0, omega=1.0,
                  cfl=0.9, dt=0.0, precision="fp32", gamma=1.4, g=9.81, ch_factor=6.0, adv_speed=(1.0, 0.0),
-                 stream=None):
+                 stream=None, form="distributions"):
         n = tuple(int(v) for v in n)
         dim = len(n)
         lo = tuple(float(v) for v in np.atleast_1d(lo))
@@ -148,6 +150,8 @@ class Sim:
         _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
         self.p = self.info.p
         self.shape = (self.p,) + tuple(reversed(n))
+        if form != "distributions":
+            self.set_form(form)
 
     # ------------------------------------------------------------------ core
     @property
@@ -169,6 +173,12 @@ class Sim:
         """Step-kernel tile: tx cells by ty rows per block; ty = -1 fits the
         grid to whole waves of resident blocks (resolved height in info.tile_y)."""
         _check(_lib.vklb_set_tiling(self._h, int(tx), int(ty)), "vklb_set_tiling")
+        _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
+
+    def set_form(self, form):
+        """"distributions" (0) or "moments" (1); the state must be set afterwards."""
+        code = {"distributions": 0, "moments": 1}.get(form, form)
+        _check(_lib.vklb_set_form(self._h, int(code)), "vklb_set_form")
         _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
 
     def set_variant(self, variant, stages=0):
