@@ -9,6 +9,7 @@ Usage: python -m paper_2608_04283_b300.build  (or build() from Python).
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -40,14 +41,26 @@ def _run(cmd):
     return res
 
 
+# translation units of libvklb.so: the C ABI and one per system's kernels
+UNITS = ["vklb.cu", "ops_advect.cu", "ops_swe.cu", "ops_euler.cu", "ops_mhd.cu", "ops_mhd_fp64.cu",
+         "ops_mhd_fp32.cu", "ops_mhd_bf16.cu"]
+
+
 def build(force=False, verbose=False):
     deps = _sources()
     if force or _stale(LIB, deps):
-        cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-               "-I" + INCLUDE, "-o", LIB, os.path.join(CSRC, "vklb.cu")]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        _run(cmd)
+        objdir = os.path.join(HERE, "_build")
+        os.makedirs(objdir, exist_ok=True)
+        cmds = []
+        for u in UNITS:
+            cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-c", "-I" + INCLUDE,
+                   "-o", os.path.join(objdir, u + ".o"), os.path.join(CSRC, u)]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+            cmds.append(cmd)
+        with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+            list(ex.map(_run, cmds))
+        _run([NVCC, *ARCH, "-shared", "-o", LIB] + [os.path.join(objdir, u + ".o") for u in UNITS])
     if force or _stale(HOSTCHECK, deps):
         cmd = [NVCC, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-I" + INCLUDE,
                "-o", HOSTCHECK, os.path.join(CSRC, "hostcheck.cu")]

@@ -1,0 +1,408 @@
+// Host-side machinery shared by the translation units of libvklb.so: the
+// simulation and batch records, the per-(system, precision, lattice) kernel
+// launchers (Impl, BatchImpl) and their dispatch tables (Ops).  Each system's
+// tables are instantiated in a translation unit of its own (ops_*.cu) so that
+// the library compiles in parallel; vklb.cu holds the C ABI.
+#pragma once
+#include <atomic>
+#include <cmath>
+#include <mutex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vk_kernels.cuh"
+#include "vklb.h"
+
+using namespace vk;
+
+// kernel launches enqueued through the library (vklb_launch_count)
+extern std::atomic<long long> g_launches;
+
+const int kRedBlocks = 296;  // conservation-total pass 1: 2 blocks per SM on 148 SMs
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? VKLB_OK : VKLB_ERR_CUDA; }
+
+struct Ops;
+
+struct vklb_sim {
+  int kind, lattice, dim, P, Q, prec, store_bytes;
+  int64_t nx, ny, cells, pitch;
+  double dx, ch_factor;
+  SysParams sp;
+  int set;
+  double c, k, omega, cfl, fixed_xi;
+  int bc_lo, bc_hi;
+  cudaStream_t stream;
+  void* f[2];
+  int cur;                 // f[cur] holds the current state
+  long long launched;      // step launches so far (slot = launched % 3)
+  Ctl* ctl;
+  double* part;            // [p][kRedBlocks] partial sums
+  double* dvec;            // [p] device totals
+  double* stage;           // [p][cells] double staging for set_state / moments
+  int tile_x, tile_y;
+  int variant, stages;     // step kernel: 0 plain, 1 bulk-copy row pipeline with `stages` rows in flight
+  int form;                // 0 distributions f, 1 moments U (omega = 1, D2Q5)
+  int QS;                  // stored components a field: Q (form 0) or 1 (form 1)
+  bool ready;
+  const Ops* ops;
+};
+
+struct Ops {
+  int (*init)(vklb_sim*, const double*);
+  int (*step)(vklb_sim*, int64_t, double);   // enqueue n step launches with t_end
+  int (*moments)(vklb_sim*, double*);
+  int (*totals)(vklb_sim*, double*);
+  int (*batch)(vklb_batch*, int64_t, int);
+  size_t (*smem)(int variant, int p, int tx, int ty, int stages);
+  int (*occupancy)(int variant, int tx, int ty, int stages);
+  int (*batch_occupancy)(int variant, int tx, int ty, int stages);
+  size_t real_bytes;
+  size_t args_bytes;
+};
+
+struct vklb_batch {
+  std::vector<vklb_sim*> sims;
+  int tile_x, tile_y;
+  void* d_desc;
+  BatchWork* d_work;
+  int nwork;
+  int variant, stages;
+  std::vector<unsigned char> h_desc;
+  cudaStream_t stream;
+  const Ops* ops;
+  int64_t graph_n;
+  cudaGraph_t graph;
+  cudaGraphExec_t gexec;
+  cudaStream_t own;        // private stream: graphs cannot be captured on the legacy stream
+  cudaEvent_t ev_in, ev_out;
+};
+
+
+// The dispatch table of each system, one translation unit each.
+const Ops* vk_ops_advect(int dim, int prec);
+const Ops* vk_ops_swe(int dim, int prec);
+const Ops* vk_ops_euler(int dim, int prec);
+const Ops* vk_ops_mhd(int dim, int prec);
+
+namespace {
+
+// Kernel selector: 0 plain distribution step, 1 bulk-copy distribution step,
+// 2 moment-form step.
+int kernel_variant(const vklb_sim* s) { return s->form == 1 ? 2 : s->variant; }
+
+template <class T>
+StepArgs<T> make_args(const vklb_sim* s, double t_end) {
+  StepArgs<T> a;
+  a.f[0] = (T*)s->f[0];
+  a.f[1] = (T*)s->f[1];
+  a.parity = s->cur;
+  a.nx = (int)s->nx;
+  a.ny = (int)s->ny;
+  a.pitch = (int)s->pitch;
+  a.dx = s->dx;
+  a.c = s->c;
+  a.omega = s->omega;
+  a.k = s->k;
+  a.inv_nu = 1.0 / s->cfl;
+  a.fixed_xi = s->fixed_xi;
+  a.t_end = t_end;
+  a.ch_factor = s->ch_factor;
+  a.set = s->set;
+  a.bc_lo = s->bc_lo;
+  a.bc_hi = s->bc_hi;
+  a.ctl = s->ctl;
+  a.slot = (int)(s->launched % 3);
+  a.sp = s->sp;
+  return a;
+}
+
+int grid_for(size_t cells, int block) {
+  size_t g = (cells + block - 1) / block;
+  if (g > 148 * 16) g = 148 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <class Sys, class T, class R, int DIM>
+struct Impl {
+  static constexpr int P = Sys::P;
+  static constexpr int Q = DIM == 1 ? 3 : 5;
+
+  static int init(vklb_sim* s, const double* dU) {
+    StepArgs<T> a = make_args<T>(s, -1.0);
+    a.parity = s->cur;
+    const int blk = 256;
+    init_max_kernel<Sys, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, s->sp, s->ctl);
+    if constexpr (DIM == 2) {
+      if (s->form == 1)
+        init_feq_kernel<Sys, T, R, DIM, 1><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, a);
+      else
+        init_feq_kernel<Sys, T, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, a);
+    } else {
+      init_feq_kernel<Sys, T, R, DIM><<<grid_for(s->cells, blk), blk, 0, s->stream>>>(dU, (size_t)s->cells, a);
+    }
+    g_launches += 2;
+    return cuda_status(cudaGetLastError());
+  }
+
+  static size_t smem_bytes(int tx, int ty) { return (size_t)(6 * P * tx + 2 * P * ty) * sizeof(R); }
+  static size_t smem_bytes_v(int variant, int tx, int ty, int d) {
+    if (variant == 1) return TmaLayout<T>::template make<R, P>(tx, ty, d).bytes;
+    return smem_bytes(tx, ty);
+  }
+
+  static int step(vklb_sim* s, int64_t n, double t_end) {
+    if constexpr (DIM == 1) {
+      int blk = (int)(((s->nx + 31) / 32) * 32);
+      if (blk > 1024) blk = 1024;
+      if (blk < 64) blk = 64;
+      StepArgs<T> a = make_args<T>(s, t_end);
+      // n steps in one launch; with t_end the kernel may stop early, so the
+      // caller re-reads the step counter (vklb_step_to).
+      step1d_kernel<Sys, T, R><<<1, blk, 0, s->stream>>>(a, (int)n);
+      g_launches += 1;
+      int st = cuda_status(cudaGetLastError());
+      if (st) return st;
+      if (t_end <= 0.0) {
+        s->cur ^= (int)(n & 1);
+        s->launched += n;
+      }
+      return VKLB_OK;
+    } else {
+      const int TX = s->tile_x, TY = s->tile_y, D = s->stages;
+      const int kv = kernel_variant(s);
+      const size_t sm = smem_bytes_v(kv, TX, TY, D);
+      set_attributes();
+      dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
+      for (int64_t i = 0; i < n; ++i) {
+        StepArgs<T> a = make_args<T>(s, t_end);
+        if (kv == 1)
+          step2d_tma_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY, D);
+        else if (kv == 2 && bounded(TX))
+          launch_lb<1>(grid, TX, sm, s->stream, a, TY);
+        else if (kv == 2)
+          step2d_u_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
+        else if (bounded(TX))
+          launch_lb<0>(grid, TX, sm, s->stream, a, TY);
+        else
+          step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
+        s->cur ^= 1;
+        s->launched += 1;
+      }
+      g_launches += n;
+      return cuda_status(cudaGetLastError());
+    }
+  }
+
+  // the plain step takes the register-bounded instantiation when it has one
+  // and the block fits its 128-thread bound
+  static constexpr bool kBounded = StepBound<Sys, R>::min_blocks > 0;
+  // the bounded instantiations exist only where they are launched
+  template <int FORM>
+  static void launch_lb(dim3 grid, int TX, size_t sm, cudaStream_t st, const StepArgs<T>& a, int TY) {
+    if constexpr (kBounded) step2d_lb_kernel<Sys, T, R, kMinBlocks, FORM><<<grid, TX, sm, st>>>(a, TX, TY);
+  }
+  static constexpr int kMinBlocks = kBounded ? StepBound<Sys, R>::min_blocks : 1;
+  static bool bounded(int tx) { return kBounded && tx <= 128; }
+
+  static void set_attributes() {
+    if constexpr (DIM == 2) {
+      static bool done = false;
+      if (done) return;
+      cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_u_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if constexpr (kBounded) {
+        cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+      }
+      done = true;
+    }
+  }
+
+  template <int FORM>
+  static cudaError_t occupancy_lb(int* nb, int tx, size_t sm) {
+    if constexpr (kBounded)
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_lb_kernel<Sys, T, R, kMinBlocks, FORM>, tx, sm);
+    else
+      return cudaErrorInvalidValue;
+  }
+
+  // resident blocks per SM of the step kernel a sim with this launch shape runs
+  static int occupancy(int variant, int tx, int ty, int d) {
+    if constexpr (DIM != 2) {
+      return 0;
+    } else {
+      set_attributes();
+      const size_t sm = smem_bytes_v(variant, tx, ty, d);
+      int nb = 0;
+      cudaError_t e;
+      if (variant == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_tma_kernel<Sys, T, R>, tx, sm);
+      else if (variant == 2 && bounded(tx))
+        e = occupancy_lb<1>(&nb, tx, sm);
+      else if (variant == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_u_kernel<Sys, T, R>, tx, sm);
+      else if (bounded(tx))
+        e = occupancy_lb<0>(&nb, tx, sm);
+      else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_kernel<Sys, T, R>, tx, sm);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return nb;
+    }
+  }
+
+  static int moments(vklb_sim* s, double* dU) {
+    const int blk = 256;
+    if (s->form == 1)
+      moments_kernel<T, P, 1><<<grid_for(s->cells, blk), blk, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx,
+                                                                              (int)s->ny, (int)s->pitch, dU);
+    else
+      moments_kernel<T, P, Q><<<grid_for(s->cells, blk), blk, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx,
+                                                                              (int)s->ny, (int)s->pitch, dU);
+    g_launches += 1;
+    return cuda_status(cudaGetLastError());
+  }
+
+  static int totals(vklb_sim* s, double* host) {
+    if (s->form == 1)
+      totals_pass1<T, P, 1><<<kRedBlocks, 256, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx, (int)s->ny,
+                                                               (int)s->pitch, s->part);
+    else
+      totals_pass1<T, P, Q><<<kRedBlocks, 256, 0, s->stream>>>((const T*)s->f[s->cur], (int)s->nx, (int)s->ny,
+                                                               (int)s->pitch, s->part);
+    double scale = DIM == 1 ? s->dx : s->dx * s->dx;
+    totals_pass2<<<1, 32, 0, s->stream>>>(s->part, kRedBlocks, P, scale, s->dvec);
+    g_launches += 2;
+    int st = cuda_status(cudaGetLastError());
+    if (st) return st;
+    return cuda_status(cudaMemcpyAsync(host, s->dvec, sizeof(double) * P, cudaMemcpyDeviceToHost, s->stream));
+  }
+};
+
+template <class Sys, class T, class R, int DIM>
+struct BatchImpl {
+  static void launch(vklb_batch* b, int64_t n) {
+    if constexpr (DIM == 2) {
+    const int TX = b->tile_x, TY = b->tile_y, D = b->stages;
+    const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(b->variant, TX, TY, D);
+    for (int64_t i = 0; i < n; ++i) {
+      if (b->variant == 1)
+        step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX, sm, b->own>>>(
+            (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+      else if (b->variant == 2)
+        step2d_batch_kernel<Sys, T, R, 2><<<b->nwork, TX, sm, b->own>>>(
+            (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+      else
+        step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(
+            (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+    }
+    }
+  }
+  // resident blocks per SM of the batched step kernel at this launch shape
+  static int occupancy(int variant, int tx, int ty, int d) {
+    if constexpr (DIM != 2) {
+      return 0;
+    } else {
+      const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(variant, tx, ty, d);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      int nb = 0;
+      cudaError_t e =
+          variant == 1   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx, sm)
+          : variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 2>, tx, sm)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 0>, tx, sm);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return nb;
+    }
+  }
+  static int step(vklb_batch* b, int64_t n, int use_graph) {
+    if constexpr (DIM != 2) {
+      return VKLB_ERR_UNSUPPORTED;
+    } else {
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_set = true;
+    }
+    StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
+    for (size_t i = 0; i < b->sims.size(); ++i) h[i] = make_args<T>(b->sims[i], -1.0);
+    // order after the work already queued on the simulations' streams
+    int st = VKLB_OK;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+      if (i > 0 && b->sims[i]->stream == b->sims[i - 1]->stream) continue;
+      if ((st = cuda_status(cudaEventRecord(b->ev_in, b->sims[i]->stream)))) return st;
+      if ((st = cuda_status(cudaStreamWaitEvent(b->own, b->ev_in, 0)))) return st;
+    }
+    // pageable source: the runtime stages it before returning, so h may be reused
+    if ((st = cuda_status(cudaMemcpyAsync(b->d_desc, h, b->h_desc.size(), cudaMemcpyHostToDevice, b->own)))) return st;
+    if (use_graph) {
+      if (!b->gexec || b->graph_n != n) {
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->gexec = nullptr;
+        b->graph = nullptr;
+        if ((st = cuda_status(cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal)))) return st;
+        launch(b, n);
+        if ((st = cuda_status(cudaStreamEndCapture(b->own, &b->graph)))) return st;
+        if ((st = cuda_status(cudaGraphInstantiate(&b->gexec, b->graph, 0)))) return st;
+        b->graph_n = n;
+      }
+      if ((st = cuda_status(cudaGraphLaunch(b->gexec, b->own)))) return st;
+    } else {
+      launch(b, n);
+    }
+    g_launches += n;
+    if ((st = cuda_status(cudaGetLastError()))) return st;
+    // later work on the simulations' streams waits for the batch
+    if ((st = cuda_status(cudaEventRecord(b->ev_out, b->own)))) return st;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+      if (i > 0 && b->sims[i]->stream == b->sims[i - 1]->stream) continue;
+      if ((st = cuda_status(cudaStreamWaitEvent(b->sims[i]->stream, b->ev_out, 0)))) return st;
+    }
+    for (vklb_sim* s : b->sims) {
+      s->cur ^= (int)(n & 1);
+      s->launched += n;
+    }
+    return VKLB_OK;
+    }
+  }
+};
+
+template <class Sys, class T, class R, int DIM>
+size_t smem_of(int variant, int p, int tx, int ty, int stages) {
+  return Impl<Sys, T, R, DIM>::smem_bytes_v(variant, tx, ty, stages);
+}
+
+template <class Sys, class T, class R, int DIM>
+const Ops* ops_of() {
+  static const Ops o = {&Impl<Sys, T, R, DIM>::init,    &Impl<Sys, T, R, DIM>::step,
+                        &Impl<Sys, T, R, DIM>::moments, &Impl<Sys, T, R, DIM>::totals,
+                        &BatchImpl<Sys, T, R, DIM>::step, &smem_of<Sys, T, R, DIM>,
+                        &Impl<Sys, T, R, DIM>::occupancy, &BatchImpl<Sys, T, R, DIM>::occupancy,
+                        sizeof(R),                        sizeof(StepArgs<T>)};
+  return &o;
+}
+
+template <template <class, int> class S, int DIM>
+const Ops* pick_prec(int prec) {
+  if (prec == VKLB_FP64) return ops_of<S<double, DIM>, double, double, DIM>();
+  if (prec == VKLB_FP32) return ops_of<S<float, DIM>, float, float, DIM>();
+  return ops_of<S<float, DIM>, __nv_bfloat16, float, DIM>();
+}
+
+}  // namespace

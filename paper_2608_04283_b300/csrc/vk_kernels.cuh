@@ -1073,7 +1073,7 @@ __global__ void totals_pass1(const T* __restrict__ f, int nx, int ny, int pitch,
 }
 
 // Pass 2: one thread per field sums the partials in block order.
-__global__ void totals_pass2(const double* __restrict__ part, int nblocks, int P, double scale,
+static __global__ void totals_pass2(const double* __restrict__ part, int nblocks, int P, double scale,
                              double* __restrict__ out) {
   const int s = threadIdx.x;
   if (s >= P) return;
