@@ -97,13 +97,15 @@ def configure(sim, shape):
     sim.set_tiling(*tile)          # the wave-fit height depends on the variant
 
 
-def step_kernel_name(system, prec, tile_x, variant):
+def step_kernel_name(system, prec, tile_x, variant, form=0):
     """The step kernel the library launches: the bulk-copy variant, or the plain
-    one, which FP32-compute MHD-GLM with blocks of at most 128 threads takes in
-    its register-bounded instantiation."""
+    one (moment form: step2d_u_kernel), which FP32-compute MHD-GLM with blocks
+    of at most 128 threads takes in its register-bounded instantiation."""
     if variant == 1:
         return "step2d_tma_kernel"
-    return "step2d_lb_kernel" if system == "mhd_glm" and prec != "fp64" and tile_x <= 128 else "step2d_kernel"
+    if system == "mhd_glm" and prec != "fp64" and tile_x <= 128:
+        return "step2d_lb_kernel"
+    return "step2d_u_kernel" if form == 1 else "step2d_kernel"
 
 
 def measured_peaks():
@@ -299,8 +301,9 @@ def run_ours(args, wl):
 
     prec = args.precision
     stream = torch.cuda.Stream()
-    sim = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, stream=stream, **wl["kw"])
-    tile = launch_shape(wl["system"], prec, wl["n"])
+    sim = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, stream=stream, form=args.form,
+                   **wl["kw"])
+    tile = launch_shape(wl["system"], prec, wl["n"]) if args.form == "distributions" else None
     configure(sim, tile)
     U0 = wl["ic"]()
     U0_dev = torch.from_numpy(U0).cuda()
@@ -324,7 +327,7 @@ def run_ours(args, wl):
     mean_ms = total_ms / args.steps
     achieved = bpl * cells / (mean_ms * 1e-3) / 1e9
     peaks, peak_src = measured_peaks()
-    kname = step_kernel_name(wl["system"], prec, sim.info.tile_x, sim.info.variant)
+    kname = step_kernel_name(wl["system"], prec, sim.info.tile_x, sim.info.variant, sim.info.form)
     key = f"{kname}/{wl['system']}/{prec}/{wl['n'][0]}x{wl['n'][1]}/{sim.info.tile_x}x{sim.info.tile_y}"
     traffic = traffic_record(key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -336,11 +339,12 @@ def run_ours(args, wl):
     e2e = None
     cpu = None
     if rank == 0 and not args.timed_only:
-        acc = accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps=50)
-        e2e = end_to_end(torch, vklb, wl, prec, tile, steps=min(args.steps, REINIT_EVERY), U0=U0)
+        acc = accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps=50, form=args.form)
+        e2e = end_to_end(torch, vklb, wl, prec, tile, steps=min(args.steps, REINIT_EVERY), U0=U0, form=args.form)
         if not args.no_extras and args.workload == "euler_vortex_1024":
             extras["mhd_orszag_tang_2048"] = secondary(torch, vklb, WORKLOADS["mhd_orszag_tang_2048"], prec,
                                                        flush_buf, steps=100)
+            extras["moment_form"] = moment_form(torch, vklb, flush_buf)
             extras["batched_swe_256"] = batched_swe(torch, vklb)
             extras["served_mix"] = served_mix(args.served_requests)
         if world == 1 and not args.no_cpu_baseline:
@@ -354,7 +358,7 @@ def run_ours(args, wl):
                 "data": "synthetic",
                 "config": {"workload": args.workload, "description": wl["name"], "cells": cells,
                            "precision": prec, "tile": [sim.info.tile_x, sim.info.tile_y],
-                           "variant": sim.info.variant,
+                           "variant": sim.info.variant, "form": args.form,
                            "l2": "flushed before every timed step: 256 MiB write, then 256 MiB read of another buffer",
                            "reinit_every": REINIT_EVERY, "parallelism": "replicas" if world > 1 else "single"},
                 "hbm_gbs": achieved, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -369,7 +373,7 @@ def run_ours(args, wl):
         torch.distributed.destroy_process_group()
 
 
-def accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps):
+def accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps, form="distributions"):
     """L1 / Linf of the benchmarked precision against the FP64 CUDA path (which the
     parity tests tie to the oracle at <= 1e-11) after ``steps`` steps."""
     if prec == "fp64":
@@ -378,7 +382,7 @@ def accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps):
     out = {}
     res = []
     for p in (prec, "fp64"):
-        s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=p, **wl["kw"])
+        s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=p, form=form, **wl["kw"])
         if p == prec:
             configure(s, tile)
         s.set_state(U0)
@@ -405,13 +409,13 @@ def rel_norm(a, b, norm):
     return np.array(out)
 
 
-def end_to_end(torch, vklb, wl, prec, tile, steps, U0):
+def end_to_end(torch, vklb, wl, prec, tile, steps, U0, form="distributions"):
     """Through the public API with host buffers: pinned U0 -> vklb_set_state (H2D),
     ``steps`` x vklb_step, vklb_moments -> pinned host (D2H), wall clock."""
     host_in = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True).numpy()
     host_in[...] = U0
     host_out = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True).numpy()
-    s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, **wl["kw"])
+    s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision=prec, form=form, **wl["kw"])
     configure(s, tile)
     s.set_state(host_in)
     s.step(2)
@@ -428,6 +432,38 @@ def end_to_end(torch, vklb, wl, prec, tile, steps, U0):
             "h2d_bytes_per_step": int(U0.nbytes / steps), "d2h_bytes_per_step": int(U0.nbytes / steps),
             "steps_per_solve": steps,
             "note": "one solve = H2D of U0 (pinned), the steps, D2H of U (pinned); bytes amortised per step"}
+
+
+def moment_form(torch, vklb, flush_buf, steps=100):
+    """omega = 1 workloads in both state forms (vklb_set_form), L2 flushed before
+    every timed step: distributions at the autotuned launch shape, moments at
+    128-cell rows of wave-fit height.  GB/s counts each form's own algorithmic
+    bytes (2 x 5p x 4 B a cell for f, 2 x p x 4 B for U)."""
+    out = {}
+    cases = [("mhd_orszag_tang_2048", WORKLOADS["mhd_orszag_tang_2048"]),
+             ("swe_hump_1024", dict(system="swe", n=(1024, 1024), lo=(0.0, 0.0), hi=(1.0, 1.0),
+                                    kw=dict(omega=1.0, cfl=0.3, c=0.05, k=2.0),
+                                    ic=lambda: inputs.swe_hump_2d(1024, 0.5, 0.5, 0.5, 0.08)))]
+    peaks, _ = measured_peaks()
+    for name, wl in cases:
+        row = {}
+        U0 = torch.from_numpy(wl["ic"]()).cuda()
+        cells = wl["n"][0] * wl["n"][1]
+        for form in ("distributions", "moments"):
+            stream = torch.cuda.Stream()
+            s = vklb.Sim(wl["system"], wl["n"], wl["lo"], wl["hi"], precision="fp32", stream=stream, form=form,
+                         **wl["kw"])
+            if form == "distributions":
+                configure(s, launch_shape(wl["system"], "fp32", wl["n"]))
+            ms = float(timed_steps(torch, s, stream, U0, steps, 5, flush_buf).mean())
+            gbs = s.info.bytes_per_lup * cells / (ms * 1e-3) / 1e9
+            row[form] = {"ms_per_step": ms, "MLUPS": cells / (ms * 1e-3) / 1e6, "hbm_gbs": gbs,
+                         "frac_of_peak": gbs / peaks["hbm_gbs"], "bytes_per_lup": s.info.bytes_per_lup,
+                         "tile": [s.info.tile_x, s.info.tile_y]}
+            s.close()
+        row["speedup"] = row["distributions"]["ms_per_step"] / row["moments"]["ms_per_step"]
+        out[name] = row
+    return out
 
 
 def secondary(torch, vklb, wl, prec, flush_buf, steps):
@@ -531,6 +567,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="distributions", choices=["distributions", "moments"],
+                    help="state form of the timed simulation (moments: omega = 1 workloads only)")
     ap.add_argument("--timed-only", action="store_true",
                     help="only the warm-up and timed steps (no accuracy check, end-to-end run, extras or CPU "
                          "baseline): the launch list of a profile then holds just the timed region's kernels")

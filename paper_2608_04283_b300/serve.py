@@ -2,7 +2,8 @@
 
 Requests (system, grid side, step count, initial data) arrive over time.  The
 server admits them first-in first-out while their device memory fits under an
-HBM budget, keeps every admitted simulation's distributions resident on the
+HBM budget, keeps every simulation in the moment form (all families run at
+omega = 1, where U alone is the state: 2p instead of 10p values a cell), keeps every admitted simulation's distributions resident on the
 GPU, and advances all active simulations of one system family together with a
 single batched launch per step (``vklb_batch_step``); the three families run on
 their own CUDA streams, so their work overlaps on the device.  A tick advances
@@ -33,13 +34,14 @@ FAMILY = {
 FIELDS = {"swe": 3, "euler": 4, "mhd_glm": 9}
 
 
-def device_bytes(system, n, precision="fp32"):
-    """Device memory one simulation holds: two distribution buffers plus the
-    double staging array used by set_state / moments."""
+def device_bytes(system, n, precision="fp32", form="moments"):
+    """Device memory one simulation holds: two state buffers (p or 5p values a
+    cell) plus the double staging array used by set_state / moments."""
     s = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
     pitch = ((n + 31) // 32) * 32
     p = FIELDS[system]
-    return 2 * 5 * p * pitch * n * s + p * n * n * 8
+    q = 1 if form == "moments" else 5
+    return 2 * q * p * pitch * n * s + p * n * n * 8
 
 
 @dataclass
@@ -73,7 +75,7 @@ class Report:
 
 class Server:
     def __init__(self, budget_bytes=120e9, tick_steps=50, precision="fp32", tiles=None, keep_results=False,
-                 clock=None):
+                 clock=None, form="moments"):
         import torch
         self.torch = torch
         self.budget = float(budget_bytes)
@@ -81,13 +83,14 @@ class Server:
         self.precision = precision
         self.tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (64, 16)}
         self.keep = keep_results
+        self.form = form
         self.streams = {k: torch.cuda.Stream() for k in FAMILY}
         self.clock = clock or time.perf_counter
 
     def _make(self, req):
         kw, side = FAMILY[req.system]
         sim = vklb.Sim(req.system, (req.n, req.n), (0.0, 0.0), (side, side), precision=self.precision,
-                       stream=self.streams[req.system], **kw)
+                       stream=self.streams[req.system], form=self.form, **kw)
         sim.set_tiling(*self.tiles[req.system])
         U0 = np.ascontiguousarray(inputs.request_initial_state(req))
         sim.set_state(U0)
@@ -114,7 +117,7 @@ class Server:
             # admission: first in, first out, under the memory budget
             while queue:
                 j = queue[0]
-                need = device_bytes(j.req.system, j.req.n, self.precision)
+                need = device_bytes(j.req.system, j.req.n, self.precision, self.form)
                 if used + need > self.budget and any(active.values()):
                     break
                 queue.pop(0)
@@ -181,14 +184,14 @@ def serve_alone(req, **kw):
     return rep.jobs[0].result
 
 
-def run_plain(requests, precision="fp32", tiles=None):
+def run_plain(requests, precision="fp32", tiles=None, form="moments"):
     """Baseline: the same requests one at a time, one launch per step each."""
     import torch
     tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (64, 16)}
     t0 = time.perf_counter()
     for r in requests:
         kw, side = FAMILY[r.system]
-        sim = vklb.Sim(r.system, (r.n, r.n), (0.0, 0.0), (side, side), precision=precision, **kw)
+        sim = vklb.Sim(r.system, (r.n, r.n), (0.0, 0.0), (side, side), precision=precision, form=form, **kw)
         sim.set_tiling(*tiles[r.system])
         sim.set_state(np.ascontiguousarray(inputs.request_initial_state(r)))
         sim.step(r.steps)
