@@ -156,9 +156,19 @@ struct Impl {
 
   static int step(vklb_sim* s, int64_t n, double t_end) {
     if constexpr (DIM == 1) {
+      // one block; as many threads as the grid has cells, within what the
+      // kernel's registers allow per block
+      static int max_blk = 0;
+      if (max_blk == 0) {
+        cudaFuncAttributes fa;
+        max_blk = cudaFuncGetAttributes(&fa, step1d_kernel<Sys, T, R>) == cudaSuccess ? fa.maxThreadsPerBlock : 256;
+        max_blk = max_blk / 32 * 32;
+        if (max_blk < 32) max_blk = 32;
+        cudaGetLastError();
+      }
       int blk = (int)(((s->nx + 31) / 32) * 32);
-      if (blk > 1024) blk = 1024;
-      if (blk < 64) blk = 64;
+      if (blk > max_blk) blk = max_blk;
+      if (blk < 64 && max_blk >= 64) blk = 64;
       StepArgs<T> a = make_args<T>(s, t_end);
       // n steps in one launch; with t_end the kernel may stop early, so the
       // caller re-reads the step counter (vklb_step_to).
