@@ -268,6 +268,14 @@ int vklb_conservation_totals_noalloc(const void* f_dev, int32_t precision, int32
 /* Number of kernel launches this process has enqueued through the library. */
 int64_t vklb_launch_count(void);
 
+/* Self-test of the device-side failure detection (no counterpart in the paper):
+ * runs the bounded mbarrier wait of the bulk-copy step on a barrier that nothing
+ * arrives at, with a limit of limit_ns nanoseconds (1 us .. 100 ms, else
+ * VKLB_ERR_ARG), and returns what a step would: VKLB_ERR_TIMEOUT from the
+ * device error word.  The wait is bounded, so the GPU and the context stay
+ * usable afterwards.  Synchronises cuda_stream; allocates one control block. */
+int vklb_selftest_wait_timeout(int64_t limit_ns, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -506,15 +506,29 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Gives up after kWaitNs nanoseconds of polling (checked every 64 polls).
+// Gives up after limit_ns nanoseconds of polling (checked every 64 polls).
 constexpr uint64_t kWaitNs = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+    if ((i & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
   }
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at, gives up after limit_ns and latches ERR_TIMEOUT in the error word,
+// as the bulk-copy step does when a copy never lands.  Bounded: it cannot hang.
+static __global__ void wait_selftest_kernel(Ctl* ctl, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0u, limit_ns)) atomicOr(&ctl->err, ERR_TIMEOUT);
+  __syncthreads();
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(

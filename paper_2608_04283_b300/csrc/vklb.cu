@@ -81,6 +81,28 @@ const char* vklb_strerror(int status) {
 
 int64_t vklb_launch_count(void) { return g_launches.load(); }
 
+int vklb_selftest_wait_timeout(int64_t limit_ns, void* cuda_stream) {
+  if (limit_ns < 1000 || limit_ns > 100000000) return VKLB_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Ctl* ctl = nullptr;
+  if (cudaMalloc((void**)&ctl, sizeof(Ctl)) != cudaSuccess) {
+    cudaGetLastError();
+    return VKLB_ERR_NOMEM;
+  }
+  int rc = cuda_status(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+  if (!rc) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(ctl, (uint64_t)limit_ns);
+    g_launches += 1;
+    rc = cuda_status(cudaGetLastError());
+  }
+  Ctl h;
+  if (!rc) rc = cuda_status(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+  cudaFree(ctl);
+  if (rc) return rc;
+  return err_of(h);
+}
+
 // Tile height that makes the grid fill whole waves of resident blocks: with
 // `slots` = SMs x resident blocks per SM and gx tiles across, the first k for
 // which ceil(ny / (k * floor(slots / gx))) <= 256 rows.

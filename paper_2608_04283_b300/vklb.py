@@ -85,6 +85,7 @@ _SIGS = {
     "vklb_batch_step": (C.c_int, [_P, C.c_int64, C.c_int32]),
     "vklb_batch_destroy": (C.c_int, [_P]),
     "vklb_launch_count": (C.c_int64, []),
+    "vklb_selftest_wait_timeout": (C.c_int, [C.c_int64, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -105,6 +106,11 @@ def _check(st, where):
 
 def launch_count():
     return int(_lib.vklb_launch_count())
+
+
+def selftest_wait_timeout(limit_ns=1_000_000, stream=None):
+    """Status of a bounded device wait that is made to run out (ERR_TIMEOUT expected)."""
+    return int(_lib.vklb_selftest_wait_timeout(int(limit_ns), _stream_handle(stream)))
 
 
 def lib():
