@@ -24,6 +24,18 @@ const int kRedBlocks = 296;  // conservation-total pass 1: 2 blocks per SM on 14
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? VKLB_OK : VKLB_ERR_CUDA; }
 
+// True the first time it is called for the current device with this mask:
+// function attributes (the dynamic shared-memory limit) are set per device.
+inline bool first_on_device(std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return true;
+  }
+  const unsigned long long bit = 1ull << dev;
+  return (mask.fetch_or(bit) & bit) == 0;
+}
+
 struct Ops;
 
 struct vklb_sim {
@@ -220,8 +232,8 @@ struct Impl {
 
   static void set_attributes() {
     if constexpr (DIM == 2) {
-      static bool done = false;
-      if (done) return;
+      static std::atomic<unsigned long long> done{0};
+      if (!first_on_device(done)) return;
       cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_u_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -231,7 +243,6 @@ struct Impl {
         cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
       }
-      done = true;
     }
   }
 
@@ -342,12 +353,11 @@ struct BatchImpl {
     if constexpr (DIM != 2) {
       return VKLB_ERR_UNSUPPORTED;
     } else {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_set{0};
+    if (first_on_device(attr_set)) {
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set = true;
     }
     StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
     for (size_t i = 0; i < b->sims.size(); ++i) h[i] = make_args<T>(b->sims[i], -1.0);
