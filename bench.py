@@ -346,6 +346,7 @@ def run_ours(args, wl):
                                                        flush_buf, steps=100)
             extras["moment_form"] = moment_form(torch, vklb, flush_buf)
             extras["batched_swe_256"] = batched_swe(torch, vklb)
+            extras["batched_swe_256_moment_form"] = batched_swe(torch, vklb, form="moments")
             extras["served_mix"] = served_mix(args.served_requests)
         if world == 1 and not args.no_cpu_baseline:
             v, dt, threads = oracle_mlups(wl, wl["n"][1], 1, 0)
@@ -483,7 +484,7 @@ def secondary(torch, vklb, wl, prec, flush_buf, steps):
             "tile": [s.info.tile_x, s.info.tile_y], "variant": s.info.variant, "steps": steps}
 
 
-def batched_swe(torch, vklb, count=256, steps=500):
+def batched_swe(torch, vklb, count=256, steps=500, form="distributions"):
     """Batched form: 256 seeded SWE instances (sides 64..1024, Gaussian humps),
     500 steps each, one launch per step over all instances (CUDA graph), against
     the same instances launched one at a time, each at its own wave-fit tiling.
@@ -494,7 +495,8 @@ def batched_swe(torch, vklb, count=256, steps=500):
     sims = []
     U0s = []
     for sp in specs:
-        s = vklb.Sim("swe", (sp.n, sp.n), (0, 0), (1, 1), omega=1.0, cfl=0.3, precision="fp32", stream=stream)
+        s = vklb.Sim("swe", (sp.n, sp.n), (0, 0), (1, 1), omega=1.0, cfl=0.3, precision="fp32", stream=stream,
+                     form=form)
         s.set_tiling(*tile)
         U0 = torch.from_numpy(inputs.swe_hump_2d(sp.n, sp.amp, sp.x0, sp.y0, sp.sigma)).cuda()
         U0s.append(U0)
@@ -530,7 +532,7 @@ def batched_swe(torch, vklb, count=256, steps=500):
     b.close()
     for s in sims:
         s.close()
-    return {"instances": count, "steps": steps, "cells_total": cells, "tile": list(tile),
+    return {"instances": count, "steps": steps, "cells_total": cells, "tile": list(tile), "form": form,
             "batched_solves_per_s": count / tb, "plain_solves_per_s": count / tp,
             "batched_MLUPS": cells * steps / tb / 1e6, "plain_MLUPS": cells * steps / tp / 1e6,
             "speedup": tp / tb, "batched_vs_plain_rel_l1": diff,
