@@ -130,7 +130,7 @@ __device__ __forceinline__ R relax(R f, R e, R om) {
 
 // Collision (Eq. 42) of one D2Q5 cell: load f, U = sum_q f_q (Eq. 3), the
 // equilibria, relax.
-template <class Sys, class T, class R, int MODE>
+template <class Sys, class T, class R, int MODE, bool KEEP = false>
 __device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict__ fin, size_t plane,
                                              size_t idx, R xinv, R c, R om, int set, R k, R ch,
                                              R (&out)[5][Sys::P]) {
@@ -139,7 +139,10 @@ __device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict
 #pragma unroll
   for (int q = 0; q < 5; ++q)
 #pragma unroll
-    for (int i = 0; i < P; ++i) f[q][i] = Store<T>::ld(fin + (size_t)(q * P + i) * plane + idx);
+    for (int i = 0; i < P; ++i) {
+      const T* ptr = fin + (size_t)(q * P + i) * plane + idx;
+      f[q][i] = KEEP ? Store<T>::ld_keep(ptr) : Store<T>::ld(ptr);
+    }
   R U[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
@@ -255,17 +258,20 @@ struct StateForm {
 };
 
 // Post-collision components of cell (x, y) that MODE needs.
-template <class Sys, class T, class R, int MODE, int FORM>
+template <class Sys, class T, class R, int MODE, int FORM, bool KEEP = false>
 __device__ __forceinline__ void cell_post(const Sys& sys, const T* __restrict__ fin, int x, int y, int nxb, R xinv,
                                           R c, R om, int set, R k, R ch, R (&o)[5][Sys::P]) {
   constexpr int P = Sys::P;
   const size_t b = brick_base(x, y, nxb, StateForm<Sys, FORM>::NS);
   if constexpr (FORM == 0) {
-    collide_d2q5<Sys, T, R, MODE>(sys, fin, kBrick, b, xinv, c, om, set, k, ch, o);
+    collide_d2q5<Sys, T, R, MODE, KEEP>(sys, fin, kBrick, b, xinv, c, om, set, k, ch, o);
   } else {
     R U[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) U[i] = Store<T>::ld(fin + b + (size_t)i * kBrick);
+    for (int i = 0; i < P; ++i) {
+      const T* ptr = fin + b + (size_t)i * kBrick;
+      U[i] = KEEP ? Store<T>::ld_keep(ptr) : Store<T>::ld(ptr);
+    }
     equilibria_d2q5<Sys, R, MODE>(sys, U, xinv, c, set, k, ch, o);
   }
 }
@@ -307,18 +313,21 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   R* ringL = rb2 + 3 * P * TX;           // [P][TY]     f*_1 at x0 - 1, by tile row
   R* ringR = ringL + P * TY;             // [P][TY]     f*_2 at x0 + w
 
-  // x ring: only the component that streams into the tile, from the x split
+  // x ring: only the component that streams into the tile, from the x split.
+  // Read up front for all rows, long before the neighbouring tile reaches the
+  // later rows; the step streams more bytes than L2 holds, so these loads ask
+  // L2 to keep their lines (else they are fetched from DRAM twice).
   for (int t = tx; t < 2 * h; t += blockDim.x) {
     const int side = t >= h;
     const int r = side ? t - h : t;
     const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
     R o[5][P];
     if (!side) {
-      cell_post<Sys, T, R, C_Q1, FORM>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
+      cell_post<Sys, T, R, C_Q1, FORM, true>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) ringL[i * TY + r] = o[0][i];
     } else {
-      cell_post<Sys, T, R, C_Q2, FORM>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
+      cell_post<Sys, T, R, C_Q2, FORM, true>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
       for (int i = 0; i < P; ++i) ringR[i * TY + r] = o[1][i];
     }
@@ -652,7 +661,7 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
     const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
     const size_t idx = brick_base(xr, y0 + r, nxb, NPL);
     R o[5][P];
-    collide_d2q5<Sys, T, R, C_Q1>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
+    collide_d2q5<Sys, T, R, C_Q1, true>(sys, fin, plane, idx, xinv, c, om, set, kk, ch, o);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       if (side)

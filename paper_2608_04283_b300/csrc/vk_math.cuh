@@ -124,19 +124,55 @@ VK_HD R alpha_dd(R a1, R l1, R a2, R l2, R k_over_lmax, R lmax, int set) {
 
 // Storage conversions.
 template <class T> struct Store;
+// ld_keep: a global load whose line L2 should keep longer (an evict_last cache
+// policy), for reads made well before another block reads the same line.
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+#endif
 template <> struct Store<double> {
   typedef double R;
   static VK_HD double ld(const double* p) { return *p; }
+  static VK_HD double ld_keep(const double* p) {
+#ifdef __CUDA_ARCH__
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(l2_keep_policy()));
+    return v;
+#else
+    return *p;
+#endif
+  }
   static VK_HD void st(double* p, double v) { *p = v; }
 };
 template <> struct Store<float> {
   typedef float R;
   static VK_HD float ld(const float* p) { return *p; }
+  static VK_HD float ld_keep(const float* p) {
+#ifdef __CUDA_ARCH__
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(l2_keep_policy()));
+    return v;
+#else
+    return *p;
+#endif
+  }
   static VK_HD void st(float* p, float v) { *p = v; }
 };
 template <> struct Store<__nv_bfloat16> {
   typedef float R;
   static VK_HD float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static VK_HD float ld_keep(const __nv_bfloat16* p) {
+#ifdef __CUDA_ARCH__
+    unsigned short b;
+    asm volatile("ld.global.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(b) : "l"(p), "l"(l2_keep_policy()));
+    return __bfloat162float(__ushort_as_bfloat16(b));
+#else
+    return __bfloat162float(*p);
+#endif
+  }
   static VK_HD void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
