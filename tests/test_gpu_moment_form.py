@@ -106,6 +106,23 @@ def test_moment_form_equals_distribution_form(vk, name, precision, dtype, tol):
         s.close()
 
 
+def test_moment_form_bf16_storage(vk):
+    """BF16 storage of U (FP32 arithmetic): the error is bounded by BF16 rounding
+    of the stored moments (about 4e-3 relative a step), the same bound as the
+    distribution form's BF16 experiment."""
+    n = (44, 40)
+    U0, lo, hi, kw, sysm = _case("euler", n)      # every field O(1), as in the distribution form's test
+    sim = vk.Sim("euler", n, lo, hi, precision="bf16", omega=1.0, cfl=0.3, form="moments")
+    assert sim.info.bytes_per_lup == 2 * 4 * 2
+    sim.set_state(U0)
+    sim.step(10)
+    ref = ovklb.Sim(sysm, n, lo, hi, omega=1.0, nu=0.3)
+    ref.set_state(U0)
+    ref.run(10)
+    assert rel_l1(sim.moments(), ref.moments()).max() <= 2e-2
+    sim.close()
+
+
 def test_moment_form_lands_on_t_and_conserves(vk):
     n = (40, 40)
     U0, lo, hi, kw, sysm = _case("swe", n)
