@@ -236,7 +236,9 @@ const char* vklb_strerror(int status);
  * keeps its own xi and c_h).  The batch borrows the simulations (they must
  * outlive it); their per-simulation state is left as if each had been stepped
  * alone.  vklb_batch_step(n) enqueues n steps on the stream of the first
- * simulation; use_graph != 0 captures them in a CUDA graph and replays it. */
+ * simulation; use_graph != 0 captures them in a CUDA graph and replays it.
+ * VKLB_ERR_STATE if a member's state form, kernel variant or state changed
+ * (vklb_set_form / vklb_set_variant) since the batch was created. */
 int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out);
 /* Same ranges as vklb_set_tiling.  tile_y = -1: the members' grids differ, so
  * the height (1..64) maximises (fill of the last wave of the work-list) x

@@ -588,6 +588,10 @@ int vklb_batch_set_tiling(vklb_batch* b, int32_t tx, int32_t ty) {
 int vklb_batch_step(vklb_batch* b, int64_t n, int32_t use_graph) {
   if (!b || n < 0) return VKLB_ERR_ARG;
   if (n == 0) return VKLB_OK;
+  // a member whose form, kernel variant or state changed since the batch was
+  // made would be stepped with the wrong kernel over a differently sized buffer
+  for (const vklb_sim* s : b->sims)
+    if (!s->ready || kernel_variant(s) != b->variant || s->stages != b->stages) return VKLB_ERR_STATE;
   return b->ops->batch(b, n, use_graph);
 }
 

@@ -175,6 +175,17 @@ def test_moment_form_batch_bitwise(vk):
             group.append(s)
     b = vk.Batch(sims, tile=(64, 8))
     b.step(12, graph=True)
+    sims[1].set_form("distributions")             # a member changed behind the batch's back
+    with pytest.raises(vk.VKLBError) as e:
+        b.step(1)
+    assert e.value.status == vk.ERR_STATE
+    b.close()
+    sims[1].close()
+    sims[1] = vk.Sim("swe", (96, 96), (0, 0), (1, 1), precision="fp32", omega=1.0, cfl=0.3, form="moments")
+    sims[1].set_tiling(64, 8)
+    sims[1].set_state(inputs.swe_hump_2d(96, 0.4, 0.5, 0.5, 0.08))
+    b = vk.Batch(sims[1:2], tile=(64, 8))
+    b.step(12, graph=True)
     b.close()
     for s in solo:
         s.step(12)
