@@ -30,8 +30,10 @@
  *    device error word and returned by the next synchronising call
  *    (vklb_sync, vklb_moments, vklb_conservation_totals, vklb_time,
  *    vklb_get_state).  No call aborts the process.
- *  - The library allocates its own device memory (cudaMalloc) for the
- *    distributions and a few control words; vklb_destroy frees it.
+ *  - The library allocates its own device memory (cudaMalloc) for the state
+ *    (distributions, or moments in the moment form of vklb_set_form) and a few
+ *    control words; vklb_destroy frees it.  vklb_conservation_totals_noalloc
+ *    is the one call that allocates nothing.
  */
 #ifndef VKLB_H
 #define VKLB_H
@@ -50,7 +52,8 @@ typedef enum {
   VKLB_ERR_CUDA = -3,         /* a CUDA runtime call failed (no device, launch error) */
   VKLB_ERR_NONPHYSICAL = -4,  /* NaN or non-positive h / rho / p produced on the device */
   VKLB_ERR_CFL = -5,          /* fixed lattice speed below max |lambda| (Eq. 28 violated) */
-  VKLB_ERR_TIMEOUT = -6,      /* reserved: a bounded device wait gave up */
+  VKLB_ERR_TIMEOUT = -6,      /* a bounded device wait gave up (bulk-copy step variant; see
+                                 vklb_selftest_wait_timeout) */
   VKLB_ERR_STATE = -7,        /* call out of order (e.g. stepping before vklb_set_state) */
   VKLB_ERR_UNSUPPORTED = -8,  /* combination not built (e.g. D1Q3 with MHD-GLM) */
   VKLB_ERR_LIMIT = -9         /* beyond the fixed scratch of vklb_conservation_totals_noalloc */
@@ -118,8 +121,9 @@ typedef struct {
   int32_t precision;         /* vklb_precision */
   int32_t store_bytes;       /* bytes per stored distribution value */
   int64_t cells;             /* nx * ny */
-  int64_t bytes_per_lup;     /* algorithmic bytes per cell update: 2 * q * p * store_bytes */
-  int64_t state_bytes;       /* bytes of one distribution buffer */
+  int64_t bytes_per_lup;     /* algorithmic bytes per cell update: 2 * q * p * store_bytes
+                                (moment form: 2 * p * store_bytes) */
+  int64_t state_bytes;       /* bytes of one state buffer (distributions, or moments) */
   double dx;
   int32_t tile_x, tile_y;    /* launch shape of the step kernel */
   int32_t kernels_per_step;  /* kernel launches one vklb_step(1) makes */
