@@ -1,0 +1,61 @@
+"""Argument checks of the C ABI that run before any CUDA call, so they are
+tested here on the CPU: empty and too-small grids, the parameter ranges the
+paper fixes (omega in (0, 2], Sec. 2.3; 0 < nu <= 1, Eq. 28; dx == dy on D2Q5,
+Sec. 3.4), combinations that are not built, and null handles."""
+import ctypes as C
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def vk():
+    from paper_2608_04283_b300 import build
+    build.build()
+    from paper_2608_04283_b300 import vklb
+    return vklb
+
+
+def _status(vk, fn):
+    with pytest.raises(vk.VKLBError) as e:
+        fn()
+    return e.value.status
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(n=(0, 32)), "ERR_ARG"),                              # empty grid
+    (dict(n=(32, 0)), "ERR_ARG"),
+    (dict(n=(2,), lo=(0.0,), hi=(1.0,)), "ERR_ARG"),           # D1Q3 needs 3 cells
+    (dict(omega=0.0), "ERR_ARG"), (dict(omega=2.5), "ERR_ARG"),
+    (dict(cfl=0.0), "ERR_ARG"), (dict(cfl=1.5), "ERR_ARG"),
+    (dict(k=-1.0), "ERR_ARG"),
+    (dict(n=(32, 16), hi=(1.0, 1.0)), "ERR_ARG"),            # dx != dy
+    (dict(hi=(0.0, 1.0)), "ERR_ARG"),                          # empty domain
+    (dict(bc="characteristic"), "ERR_UNSUPPORTED"),           # characteristic boundaries are 1D (Sec. 3.3)
+    (dict(gamma=1.0), "ERR_ARG"),                              # ideal gas needs gamma > 1
+])
+def test_create_rejects(vk, kw, status):
+    args = dict(system="euler", n=(32, 32), lo=(0.0, 0.0), hi=(1.0, 1.0), precision="fp32")
+    args.update(kw)
+    system, n, lo, hi = args.pop("system"), args.pop("n"), args.pop("lo"), args.pop("hi")
+    assert _status(vk, lambda: vk.Sim(system, n, lo, hi, **args)) == getattr(vk, status)
+
+
+def test_create_rejects_system_parameters(vk):
+    assert _status(vk, lambda: vk.Sim("swe", (32, 32), (0, 0), (1, 1), g=0.0)) == vk.ERR_ARG
+    assert _status(vk, lambda: vk.Sim("mhd_glm", (32, 32), (0, 0), (1, 1), ch_factor=0.0)) == vk.ERR_ARG
+    assert _status(vk, lambda: vk.Sim("mhd_glm", (32,), (0.0,), (1.0,))) == vk.ERR_UNSUPPORTED   # MHD-GLM is 2D
+
+
+def test_null_handles(vk):
+    lib = vk._lib
+    assert lib.vklb_step(None, 1) == vk.ERR_ARG
+    assert lib.vklb_sync(None) == vk.ERR_ARG
+    assert lib.vklb_destroy(None) == vk.ERR_ARG
+    assert lib.vklb_set_form(None, 1) == vk.ERR_ARG
+    assert lib.vklb_set_tiling(None, 128, 8) == vk.ERR_ARG
+    assert lib.vklb_batch_step(None, 1, 0) == vk.ERR_ARG
+    info = vk.Info()
+    assert lib.vklb_info(None, C.byref(info)) == vk.ERR_ARG
+    assert lib.vklb_create(None, vk.D2Q5, None, None, None, 0.0, 1, None, None) == vk.ERR_ARG
+    for st in (vk.OK, vk.ERR_ARG, vk.ERR_TIMEOUT, vk.ERR_LIMIT):
+        assert lib.vklb_strerror(st)
