@@ -87,19 +87,22 @@ class Server:
         self.streams = {k: torch.cuda.Stream() for k in FAMILY}
         self.clock = clock or time.perf_counter
 
-    def _make(self, req):
+    def _make(self, req, U0=None):
         kw, side = FAMILY[req.system]
         sim = vklb.Sim(req.system, (req.n, req.n), (0.0, 0.0), (side, side), precision=self.precision,
                        stream=self.streams[req.system], form=self.form, **kw)
         sim.set_tiling(*self.tiles[req.system])
-        U0 = np.ascontiguousarray(inputs.request_initial_state(req))
-        sim.set_state(U0)
+        if U0 is None:
+            U0 = inputs.request_initial_state(req)
+        sim.set_state(np.ascontiguousarray(U0))
         return sim
 
-    def run(self, requests, realtime=True):
+    def run(self, requests, realtime=True, payloads=None):
         """Serve ``requests`` (sorted by arrival).  With realtime, arrivals are
         honoured against the wall clock from the start; otherwise everything is
-        available at once.  Returns a Report."""
+        available at once.  ``payloads`` optionally maps a request id to its
+        initial state U_0 (the data a client sends with the request); without
+        it the server generates U_0 itself.  Returns a Report."""
         t0 = self.clock()
         now = lambda: self.clock() - t0
         pending = list(requests)
@@ -121,7 +124,7 @@ class Server:
                 if used + need > self.budget and any(active.values()):
                     break
                 queue.pop(0)
-                j.sim = self._make(j.req)
+                j.sim = self._make(j.req, None if payloads is None else payloads.get(j.req.rid))
                 j.t_admit = now()
                 j.status = "running"
                 j.need = need
@@ -184,7 +187,7 @@ def serve_alone(req, **kw):
     return rep.jobs[0].result
 
 
-def run_plain(requests, precision="fp32", tiles=None, form="moments"):
+def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=None):
     """Baseline: the same requests one at a time, one launch per step each."""
     import torch
     tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (64, 16)}
@@ -193,7 +196,8 @@ def run_plain(requests, precision="fp32", tiles=None, form="moments"):
         kw, side = FAMILY[r.system]
         sim = vklb.Sim(r.system, (r.n, r.n), (0.0, 0.0), (side, side), precision=precision, form=form, **kw)
         sim.set_tiling(*tiles[r.system])
-        sim.set_state(np.ascontiguousarray(inputs.request_initial_state(r)))
+        U0 = inputs.request_initial_state(r) if payloads is None else payloads[r.rid]
+        sim.set_state(np.ascontiguousarray(U0))
         sim.step(r.steps)
         sim.moments()
         sim.close()
