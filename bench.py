@@ -59,10 +59,15 @@ KERNEL_SOURCES = ("vk_ctl.cuh", "vk_kernels.cuh", "vk_math.cuh", "vk_systems.cuh
 
 
 def csrc_hash():
+    """Hash of the kernel sources' code: comments and blank lines are left out,
+    so editing a comment does not invalidate a recorded profile."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2608_04283_b300", "csrc")
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(d, f), "rb").read())
+        for line in open(os.path.join(d, f), encoding="utf-8"):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

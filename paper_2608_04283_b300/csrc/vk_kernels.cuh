@@ -1,9 +1,14 @@
 // CUDA kernels of the VKLB step (Sec. 3.5, Fig. 5) for sm_103a.
 //
-// Layout in HBM: f[q][k][y][x] (structure of arrays), q = lattice velocity,
-// k = conserved field, x fastest; two such buffers ping-pong between steps.
+// Layout in HBM (two buffers ping-pong between steps): D2Q5 in 32-cell bricks,
+// component q p + k of cell (x, y) at ((y nxb + x / 32) 5p + q p + k) 32 + x % 32
+// (brick_base below); D1Q3 in component planes f[(q p + k) nx + x].  The moment
+// form (omega = 1) stores the p fields of U in bricks of p components.
 //
-// step2d_kernel: one launch = one step on D2Q5, periodic (Eq. 37).  A block owns
+// step2d_kernel: one launch = one step on D2Q5, periodic (Eq. 37).  (Its
+// variants: step2d_lb_kernel, the same body with a register bound; step2d_u_kernel,
+// the moment form; step2d_tma_kernel, rows staged by bulk copies; the batched
+// kernel over a work-list of tiles of many simulations.)  A block owns
 // a tile of TX columns x TY rows; each thread owns one column and marches up the
 // tile.  Per cell it loads the 5p values of f^n (coalesced across the warp),
 // forms U = sum_q f_q (Eq. 3), splits F^(1), F^(2) (Eqs. 25-27), builds the
