@@ -83,6 +83,7 @@ struct vklb_batch {
   int nwork;
   int variant, stages;
   std::vector<unsigned char> h_desc;
+  std::vector<BatchWork> h_work;   // host copy of the work-list (source of its async upload)
   cudaStream_t stream;
   const Ops* ops;
   int64_t graph_n;

@@ -478,19 +478,29 @@ int vklb_put_state(vklb_sim* s, const void* blob, size_t bytes) {
 }
 
 // ------------------------------------------------------------------- batches
+// The batch's device buffers are stream-ordered allocations on its own stream
+// (cudaMallocAsync / cudaFreeAsync): creating and destroying a batch then never
+// synchronises the device, so a server that rebuilds batches as its membership
+// changes does not stall the other families' work.
 static int batch_build_work(vklb_batch* b) {
-  std::vector<BatchWork> w;
+  std::vector<BatchWork>& w = b->h_work;
+  cudaStreamSynchronize(b->own);   // the previous list's upload has finished reading h_work
+  w.clear();
   for (size_t i = 0; i < b->sims.size(); ++i) {
     const vklb_sim* s = b->sims[i];
     const int gx = (int)((s->nx + b->tile_x - 1) / b->tile_x), gy = (int)((s->ny + b->tile_y - 1) / b->tile_y);
     for (int by = 0; by < gy; ++by)
       for (int bx = 0; bx < gx; ++bx) w.push_back(BatchWork{(int)i, bx, by});
   }
-  if (b->d_work) cudaFree(b->d_work);
+  if (b->d_work) cudaFreeAsync(b->d_work, b->own);
   b->d_work = nullptr;
-  if (cudaMalloc((void**)&b->d_work, sizeof(BatchWork) * w.size()) != cudaSuccess) return VKLB_ERR_NOMEM;
+  if (cudaMallocAsync((void**)&b->d_work, sizeof(BatchWork) * w.size(), b->own) != cudaSuccess) {
+    cudaGetLastError();
+    return VKLB_ERR_NOMEM;
+  }
   b->nwork = (int)w.size();
-  int st = cuda_status(cudaMemcpy(b->d_work, w.data(), sizeof(BatchWork) * w.size(), cudaMemcpyHostToDevice));
+  int st = cuda_status(
+      cudaMemcpyAsync(b->d_work, w.data(), sizeof(BatchWork) * w.size(), cudaMemcpyHostToDevice, b->own));
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->gexec = nullptr;
@@ -521,15 +531,16 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
   b->stream = s0->stream;
   b->ops = s0->ops;
   b->h_desc.resize(s0->ops->args_bytes * n);
-  if (cudaMalloc(&b->d_desc, b->h_desc.size()) != cudaSuccess) {
-    delete b;
-    return VKLB_ERR_NOMEM;
-  }
   if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
     vklb_batch_destroy(b);
     return VKLB_ERR_CUDA;
+  }
+  if (cudaMallocAsync(&b->d_desc, b->h_desc.size(), b->own) != cudaSuccess) {
+    cudaGetLastError();
+    vklb_batch_destroy(b);
+    return VKLB_ERR_NOMEM;
   }
   int st = batch_build_work(b);
   if (st) {
@@ -597,11 +608,13 @@ int vklb_batch_step(vklb_batch* b, int64_t n, int32_t use_graph) {
 
 int vklb_batch_destroy(vklb_batch* b) {
   if (!b) return VKLB_ERR_ARG;
-  if (b->own) cudaStreamSynchronize(b->own);
+  if (b->own) cudaStreamSynchronize(b->own);   // this batch's own work only
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  cudaFree(b->d_desc);
-  cudaFree(b->d_work);
+  if (b->own) {
+    if (b->d_desc) cudaFreeAsync(b->d_desc, b->own);
+    if (b->d_work) cudaFreeAsync(b->d_work, b->own);
+  }
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->own) cudaStreamDestroy(b->own);
