@@ -84,8 +84,8 @@ VK_HD size_t cell_base(int Q, int P, int x, int y, int pitch) {
 }
 VK_HD size_t comp_stride(int Q, int pitch, int ny) { return Q != 3 ? (size_t)kBrick : (size_t)pitch * ny; }
 
-// Which post-collision components a cell must produce.
-enum CollideMode { C_FULL = 0, C_Q1 = 1, C_Q2 = 2, C_Q4 = 3, C_Q5 = 4 };
+// Which post-collision components a cell must produce (C_QX: f*_1 and f*_2).
+enum CollideMode { C_FULL = 0, C_Q1 = 1, C_Q2 = 2, C_Q4 = 3, C_Q5 = 4, C_QX = 5 };
 
 // Weighted equilibria of Eq. (41) from U, the components MODE needs:
 //   e1 = c U + F(1,+)/xi, e2 = c U - F(1,-)/xi, e4 = c U + F(2,+)/xi,
@@ -109,7 +109,7 @@ __device__ __forceinline__ void equilibria_d2q5(const Sys& sys, const R (&U)[Sys
     return;
   }
   R Fp[P], F[P];
-  if (MODE == C_Q1 || MODE == C_Q2) {
+  if (MODE == C_Q1 || MODE == C_Q2 || MODE == C_QX) {
     sys.split(U, 0, set, k, ch, Fp, F);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -155,7 +155,7 @@ __device__ __forceinline__ void collide_d2q5(const Sys& sys, const T* __restrict
   equilibria_d2q5<Sys, R, MODE>(sys, U, xinv, c, set, k, ch, e);
 #pragma unroll
   for (int i = 0; i < P; ++i) {
-    if (MODE == C_FULL || MODE == C_Q1 || MODE == C_Q2) {
+    if (MODE == C_FULL || MODE == C_Q1 || MODE == C_Q2 || MODE == C_QX) {
       out[0][i] = relax(f[0][i], e[0][i], om);
       out[1][i] = relax(f[1][i], e[1][i], om);
     }
@@ -288,15 +288,13 @@ __device__ __forceinline__ void cell_post(const Sys& sys, const T* __restrict__ 
 // the second read then hitting L2.  Going up, f^{n+1}_4(y) = f*_4(y - 1) comes
 // from the previous row and f^{n+1}_5(y) = f*_5(y + 1) from the next one; going
 // down the two roles swap.
-// DIR = +1 / -1 fixes the direction at compile time (two bodies, used for the
-// small systems); DIR = 0 picks it at run time in one body (MHD-GLM, whose
-// arithmetic is large enough that a second copy costs more in instruction-cache
-// misses than the register selects).
+// DIR = +1 / -1 fixes the direction at compile time (two bodies; the small
+// systems, whose code fits the instruction cache either way).
 template <class Sys, class T, class R, int DIR, int FORM>
 __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const BlockConsts<Sys, R>& bc, int bx,
                                                 int by, int TX, int TY, unsigned char* smem) {
   constexpr int P = Sys::P;
-  const bool up = DIR > 0 ? true : (DIR < 0 ? false : (by & 1) == 0);
+  const bool up = DIR > 0;
   const Sys sys = bc.sys;
   const int tx = threadIdx.x;
   const int x0 = bx * TX, y0 = by * TY;
@@ -438,6 +436,131 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   commit_max<R>(m1, m2, bad, a.ctl, s1);
 }
 
+// The same march for a system whose split is long (MHD-GLM: two 9-wave
+// eigen-decompositions a cell), written so that the split's code appears as few
+// times as possible: the direction is picked at run time, the ring rows behind
+// and ahead of the tile go through the same call as the tile's rows (computing
+// an x split they do not need, 2 rows a tile), and the x ring's two sides share
+// one call.  Each inlined copy of the split is several kilobytes of code; with
+// one copy per call site the march above holds ten, which overflow the
+// instruction cache (measured: 68 % hit rate, instruction fetch the largest
+// stall).  Rows in march order: R_-1 (the ring row behind), R_0 .. R_{h-1}, R_h
+// (the ring row ahead); row r is finished once R_{r+1} is collided.
+template <class Sys, class T, class R, int FORM>
+__device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const BlockConsts<Sys, R>& bc, int bx,
+                                                int by, int TX, int TY, unsigned char* smem) {
+  constexpr int P = Sys::P;
+  const bool up = (by & 1) == 0;
+  const Sys sys = bc.sys;
+  const int tx = threadIdx.x;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int nx = a.nx, ny = a.ny;
+  const int w = min(TX, nx - x0), h = min(TY, ny - y0);
+  const int x = x0 + tx;
+  const bool act = tx < w;
+  constexpr int NS = StateForm<Sys, FORM>::NS;
+  const int nxb = a.pitch / kBrick;
+  const T* __restrict__ fin = a.f[a.parity];
+  T* __restrict__ fout = a.f[a.parity ^ 1];
+  const int s1 = (a.slot + 1) % 3;
+  const R xinv = bc.xinv, ch = bc.ch, c = bc.c, om = bc.om, kk = bc.k;
+  const int set = a.set;
+
+  R* rb1 = reinterpret_cast<R*>(smem);   // [3][P][TX]  f*_1 of the row
+  R* rb2 = rb1 + 3 * P * TX;             // [3][P][TX]  f*_2 of the row
+  R* ringL = rb2 + 3 * P * TX;           // [P][TY]     f*_1 at x0 - 1, by tile row
+  R* ringR = ringL + P * TY;             // [P][TY]     f*_2 at x0 + w
+
+  // x ring, read up front with the L2 keep policy (as in the march above);
+  // the loops stay rolled so that the split is not copied
+#pragma unroll 1
+  for (int t = tx; t < 2 * h; t += blockDim.x) {
+    const int side = t >= h;
+    const int r = side ? t - h : t;
+    const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
+    R o[5][P];
+    cell_post<Sys, T, R, C_QX, FORM, true>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
+    R* dst = side ? ringR : ringL;
+#pragma unroll
+    for (int i = 0; i < P; ++i) dst[i * TY + r] = side ? o[1][i] : o[0][i];
+  }
+
+  // bprev: the component streaming along the march of R_{r-1}; bcur: the same
+  // of R_r; f3c: f*_3 of R_r
+  R bprev[P], bcur[P], f3c[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) bprev[i] = bcur[i] = f3c[i] = R(0);
+  R m1 = R(0), m2 = R(0);
+  bool bad = false;
+#pragma unroll 1
+  for (int r = -1; r <= h; ++r) {
+    R an[P], bn[P], f3n[P];
+    if (act) {
+      const int jr = ((up ? y0 + r : y0 + h - 1 - r) + ny) % ny;
+      R o[5][P];
+      cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, jr, nxb, xinv, c, om, set, kk, ch, o);
+      const int nb = (r + 3) % 3;
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        if (r >= 0 && r < h) {
+          rb1[(nb * P + i) * TX + tx] = o[0][i];
+          rb2[(nb * P + i) * TX + tx] = o[1][i];
+        }
+        f3n[i] = o[2][i];
+        bn[i] = up ? o[3][i] : o[4][i];
+        an[i] = up ? o[4][i] : o[3][i];
+      }
+    }
+    if (r >= 1) {
+      // finish row r - 1 of the march
+      __syncthreads();
+      if (act) {
+        const int rr = r - 1;
+        const int j = up ? y0 + rr : y0 + h - 1 - rr;
+        const int cb = rr % 3;
+        const size_t base = brick_base(x, j, nxb, NS);
+        const int rt = j - y0;
+        R U[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          R g[5];
+          g[0] = tx == 0 ? ringL[i * TY + rt] : rb1[(cb * P + i) * TX + tx - 1];
+          g[1] = tx == w - 1 ? ringR[i * TY + rt] : rb2[(cb * P + i) * TX + tx + 1];
+          g[2] = f3c[i];
+          g[3] = up ? bprev[i] : an[i];
+          g[4] = up ? an[i] : bprev[i];
+          const T* tp = nullptr;
+          if constexpr (FORM == 0) {
+            R acc = R(0);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+              Store<T>::st(fout + (size_t)(q * P + i) * kBrick + base, g[q]);
+              acc += round_store(g[q], tp);
+            }
+            U[i] = acc;
+          } else {
+            // Eq. (3), summed in the order of the distribution form's next collision
+            const R u = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];
+            Store<T>::st(fout + (size_t)i * kBrick + base, u);
+            U[i] = round_store(u, tp);
+          }
+        }
+        R e1, e2;
+        bad |= !sys.epilogue(U, e1, e2);
+        m1 = vmax(m1, e1);
+        m2 = vmax(m2, e2);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      bprev[i] = bcur[i];
+      bcur[i] = bn[i];
+      f3c[i] = f3n[i];
+    }
+  }
+  commit_max<R>(m1, m2, bad, a.ctl, s1);
+}
+
 template <class Sys, class T, class R, int FORM = 0>
 __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by, int TX, int TY,
                                             unsigned char* smem) {
@@ -480,7 +603,7 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     else
       step2d_tile_dir<Sys, T, R, +1, FORM>(a, s_bc, bx, by, TX, TY, smem);
   } else {
-    step2d_tile_dir<Sys, T, R, 0, FORM>(a, s_bc, bx, by, TX, TY, smem);
+    step2d_tile_one<Sys, T, R, FORM>(a, s_bc, bx, by, TX, TY, smem);
   }
 }
 

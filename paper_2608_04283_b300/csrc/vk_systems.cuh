@@ -353,9 +353,35 @@ struct MHDGLM {
     return rho > R(0) && p > R(0);
   }
 
+  // Both directions through one copy of split_x (a loop the compiler keeps):
+  // the split is several kilobytes of code, and a second inlined copy costs
+  // more in instruction-cache misses than the loop's register moves.
   VK_HD void split2(const R* U, int set, R k, R ch, R* Fp1, R* F1, R* Fp2, R* F2) const {
+#ifndef VK_SPLIT2_UNROLLED
+#pragma unroll 1
+    for (int d = 0; d < 2; ++d) {
+      const bool y = d == 1;
+      const R V[9] = {U[0], y ? U[2] : U[1], y ? U[1] : U[2], U[3], U[4],
+                      y ? U[6] : U[5], y ? U[5] : U[6], U[7], U[8]};
+      R a[9], b[9];
+      split_x(V, set, k, ch, a, b);
+      if (!y) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          Fp1[i] = a[i];
+          F1[i] = b[i];
+        }
+      } else {
+        Fp2[0] = a[0]; Fp2[1] = a[2]; Fp2[2] = a[1]; Fp2[3] = a[3]; Fp2[4] = a[4];
+        Fp2[5] = a[6]; Fp2[6] = a[5]; Fp2[7] = a[7]; Fp2[8] = a[8];
+        F2[0] = b[0]; F2[1] = b[2]; F2[2] = b[1]; F2[3] = b[3]; F2[4] = b[4];
+        F2[5] = b[6]; F2[6] = b[5]; F2[7] = b[7]; F2[8] = b[8];
+      }
+    }
+#else
     split(U, 0, set, k, ch, Fp1, F1);
     split(U, 1, set, k, ch, Fp2, F2);
+#endif
   }
 
   // m1 = max_d (|u_d| + c_f,d), m2 = max_d c_f,d, physical test of U^{n+1}
