@@ -405,17 +405,21 @@ def accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps, form="distributions"):
     out["steps"] = steps
     out["rel_l1_max_field"] = float(rel_norm(a, b, lambda x: np.abs(x).sum()).max())
     out["rel_linf_max_field"] = float(rel_norm(a, b, lambda x: np.abs(x).max()).max())
-    out["rule"] = ("per field |a - b| / |b|; a field whose reference norm is below 1e-12 of the largest "
-                   "field's (e.g. psi, B_z, m_z of Orszag-Tang, zero up to rounding) is scaled by the largest")
+    out["rule"] = ("per field |a - b| / |b|; a field whose reference norm is below 1e-2 of the largest "
+                   "field's (psi, B_z, m_z of Orszag-Tang: zero or at rounding level) is scaled by the largest")
     return out
 
 
-def rel_norm(a, b, norm):
+def rel_norm(a, b, norm, small=1e-2):
+    """Per-field norm of a - b relative to b's; a field whose norm is below
+    ``small`` of the largest field's is measured against the largest instead
+    (MHD-GLM's psi stays at rounding level in Orszag-Tang, 1e-7 of the energy,
+    and the divergence errors that feed it differ from FP32 to FP64 run)."""
     big = max(norm(b[k]) for k in range(b.shape[0]))
     out = []
     for k in range(b.shape[0]):
         s = norm(b[k])
-        if s <= 1e-12 * big:
+        if s <= small * big:
             s = big
         out.append(norm(a[k] - b[k]) / s)
     return np.array(out)

@@ -161,7 +161,11 @@ struct Impl {
     return cuda_status(cudaGetLastError());
   }
 
-  static size_t smem_bytes(int tx, int ty) { return (size_t)(6 * P * tx + 2 * P * ty) * sizeof(R); }
+  // rows f*_1 / f*_2 (3 each) and the x ring; the long-split march (P > 4)
+  // also keeps its column state (3 rows of P) in shared memory
+  static size_t smem_bytes(int tx, int ty) {
+    return (size_t)(((P > 4) ? 9 : 6) * P * tx + 2 * P * ty) * sizeof(R);
+  }
   static size_t smem_bytes_v(int variant, int tx, int ty, int d) {
     if (variant == 1) return TmaLayout<T>::template make<R, P>(tx, ty, d).bytes;
     return smem_bytes(tx, ty);

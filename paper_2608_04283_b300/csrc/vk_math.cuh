@@ -126,6 +126,9 @@ VK_HD R alpha_dd(R a1, R l1, R a2, R l2, R k_over_lmax, R lmax, int set) {
 template <class T> struct Store;
 // ld_keep: a global load whose line L2 should keep longer (an evict_last cache
 // policy), for reads made well before another block reads the same line.
+// ld_again: a second read of a value this thread loaded moments before (an L1
+// hit), issued as its own instruction so that the compiler cannot keep the first
+// load's register live in its place.
 #ifdef __CUDA_ARCH__
 __device__ __forceinline__ unsigned long long l2_keep_policy() {
   unsigned long long pol;
@@ -145,6 +148,15 @@ template <> struct Store<double> {
     return *p;
 #endif
   }
+  static VK_HD double ld_again(const double* p) {
+#ifdef __CUDA_ARCH__
+    double v;
+    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+#else
+    return *p;
+#endif
+  }
   static VK_HD void st(double* p, double v) { *p = v; }
 };
 template <> struct Store<float> {
@@ -159,6 +171,15 @@ template <> struct Store<float> {
     return *p;
 #endif
   }
+  static VK_HD float ld_again(const float* p) {
+#ifdef __CUDA_ARCH__
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+#else
+    return *p;
+#endif
+  }
   static VK_HD void st(float* p, float v) { *p = v; }
 };
 template <> struct Store<__nv_bfloat16> {
@@ -168,6 +189,15 @@ template <> struct Store<__nv_bfloat16> {
 #ifdef __CUDA_ARCH__
     unsigned short b;
     asm volatile("ld.global.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(b) : "l"(p), "l"(l2_keep_policy()));
+    return __bfloat162float(__ushort_as_bfloat16(b));
+#else
+    return __bfloat162float(*p);
+#endif
+  }
+  static VK_HD float ld_again(const __nv_bfloat16* p) {
+#ifdef __CUDA_ARCH__
+    unsigned short b;
+    asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(b) : "l"(p));
     return __bfloat162float(__ushort_as_bfloat16(b));
 #else
     return __bfloat162float(*p);

@@ -357,7 +357,6 @@ struct MHDGLM {
   // the split is several kilobytes of code, and a second inlined copy costs
   // more in instruction-cache misses than the loop's register moves.
   VK_HD void split2(const R* U, int set, R k, R ch, R* Fp1, R* F1, R* Fp2, R* F2) const {
-#ifndef VK_SPLIT2_UNROLLED
 #pragma unroll 1
     for (int d = 0; d < 2; ++d) {
       const bool y = d == 1;
@@ -378,10 +377,6 @@ struct MHDGLM {
         F2[5] = b[6]; F2[6] = b[5]; F2[7] = b[7]; F2[8] = b[8];
       }
     }
-#else
-    split(U, 0, set, k, ch, Fp1, F1);
-    split(U, 1, set, k, ch, Fp2, F2);
-#endif
   }
 
   // m1 = max_d (|u_d| + c_f,d), m2 = max_d c_f,d, physical test of U^{n+1}
