@@ -4,7 +4,8 @@ max_rel:  per field max_x |a - b| / max_x |b| (reading R16 of the tolerance); a
           field that is identically zero in the reference must be zero to the
           absolute tolerance scaled by the largest field.
 rel_l1:   per field sum |a - b| / sum |b|, with the same rule for zero fields.
-rel_l1_coupled: rel_l1, but a field below 1e-2 of the largest (in L1) takes the
+max_rel_coupled / rel_l1_coupled: max_rel / rel_l1, but a field below 1e-2 of
+          the largest takes the
           largest field's norm as its scale.  For FP32 MHD-GLM: psi (and a weak
           B_z or m_z) is carried by distribution components dominated by the
           c_h B_x / B coupling terms of Eq. (58), so its rounding error scales
@@ -38,3 +39,7 @@ def rel_l1(a, b):
 
 def rel_l1_coupled(a, b):
     return _per_field(a, b, lambda x: np.sum(np.abs(x)), small=1e-2)
+
+
+def max_rel_coupled(a, b):
+    return _per_field(a, b, lambda x: np.max(np.abs(x)), small=1e-2)

@@ -1,6 +1,7 @@
 """Parity at the benchmark's full size and launch shape: the 1024^2 Euler
 isentropic vortex (omega 2, CFL 0.3, c 0.05, k 2) in the launch shape bench.py
-times (the autotuned tile and kernel variant), in FP32 and FP64.
+times (the autotuned tile and kernel variant), in FP32 and FP64; and the 2048^2
+MHD-GLM Orszag-Tang vortex (omega 1, CFL 0.3, c_h factor 6) the same way.
 
 The oracle cannot step 10^6 cells in seconds, but one step of the update at a
 cell depends only on its 5-point neighbourhood and on the global lattice speed
@@ -21,7 +22,7 @@ import pytest
 
 from oracle import systems, vklb as ovklb
 from paper_2608_04283_b300 import inputs
-from parity_util import max_rel
+from parity_util import max_rel, max_rel_coupled
 
 pytestmark = pytest.mark.gpu
 
@@ -115,3 +116,54 @@ def test_fullsize_conservation(vk, U0, precision, tol):
     sim.close()
     scale = np.abs(t0).max()
     assert np.abs(t1 - t0).max() <= tol * scale, (t0, t1)
+
+
+MN = 2048
+ML = 2 * np.pi
+MKW = dict(omega=1.0, cfl=0.3, c=0.05, k=2.0, gamma=5.0 / 3.0, ch_factor=6.0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-11)])
+def test_fullsize_mhd_one_step_sampled(vk, precision, tol):
+    """As the Euler case, with c_h (reading R4: ch_factor x the largest fast
+    speed of the full grid) also taken from the full grid for every patch.
+    FP32: psi stays at rounding level, so fields below 1e-2 of the largest are
+    measured against the largest (as in the whole-grid MHD-GLM parity tests)."""
+    bench = _bench()
+    U0 = np.ascontiguousarray(inputs.orszag_tang(MN))
+    shape = bench.launch_shape("mhd_glm", "fp32", (MN, MN))
+    sim = vk.Sim("mhd_glm", (MN, MN), (0.0, 0.0), (ML, ML), precision=precision, **MKW)
+    bench.configure(sim, shape)
+    tx, ty = sim.info.tile_x, sim.info.tile_y
+    sim.set_state(U0)
+    sim.step(1)
+    got = sim.moments()
+    t, nsteps, _ = sim.time()
+    sim.close()
+
+    sysm = systems.MHDGLM(MKW["gamma"])
+    full = ovklb.Sim(sysm, (MN, MN), (0.0, 0.0), (ML, ML), omega=1.0, nu=MKW["cfl"], ch_factor=MKW["ch_factor"])
+    full.refresh_ch(U0)
+    ch = full.sys.ch
+    xi0 = full.max_lambda(U0) / MKW["cfl"]
+    dx = ML / MN
+    assert nsteps == 1
+    assert abs(t - dx / xi0) <= (1e-6 if precision == "fp32" else 1e-13) * (dx / xi0)
+
+    rng = np.random.default_rng(21)
+    xs = sorted({0, 1, tx - 1, tx, tx + 1, 2 * tx - 1, MN // 2, MN - 2, MN - 1})
+    ys = sorted({0, 1, ty - 1, ty, ty + 1, 2 * ty - 1, 2 * ty, MN // 2, MN - 2, MN - 1})
+    pts = [(x, y) for x in xs[::2] for y in ys[::2]]
+    pts += [(int(x), int(y)) for x, y in rng.integers(0, MN, size=(16, 2))]
+    want = np.empty((9, len(pts)))
+    for i, (x, y) in enumerate(pts):
+        patch = U0[:, np.arange(y - 2, y + 3) % MN][:, :, np.arange(x - 2, x + 3) % MN]
+        ref = ovklb.Sim(systems.MHDGLM(MKW["gamma"]), (5, 5), (0.0, 0.0), (5 * dx, 5 * dx), omega=1.0,
+                        nu=MKW["cfl"], c=MKW["c"], k=MKW["k"], dt=dx / xi0, ch_factor=MKW["ch_factor"])
+        ref.refresh_ch = lambda U, r=ref: setattr(r.sys, "ch", ch)      # the full grid's c_h
+        ref.set_state(patch)
+        ref.step()
+        want[:, i] = ref.moments()[:, 2, 2]
+    have = np.stack([got[:, y, x] for x, y in pts], axis=1)
+    err = max_rel_coupled(have, want)
+    assert err.max() <= tol, err
