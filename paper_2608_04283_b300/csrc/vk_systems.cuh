@@ -511,12 +511,26 @@ struct MHDGLM {
     lH[3] = -hp * ia2;
 
     // coefficients c_j = alpha_j l_j.G + l_j.ga sum_+- phi_+- (alpha_j - alpha_+-)/(lam_j - lam_+-)
+    // The plain quotients first (alpha_dd's branch for well separated speeds,
+    // which is every wave when c_h is several times the fast speed); the
+    // stable forms only where a speed comes within 0.05 lmax of +-c_h, or for
+    // the other weight sets, in a branch a warp rarely enters.
     R cc[7];
+    bool near = set != SET_WEIGHTED;
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
-      R ddp = alpha_dd(al[j], lam[j], alp, ch, kl, lmax, set);
-      R ddm = alpha_dd(al[j], lam[j], alm, -ch, kl, lmax, set);
+      const R dp = lam[j] - ch, dm = lam[j] + ch;
+      near = near || !(vabs(dp) > R(0.05) * lmax) || !(vabs(dm) > R(0.05) * lmax);
+      const R ddp = (al[j] - alp) * vrcp(dp), ddm = (al[j] - alm) * vrcp(dm);
       cc[j] = al[j] * lG[j] + lH[j] * (php * ddp + phm * ddm);
+    }
+    if (near) {
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        R ddp = alpha_dd(al[j], lam[j], alp, ch, kl, lmax, set);
+        R ddm = alpha_dd(al[j], lam[j], alm, -ch, kl, lmax, set);
+        cc[j] = al[j] * lG[j] + lH[j] * (php * ddp + phm * ddm);
+      }
     }
     // S = sum_j c_j r_j (primitive), then F+_7 = M S
     const R fs = cc[6] + cc[0], fd = cc[6] - cc[0];
