@@ -30,10 +30,13 @@
  *    device error word and returned by the next synchronising call
  *    (vklb_sync, vklb_moments, vklb_conservation_totals, vklb_time,
  *    vklb_get_state).  No call aborts the process.
- *  - The library allocates its own device memory (cudaMalloc) for the state
- *    (distributions, or moments in the moment form of vklb_set_form) and a few
- *    control words; vklb_destroy frees it.  vklb_conservation_totals_noalloc
- *    is the one call that allocates nothing.
+ *  - The library allocates its own device memory for the state (distributions,
+ *    or moments in the moment form of vklb_set_form) and a few control words,
+ *    as stream-ordered allocations on the simulation's stream (cudaMallocAsync);
+ *    vklb_destroy waits for that stream alone and frees them on it, so it does
+ *    not wait for work on other streams.  A batch's buffers live on the batch's
+ *    own stream the same way.  vklb_conservation_totals_noalloc is the one call
+ *    that allocates nothing.
  */
 #ifndef VKLB_H
 #define VKLB_H

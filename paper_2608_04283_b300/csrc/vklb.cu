@@ -42,14 +42,20 @@ int err_of(const Ctl& h) {
   return VKLB_OK;
 }
 
+// A simulation's device buffers are stream-ordered allocations on its stream
+// (cudaMallocAsync / cudaFreeAsync): creating or destroying one while other
+// simulations run on other streams does not wait for their work.
+void free_on(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
 void free_sim(vklb_sim* s) {
   if (!s) return;
-  cudaFree(s->f[0]);
-  cudaFree(s->f[1]);
-  cudaFree(s->ctl);
-  cudaFree(s->part);
-  cudaFree(s->dvec);
-  cudaFree(s->stage);
+  free_on(s->f[0], s->stream);
+  free_on(s->f[1], s->stream);
+  free_on(s->ctl, s->stream);
+  free_on(s->part, s->stream);
+  free_on(s->dvec, s->stream);
+  free_on(s->stage, s->stream);
   delete s;
 }
 
@@ -205,11 +211,13 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->ops = ops;
   const size_t fbytes = (size_t)s->Q * s->P * (size_t)s->pitch * s->ny * s->store_bytes;
   cudaError_t e = cudaSuccess;
-  if ((e = cudaMalloc(&s->f[0], fbytes)) != cudaSuccess || (e = cudaMalloc(&s->f[1], fbytes)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&s->ctl, sizeof(Ctl))) != cudaSuccess ||
-      (e = cudaMalloc((void**)&s->part, sizeof(double) * s->P * kRedBlocks)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&s->dvec, sizeof(double) * s->P)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&s->stage, sizeof(double) * s->P * (size_t)s->cells)) != cudaSuccess) {
+  cudaStream_t st = s->stream;
+  if ((e = cudaMallocAsync(&s->f[0], fbytes, st)) != cudaSuccess ||
+      (e = cudaMallocAsync(&s->f[1], fbytes, st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void**)&s->ctl, sizeof(Ctl), st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void**)&s->part, sizeof(double) * s->P * kRedBlocks, st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void**)&s->dvec, sizeof(double) * s->P, st)) != cudaSuccess ||
+      (e = cudaMallocAsync((void**)&s->stage, sizeof(double) * s->P * (size_t)s->cells, st)) != cudaSuccess) {
     free_sim(s);
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? VKLB_ERR_NOMEM : VKLB_ERR_CUDA;
@@ -235,7 +243,7 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
 
 int vklb_destroy(vklb_sim* s) {
   if (!s) return VKLB_ERR_ARG;
-  cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->stream);   // this simulation's stream only
   free_sim(s);
   return cuda_status(cudaGetLastError());
 }
@@ -296,18 +304,18 @@ int vklb_set_form(vklb_sim* s, int32_t form) {
   const int qs = form == 1 ? 1 : s->Q;
   const size_t fbytes = (size_t)qs * s->P * (size_t)s->pitch * s->ny * s->store_bytes;
   void* nf[2] = {nullptr, nullptr};
-  cudaError_t e = cudaMalloc(&nf[0], fbytes);
-  if (e == cudaSuccess) e = cudaMalloc(&nf[1], fbytes);
+  cudaError_t e = cudaMallocAsync(&nf[0], fbytes, s->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&nf[1], fbytes, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(nf[0], 0, fbytes, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(nf[1], 0, fbytes, s->stream);
   if (e != cudaSuccess) {
-    cudaFree(nf[0]);
-    cudaFree(nf[1]);
+    free_on(nf[0], s->stream);
+    free_on(nf[1], s->stream);
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? VKLB_ERR_NOMEM : VKLB_ERR_CUDA;
   }
-  cudaFree(s->f[0]);
-  cudaFree(s->f[1]);
+  free_on(s->f[0], s->stream);
+  free_on(s->f[1], s->stream);
   s->f[0] = nf[0];
   s->f[1] = nf[1];
   s->form = form;

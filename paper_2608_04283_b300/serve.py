@@ -7,9 +7,10 @@ omega = 1, where U alone is the state: 2p instead of 10p values a cell), keeps e
 GPU, and advances all active simulations of one system family together with a
 single batched launch per step (``vklb_batch_step``); the three families run on
 their own CUDA streams, so their work overlaps on the device.  A tick advances
-each family by K steps, K = min(tick_steps, fewest steps any member still
-needs), after which finished simulations are read back and freed and waiting
-requests are admitted into the freed memory.  Every request's result is the
+a family by K steps, K = min(tick_steps, fewest steps any member still needs);
+when it completes, that family's finished simulations are read back and freed,
+waiting requests are admitted into the freed memory and its next tick is
+launched, without waiting for the other families' ticks.  Every request's result is the
 same as when it is served alone: the batched kernel computes each tile of each
 member independently, with the family's fixed tiling.
 
@@ -102,13 +103,19 @@ class Server:
         honoured against the wall clock from the start; otherwise everything is
         available at once.  ``payloads`` optionally maps a request id to its
         initial state U_0 (the data a client sends with the request); without
-        it the server generates U_0 itself.  Returns a Report."""
+        it the server generates U_0 itself.  Returns a Report.
+
+        Each family has at most one tick in flight on its stream, and a family
+        is served as soon as its own tick completes (its finished requests read
+        back and freed, waiting requests admitted, its next tick launched),
+        while the other families' ticks keep the GPU busy."""
+        torch = self.torch
         t0 = self.clock()
         now = lambda: self.clock() - t0
-        pending = list(requests)
-        jobs = [Job(req=r, left=r.steps) for r in pending]
+        jobs = [Job(req=r, left=r.steps) for r in requests]
         queue, active = [], {k: [] for k in FAMILY}
         batches = {}
+        inflight = {}   # family -> (event, members stepped, k), in launch order
         used = 0.0
         peak = 0.0
         qi = 0
@@ -135,10 +142,10 @@ class Server:
                 if qi < len(jobs):
                     time.sleep(max(0.0, min(0.01, jobs[qi].req.arrival - now())))
                 continue
-            # one tick: every family advances together on its own stream; a
-            # family's batch is rebuilt only when its membership changed
+            # launch a tick of every family that has none in flight; a family's
+            # batch is rebuilt only when its membership changed
             for fam, js in active.items():
-                if not js:
+                if not js or fam in inflight:
                     continue
                 key = tuple(j.req.rid for j in js)
                 if batches.get(fam, (None,))[0] != key:
@@ -147,16 +154,28 @@ class Server:
                     batches[fam] = (key, vklb.Batch([j.sim for j in js], tile=self.tiles[fam]))
                 k = min(self.tick, min(j.left for j in js))
                 batches[fam][1].step(k, graph=False)
-                for j in js:
+                ev = torch.cuda.Event()
+                ev.record(self.streams[fam])
+                inflight[fam] = (ev, list(js), k)
+            # serve the families whose tick has completed (polled, so that the
+            # first family to finish is served first), or admit an arrival
+            done = [fam for fam, (ev, _, _) in inflight.items() if ev.query()]
+            while not done and inflight:
+                if realtime and qi < len(jobs) and jobs[qi].req.arrival <= now():
+                    break
+                if len(inflight) == 1:
+                    next(iter(inflight.values()))[0].synchronize()
+                else:
+                    time.sleep(1e-4)
+                done = [fam for fam, (ev, _, _) in inflight.items() if ev.query()]
+            for fam in done:
+                _, stepped, k = inflight.pop(fam)
+                for j in stepped:
                     j.left -= k
-            for fam, js in active.items():
-                if not js:
-                    continue
-                self.streams[fam].synchronize()
-                if any(j.left == 0 for j in js) and fam in batches:
+                if any(j.left == 0 for j in stepped):
                     batches.pop(fam)[1].close()
                 still = []
-                for j in js:
+                for j in active[fam]:
                     if j.left > 0:
                         still.append(j)
                         continue
