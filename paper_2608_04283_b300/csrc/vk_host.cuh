@@ -316,17 +316,43 @@ struct Impl {
 
 template <class Sys, class T, class R, int DIM>
 struct BatchImpl {
+  // the plain and moment-form bodies take the register-bounded instantiation
+  // where the single-simulation step does (blocks of at most 128 threads)
+  static constexpr bool kBounded = Impl<Sys, T, R, DIM>::kBounded;
+  static constexpr int kMinBlocks = Impl<Sys, T, R, DIM>::kMinBlocks;
+  static bool bounded(int variant, int tx) { return variant != 1 && Impl<Sys, T, R, DIM>::bounded(tx); }
+  template <int V>
+  static void launch_lb(const vklb_batch* b, int i, int TX, int TY, int D, size_t sm) {
+    if constexpr (kBounded)
+      step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks><<<b->nwork, TX, sm, b->own>>>(
+          (const StepArgs<T>*)b->d_desc, b->d_work, i, TX, TY, D);
+  }
+  template <int V>
+  static cudaError_t occupancy_lb(int* nb, int tx, size_t sm) {
+    if constexpr (kBounded) {
+      cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks>, tx,
+                                                           sm);
+    }
+    return cudaErrorInvalidValue;
+  }
   static void launch(vklb_batch* b, int64_t n) {
     if constexpr (DIM == 2) {
     const int TX = b->tile_x, TY = b->tile_y, D = b->stages;
     const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(b->variant, TX, TY, D);
+    const bool lb = bounded(b->variant, TX);
     for (int64_t i = 0; i < n; ++i) {
       if (b->variant == 1)
         step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+      else if (b->variant == 2 && lb)
+        launch_lb<2>(b, (int)i, TX, TY, D, sm);
       else if (b->variant == 2)
         step2d_batch_kernel<Sys, T, R, 2><<<b->nwork, TX, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+      else if (lb)
+        launch_lb<0>(b, (int)i, TX, TY, D, sm);
       else
         step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
@@ -343,10 +369,14 @@ struct BatchImpl {
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       int nb = 0;
+      const bool lb = bounded(variant, tx);
       cudaError_t e =
           variant == 1   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx, sm)
-          : variant == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 2>, tx, sm)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 0>, tx, sm);
+          : variant == 2 ? (lb ? occupancy_lb<2>(&nb, tx, sm)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 2>,
+                                                                               tx, sm))
+          : lb ? occupancy_lb<0>(&nb, tx, sm)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 0>, tx, sm);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -363,6 +393,12 @@ struct BatchImpl {
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if constexpr (kBounded) {
+        cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, 0, kMinBlocks>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, 2, kMinBlocks>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      }
     }
     StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
     for (size_t i = 0; i < b->sims.size(); ++i) h[i] = make_args<T>(b->sims[i], -1.0);

@@ -958,9 +958,9 @@ struct BatchWork {
 };
 
 template <class Sys, class T, class R, int VARIANT>
-__global__ void step2d_batch_kernel(const StepArgs<T>* __restrict__ desc, const BatchWork* __restrict__ work,
-                                    int step_off, int TX, int TY, int D) {
-  extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ void step2d_batch_body(const StepArgs<T>* __restrict__ desc,
+                                                  const BatchWork* __restrict__ work, int step_off, int TX, int TY,
+                                                  int D, unsigned char* smem) {
   const BatchWork wk = work[blockIdx.x];
   StepArgs<T> a = desc[wk.sim];
   a.parity = (a.parity + step_off) & 1;
@@ -971,6 +971,23 @@ __global__ void step2d_batch_kernel(const StepArgs<T>* __restrict__ desc, const 
     step2d_tile<Sys, T, R, 1>(a, wk.bx, wk.by, TX, TY, smem);   // moment form
   else
     step2d_tile<Sys, T, R>(a, wk.bx, wk.by, TX, TY, smem);
+}
+
+template <class Sys, class T, class R, int VARIANT>
+__global__ void step2d_batch_kernel(const StepArgs<T>* __restrict__ desc, const BatchWork* __restrict__ work,
+                                    int step_off, int TX, int TY, int D) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  step2d_batch_body<Sys, T, R, VARIANT>(desc, work, step_off, TX, TY, D, smem);
+}
+
+// The batched step with the plain step's register bound (StepBound), for blocks
+// of at most 128 threads (plain and moment-form bodies).
+template <class Sys, class T, class R, int VARIANT, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+    step2d_batch_lb_kernel(const StepArgs<T>* __restrict__ desc, const BatchWork* __restrict__ work, int step_off,
+                           int TX, int TY, int D) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  step2d_batch_body<Sys, T, R, VARIANT>(desc, work, step_off, TX, TY, D, smem);
 }
 
 // ------------------------------------------------------------------ D1Q3 steps

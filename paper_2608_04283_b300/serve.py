@@ -82,7 +82,7 @@ class Server:
         self.budget = float(budget_bytes)
         self.tick = int(tick_steps)
         self.precision = precision
-        self.tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (64, 16)}
+        self.tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (128, 16)}
         self.keep = keep_results
         self.form = form
         self.streams = {k: torch.cuda.Stream() for k in FAMILY}
@@ -209,7 +209,7 @@ def serve_alone(req, **kw):
 def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=None):
     """Baseline: the same requests one at a time, one launch per step each."""
     import torch
-    tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (64, 16)}
+    tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (128, 16)}
     t0 = time.perf_counter()
     for r in requests:
         kw, side = FAMILY[r.system]
