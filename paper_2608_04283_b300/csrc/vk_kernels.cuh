@@ -51,7 +51,9 @@ template <> VK_HD Euler<double, 2> make_sys(const SysParams& s) { Euler<double, 
 template <> VK_HD MHDGLM<float> make_sys(const SysParams& s) { MHDGLM<float> r; r.gamma = (float)s.gamma; return r; }
 template <> VK_HD MHDGLM<double> make_sys(const SysParams& s) { MHDGLM<double> r; r.gamma = s.gamma; return r; }
 
-// Everything one step of one simulation needs.
+// Everything one step of one simulation needs.  The buffer pair is selected
+// with src() / dst(), not indexed by the parity: an indexed member array would
+// keep a copy of the struct (the batched kernels make one) in local memory.
 template <class T>
 struct StepArgs {
   T* f[2];         // ping-pong distribution buffers
@@ -64,6 +66,8 @@ struct StepArgs {
   Ctl* ctl;
   int slot;        // n % 3
   SysParams sp;
+  VK_HD T* src() const { return parity ? f[1] : f[0]; }
+  VK_HD T* dst() const { return parity ? f[0] : f[1]; }
 };
 
 // 2D distribution layout: 32-cell bricks.  Component k = q p + i of cell (x, y)
@@ -319,8 +323,8 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   const bool act = tx < w;
   constexpr int NS = StateForm<Sys, FORM>::NS;
   const int nxb = a.pitch / kBrick;
-  const T* __restrict__ fin = a.f[a.parity];
-  T* __restrict__ fout = a.f[a.parity ^ 1];
+  const T* __restrict__ fin = a.src();
+  T* __restrict__ fout = a.dst();
   const int s1 = (a.slot + 1) % 3;
   const R xinv = bc.xinv, ch = bc.ch, c = bc.c, om = bc.om, kk = bc.k;
   const int set = a.set;
@@ -478,8 +482,8 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
   const bool act = tx < w;
   constexpr int NS = StateForm<Sys, FORM>::NS;
   const int nxb = a.pitch / kBrick;
-  const T* __restrict__ fin = a.f[a.parity];
-  T* __restrict__ fout = a.f[a.parity ^ 1];
+  const T* __restrict__ fin = a.src();
+  T* __restrict__ fout = a.dst();
   const int s1 = (a.slot + 1) % 3;
   const R xinv = bc.xinv, ch = bc.ch, c = bc.c, om = bc.om, kk = bc.k;
   const int set = a.set;
@@ -606,7 +610,7 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
       for (int r = 0; r < h; ++r)
         for (int i = 0; i < NS; ++i) {
           const size_t o = brick_base(x0 + tx, y0 + r, a.pitch / kBrick, NS) + (size_t)i * kBrick;
-          a.f[a.parity ^ 1][o] = a.f[a.parity][o];
+          a.dst()[o] = a.src()[o];
         }
     if (bx == 0 && by == 0 && tx == 0) {
       const int s1 = (a.slot + 1) % 3, s2 = (a.slot + 2) % 3;
@@ -738,8 +742,8 @@ __device__ __forceinline__ void step2d_tile_tma(const StepArgs<T>& a, int bx, in
   const bool act = tid < w;
   const bool up = (by & 1) == 0;
   constexpr size_t plane = kBrick;   // component stride in the brick layout
-  const T* __restrict__ fin = a.f[a.parity];
-  T* __restrict__ fout = a.f[a.parity ^ 1];
+  const T* __restrict__ fin = a.src();
+  T* __restrict__ fout = a.dst();
   __shared__ StepScalars s_sc;
   __shared__ BlockConsts<Sys, R> s_bc;
   if (tid == 0) {
