@@ -81,7 +81,7 @@ class Sim:
     """
 
     def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted",
-                 c=0.05, k=2.0, omega=1.0, nu=0.9, dt=None, ch_factor=6.0):
+                 c=0.05, k=2.0, omega=1.0, nu=0.9, dt=None, ch_factor=6.0, eta=None):
         self.sys = system
         self.dim = system.dim
         self.n = tuple(int(v) for v in n)
@@ -106,6 +106,12 @@ class Sim:
         self.c, self.k, self.omega, self.nu = float(c), float(k), float(omega), float(nu)
         if not (0.0 < self.omega <= 2.0):
             raise ValueError("omega must lie in (0, 2] (Sec. 2.3)")
+        # eta: the subcharacteristic condition of the centered set (Sec. 2.3),
+        # xi > sqrt(3/2) max_j |lambda_j|, taken as xi = sqrt(3/2) max|lambda| / eta
+        # with eta < 1 (the paper runs the centered set at eta = 0.9, Sec. 5)
+        if eta is not None and not (0.0 < eta < 1.0):
+            raise ValueError("eta must lie in (0, 1) (Sec. 2.3)")
+        self.eta = None if eta is None else float(eta)
         self.fixed_xi = None if dt is None or dt <= 0 else self.dx / float(dt)
         self.ch_factor = float(ch_factor)
         self.f = None
@@ -143,9 +149,12 @@ class Sim:
         return max(float(np.max(self.sys.max_speed(Uf, d))) for d in range(self.dim))
 
     def cfl_xi(self, U):
-        """Eq. (29): xi = max_j |lambda_j| / nu (or the fixed dx/dt)."""
+        """Eq. (29): xi = max_j |lambda_j| / nu (or the fixed dx/dt); with eta,
+        the subcharacteristic rule xi = sqrt(3/2) max_j |lambda_j| / eta (Sec. 2.3)."""
         if self.fixed_xi is not None:
             return self.fixed_xi
+        if self.eta is not None:
+            return np.sqrt(1.5) * self.max_lambda(U) / self.eta
         return self.max_lambda(U) / self.nu
 
     def stream(self, fs):

@@ -302,3 +302,45 @@ def test_one_step_is_local_given_global_xi():
         ref.set_state(U0[:, ys][:, :, xs])
         ref.step()
         np.testing.assert_allclose(ref.moments()[:, 2, 2], Uf[:, y, x], rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("kind", ["swe", "euler"])
+def test_centered_eta_rule_meets_subcharacteristic_condition(kind):
+    """Sec. 2.3: the subcharacteristic condition d/dU sum_q v_q^2 f_q^eq - (dF/dU)^2
+    > 0 (eigenvalues of the matrix).  For the centered set it holds exactly when
+    xi > sqrt(3/2) max_j |lambda_j|; the oracle's eta rule takes
+    xi = sqrt(3/2) max|lambda| / eta.  The matrix is formed here from the oracle's
+    own equilibria (complex-step derivative of the second moment) and the
+    Jacobian, so its smallest eigenvalue over the cells must be
+    max|lambda|^2 (1 / eta^2 - 1): positive for eta < 1, and it changes sign
+    when xi drops below the bound."""
+    s = systems.make(kind, 1)
+    m = 48
+    U = inputs.random_states(kind, m, seed=31, dim=1)
+    eta = 0.9
+    sim = vklb.Sim(s, (m,), (0.0,), (1.0,), set_kind="centered", eta=eta)
+    lmax = sim.max_lambda(U)
+    xi = sim.cfl_xi(U)
+    A = splitting.jacobian(s, U, 0)
+
+    def second_moment_jacobian(x):
+        h = 1e-30
+        J = np.empty((m, s.p, s.p))
+        for j in range(s.p):
+            Uc = U.astype(complex)
+            Uc[j] += 1j * h
+            feq = sim.equilibrium(Uc, x)
+            mom2 = np.tensordot((V1 * x) ** 2, feq, axes=(0, 0))
+            J[:, :, j] = (mom2.imag / h).T
+        return J
+
+    def smallest_eig(x):
+        M = second_moment_jacobian(x) - np.einsum("nij,njk->nik", A, A)
+        ev = np.linalg.eigvals(M)
+        assert np.abs(ev.imag).max() <= 1e-9 * np.abs(ev.real).max()
+        return ev.real.min()
+
+    assert smallest_eig(xi) == pytest.approx(lmax ** 2 * (1.0 / eta ** 2 - 1.0), rel=1e-9)
+    assert smallest_eig(0.98 * np.sqrt(1.5) * lmax) < 0.0
+    with pytest.raises(ValueError):
+        vklb.Sim(s, (m,), (0.0,), (1.0,), set_kind="centered", eta=1.0)
