@@ -12,6 +12,7 @@
  *   - stream   f_q(x + v_q dt) = f*_q(x)                           (Eq. 43)
  *   - moments  U = sum_q f_q                                       (Eq. 3)
  *   - CFL lattice speed  xi = max_j |lambda_j| / nu                (Eq. 29)
+ *     (or sqrt(3/2) max_j |lambda_j| / eta, the subcharacteristic rule, Sec. 2.3)
  *   - periodic (Eq. 37) and characteristic (Eqs. 33-36) boundaries.
  * One call to vklb_step advances the state by the flow chart of Fig. 5.
  *
@@ -99,7 +100,10 @@ typedef struct {
  * k), centered flux (Eqs. 8-10, 39: c = 1/Q, F+- = F/2) or discontinuous upwind
  * (Eqs. 12-18: c = 0, Heaviside weights).  omega: relaxation in (0, 2]
  * (Sec. 2.3); cfl: nu of Eq. (29).  The paper uses c = 0.05, k = 2, nu = 0.9
- * (Sec. 5). */
+ * (Sec. 5).  eta: 0 for the CFL rule; in (0, 1) the lattice speed follows the
+ * centered set's subcharacteristic condition instead (Sec. 2.3),
+ * xi = sqrt(3/2) max_j |lambda_j| / eta, as the paper runs the centered set
+ * (eta = 0.9, Sec. 5); cfl is then not used. */
 typedef enum { VKLB_SET_WEIGHTED = 0, VKLB_SET_CENTERED = 1, VKLB_SET_DISCONTINUOUS = 2 } vklb_set;
 typedef struct {
   int32_t set;
@@ -107,6 +111,7 @@ typedef struct {
   double k;
   double omega;
   double cfl;
+  double eta;
 } vklb_weight;
 
 /* Arithmetic: FP64 everywhere; FP32 distributions and arithmetic (conservation
@@ -142,7 +147,7 @@ typedef struct {
  * selects the adaptive CFL rule of Eq. (29).  cuda_stream is a cudaStream_t
  * (NULL: the legacy default stream) on which every kernel of this simulation
  * runs.  Parameter checks (returning VKLB_ERR_ARG): omega in (0, 2]
- * (Sec. 2.3); 0 < cfl <= 1 (Eq. 28); dx == dy for D2Q5 (Sec. 3.4); lattice
+ * (Sec. 2.3); 0 < cfl <= 1 (Eq. 28); eta = 0 or 0 < eta < 1 (Sec. 2.3); dx == dy for D2Q5 (Sec. 3.4); lattice
  * matches grid->dim; characteristic boundaries only on D1Q3.  On success
  * *out owns two device distribution buffers of q * p * cells values each. */
 int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid,

@@ -45,6 +45,7 @@ struct vklb_sim {
   SysParams sp;
   int set;
   double c, k, omega, cfl, fixed_xi;
+  double inv_nu;   // xi = inv_nu max|lambda|: 1 / cfl, or sqrt(3/2) / eta
   int bc_lo, bc_hi;
   cudaStream_t stream;
   void* f[2];
@@ -119,7 +120,7 @@ StepArgs<T> make_args(const vklb_sim* s, double t_end) {
   a.c = s->c;
   a.omega = s->omega;
   a.k = s->k;
-  a.inv_nu = 1.0 / s->cfl;
+  a.inv_nu = s->inv_nu;
   a.fixed_xi = s->fixed_xi;
   a.t_end = t_end;
   a.ch_factor = s->ch_factor;

@@ -147,6 +147,7 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   if (weight->set < 0 || weight->set > 2) return VKLB_ERR_ARG;
   if (!(weight->omega > 0.0 && weight->omega <= 2.0)) return VKLB_ERR_ARG;   // Sec. 2.3
   if (!(weight->cfl > 0.0 && weight->cfl <= 1.0)) return VKLB_ERR_ARG;       // Eq. (28)
+  if (!(weight->eta == 0.0 || (weight->eta > 0.0 && weight->eta < 1.0))) return VKLB_ERR_ARG;   // Sec. 2.3
   if (!(weight->k >= 0.0)) return VKLB_ERR_ARG;
   const int64_t nx = grid->n[0], ny = dim == 2 ? grid->n[1] : 1;
   if (nx < 1 || ny < 1 || nx > (1 << 30) || ny > (1 << 30)) return VKLB_ERR_ARG;
@@ -198,6 +199,8 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->k = weight->k;
   s->omega = weight->omega;
   s->cfl = weight->cfl;
+  // Eq. (29), or the centered set's subcharacteristic condition (Sec. 2.3)
+  s->inv_nu = weight->eta > 0.0 ? sqrt(1.5) / weight->eta : 1.0 / weight->cfl;
   s->fixed_xi = dt > 0.0 ? dx / dt : 0.0;
   s->bc_lo = bc->lo[0];
   s->bc_hi = bc->hi[0];
@@ -347,7 +350,7 @@ int vklb_step_to(vklb_sim* s, double t_end) {
     if (st) return st;
     if ((st = err_of(h))) return st;
     const int slot = (int)(s->launched % 3);
-    StepScalars sc = step_scalars(&h, slot, s->kind == VKLB_MHD_GLM, s->ch_factor, 1.0 / s->cfl, s->fixed_xi, t_end, s->dx);
+    StepScalars sc = step_scalars(&h, slot, s->kind == VKLB_MHD_GLM, s->ch_factor, s->inv_nu, s->fixed_xi, t_end, s->dx);
     if (sc.done) return VKLB_OK;
     // steps left if xi stayed as it is now
     double m = ceil((t_end - h.t[slot]) * sc.xi / s->dx - 1e-9);
@@ -404,7 +407,7 @@ int vklb_time(vklb_sim* s, double* t, int64_t* steps, double* xi) {
   int st = read_ctl(s, &h);
   if (st) return st;
   const int slot = (int)(s->launched % 3);
-  StepScalars sc = step_scalars(&h, slot, s->kind == VKLB_MHD_GLM, s->ch_factor, 1.0 / s->cfl, s->fixed_xi, -1.0, s->dx);
+  StepScalars sc = step_scalars(&h, slot, s->kind == VKLB_MHD_GLM, s->ch_factor, s->inv_nu, s->fixed_xi, -1.0, s->dx);
   if (t) *t = h.t[slot];
   if (steps) *steps = h.nsteps;
   if (xi) *xi = sc.xi;

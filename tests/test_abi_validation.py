@@ -27,6 +27,8 @@ def _status(vk, fn):
     (dict(n=(2,), lo=(0.0,), hi=(1.0,)), "ERR_ARG"),           # D1Q3 needs 3 cells
     (dict(omega=0.0), "ERR_ARG"), (dict(omega=2.5), "ERR_ARG"),
     (dict(cfl=0.0), "ERR_ARG"), (dict(cfl=1.5), "ERR_ARG"),
+    (dict(set_kind="centered", eta=1.0), "ERR_ARG"),          # subcharacteristic: eta < 1 (Sec. 2.3)
+    (dict(set_kind="centered", eta=-0.5), "ERR_ARG"),
     (dict(k=-1.0), "ERR_ARG"),
     (dict(n=(32, 16), hi=(1.0, 1.0)), "ERR_ARG"),            # dx != dy
     (dict(hi=(0.0, 1.0)), "ERR_ARG"),                          # empty domain

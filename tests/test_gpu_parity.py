@@ -290,6 +290,32 @@ def test_batch_mhd_equals_individual(vk, form, tile):
         s.close()
 
 
+@pytest.mark.parametrize("precision,tol,omega", [("fp64", 1e-11, 2.0), ("fp64", 1e-11, 1.0), ("fp32", 1e-5, 1.0)])
+def test_centered_subcharacteristic_2d(vk, precision, tol, omega):
+    """2D centered set (Eq. 39, c = 1/5) with the subcharacteristic lattice speed
+    xi = sqrt(3/2) max|lambda| / eta, eta = 0.9 (Sec. 2.3).  FP32 at omega = 1
+    only: at omega = 2 this configuration amplifies rounding (in the FP64 oracle
+    a 1e-7 relative perturbation of U_0 grows to 3e-5 in 15 steps; at omega = 1
+    it decays to 6e-8), so FP32 cannot meet 1e-5 there by construction."""
+    n = (40, 36)
+    U0 = np.ascontiguousarray(inputs.isentropic_vortex(40, lo=0.0, hi=10.0)[:, :36, :])
+    hi = (10.0, 9.0)
+    sim = vk.Sim("euler", n, (0.0, 0.0), hi, precision=precision, set_kind="centered", omega=omega, eta=0.9)
+    sim.set_tiling(32, 8)
+    sim.set_state(U0)
+    sim.step(15)
+    ref = ovklb.Sim(systems.Euler(1.4, 2), n, (0.0, 0.0), hi, set_kind="centered", omega=omega, eta=0.9)
+    ref.set_state(U0)
+    ref.run(15)
+    got, want = sim.moments(), ref.moments()
+    err = max_rel(got, want) if precision == "fp64" else rel_l1(got, want)
+    assert err.max() <= tol, err
+    t, nsteps, xi = sim.time()
+    assert nsteps == 15 and abs(t - ref.t) <= (1e-12 if precision == "fp64" else 1e-6) * ref.t
+    assert abs(xi - ref.xi) <= (1e-11 if precision == "fp64" else 1e-5) * ref.xi
+    sim.close()
+
+
 def test_nonphysical_state_is_reported(vk):
     n = (32, 32)
     U0 = inputs.swe_sine_2d(32)

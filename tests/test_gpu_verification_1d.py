@@ -121,3 +121,27 @@ def test_smooth_hump_characteristic_bc(vk, precision, tol):
     err = max_rel(got, want) if precision == "fp64" else np.abs(got - want).sum(axis=1) / np.abs(want).sum(axis=1).max()
     assert err.max() <= tol, err
     sim.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_smooth_hump_centered_subcharacteristic(vk, precision, tol):
+    """The paper's first 1D check (Sec. 5.1, Eq. 53): the centered set (c = 1/3,
+    F+- = F/2) with the characteristic boundaries, lattice speed from the
+    subcharacteristic rule at eta = 0.9 (Sec. 2.3), omega = 1, to T = 8, when the
+    hump has left the domain; N = 512."""
+    n, T = 512, 8.0
+    U0 = inputs.swe_smooth_hump_1d(n)
+    sim = vk.Sim("swe", (n,), (-5.0,), (5.0,), precision=precision, g=1.0, bc="characteristic",
+                 set_kind="centered", omega=1.0, eta=0.9)
+    sim.set_state(U0)
+    sim.step_to(T)
+    ref = ovklb.Sim(systems.ShallowWater(1.0, 1), (n,), (-5.0,), (5.0,), bc="characteristic",
+                    set_kind="centered", omega=1.0, eta=0.9)
+    ref.set_state(U0)
+    ref.run_to(T)
+    got, want = sim.moments(), ref.moments()
+    err = max_rel(got, want) if precision == "fp64" else np.abs(got - want).sum(axis=1) / np.abs(want).sum(axis=1).max()
+    assert err.max() <= tol, err
+    t, nsteps, _ = sim.time()
+    assert nsteps == ref.steps and t == pytest.approx(T, abs=1e-12 if precision == "fp64" else 1e-5)
+    sim.close()
