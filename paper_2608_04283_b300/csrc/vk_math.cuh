@@ -127,8 +127,9 @@ template <class T> struct Store;
 // ld_keep: a global load whose line L2 should keep longer (an evict_last cache
 // policy), for reads made well before another block reads the same line.
 // ld_again: a second read of a value this thread loaded moments before (an L1
-// hit), issued as its own instruction so that the compiler cannot keep the first
-// load's register live in its place.
+// hit, or shared memory where the caller staged the row there), issued as its
+// own instruction so that the compiler cannot keep the first load's register
+// live in its place; a generic-address load, valid for either state space.
 #ifdef __CUDA_ARCH__
 __device__ __forceinline__ unsigned long long l2_keep_policy() {
   unsigned long long pol;
@@ -151,7 +152,7 @@ template <> struct Store<double> {
   static VK_HD double ld_again(const double* p) {
 #ifdef __CUDA_ARCH__
     double v;
-    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    asm volatile("ld.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 #else
     return *p;
@@ -174,7 +175,7 @@ template <> struct Store<float> {
   static VK_HD float ld_again(const float* p) {
 #ifdef __CUDA_ARCH__
     float v;
-    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    asm volatile("ld.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 #else
     return *p;
@@ -197,7 +198,7 @@ template <> struct Store<__nv_bfloat16> {
   static VK_HD float ld_again(const __nv_bfloat16* p) {
 #ifdef __CUDA_ARCH__
     unsigned short b;
-    asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(b) : "l"(p));
+    asm volatile("ld.b16 %0, [%1];" : "=h"(b) : "l"(p));
     return __bfloat162float(__ushort_as_bfloat16(b));
 #else
     return __bfloat162float(*p);

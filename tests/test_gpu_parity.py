@@ -122,6 +122,24 @@ def test_mhd_orszag_tang(vk, precision, tol, variant):
         assert abs(gt[2] - rt[2]) <= 1e-11 * rt[2]
 
 
+@pytest.mark.parametrize("variant", [(1, 4), (0, 0)])
+@pytest.mark.parametrize("precision,tol,steps", [("fp64", 1e-11, 20), ("fp32", 1e-5, 6)])
+def test_mhd_orszag_tang_omega_not_one(vk, precision, tol, steps, variant):
+    """omega = 1.3: the long-split collision reads f again for the relaxation
+    (from global memory in the plain march, from the staged row in shared memory
+    in the bulk-copy march).  FP32 over 6 steps: at omega != 1 this
+    configuration amplifies rounding (a 1e-7 perturbation of U_0 reaches 1e-5
+    in 20 steps in the FP64 oracle)."""
+    n = (36, 32)
+    L = 2 * np.pi
+    U0 = np.ascontiguousarray(inputs.orszag_tang(36)[:, :32, :])
+    lo, hi = (0.0, 0.0), (L, L * 32 / 36)
+    got, want, gt, rt, _ = _run_pair(vk, "mhd_glm", U0, n, lo, hi, steps, precision, omega=1.3, cfl=0.3,
+                                     gamma=5 / 3, variant=variant, tile=(64, 8))
+    err = max_rel(got, want) if precision == "fp64" else rel_l1_coupled(got, want)
+    assert err.max() <= tol, err
+
+
 @pytest.mark.parametrize("set_kind", ["centered", "discontinuous"])
 def test_other_sets_fp64(vk, set_kind):
     n = (40, 32)
