@@ -75,8 +75,13 @@ class Report:
 
 
 class Server:
+    """``max_side``: grids up to this side have their results read back through a
+    pinned host buffer per family (allocated here, one direct copy per result;
+    the result a caller keeps is copied out of it); larger ones through a fresh
+    pageable array."""
+
     def __init__(self, budget_bytes=120e9, tick_steps=50, precision="fp32", tiles=None, keep_results=False,
-                 clock=None, form="moments"):
+                 clock=None, form="moments", max_side=2048):
         import torch
         self.torch = torch
         self.budget = float(budget_bytes)
@@ -87,6 +92,18 @@ class Server:
         self.form = form
         self.streams = {k: torch.cuda.Stream() for k in FAMILY}
         self.clock = clock or time.perf_counter
+        self.staging = {k: torch.empty(FIELDS[k] * max_side * max_side, dtype=torch.float64,
+                                       pin_memory=True).numpy() for k in FAMILY}
+
+    def _result(self, fam, sim):
+        """Read a finished simulation's U back (into the family's pinned buffer
+        when it fits)."""
+        shape = sim.shape
+        size = int(np.prod(shape))
+        if size > self.staging[fam].size:
+            return sim.moments()
+        U = sim.moments(out=self.staging[fam][:size].reshape(shape))
+        return U.copy() if self.keep else U
 
     def _make(self, req, U0=None):
         kw, side = FAMILY[req.system]
@@ -180,7 +197,7 @@ class Server:
                         still.append(j)
                         continue
                     try:
-                        U = j.sim.moments()
+                        U = self._result(fam, j.sim)
                         j.status = "done"
                         if self.keep:
                             j.result = U
@@ -206,10 +223,12 @@ def serve_alone(req, **kw):
     return rep.jobs[0].result
 
 
-def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=None):
-    """Baseline: the same requests one at a time, one launch per step each."""
+def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=None, max_side=2048):
+    """Baseline: the same requests one at a time, one launch per step each, the
+    results read back through a pinned buffer as the server reads them."""
     import torch
     tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (128, 16)}
+    staging = torch.empty(max(FIELDS.values()) * max_side * max_side, dtype=torch.float64, pin_memory=True).numpy()
     t0 = time.perf_counter()
     for r in requests:
         kw, side = FAMILY[r.system]
@@ -218,7 +237,11 @@ def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=N
         U0 = inputs.request_initial_state(r) if payloads is None else payloads[r.rid]
         sim.set_state(np.ascontiguousarray(U0))
         sim.step(r.steps)
-        sim.moments()
+        size = int(np.prod(sim.shape))
+        if size <= staging.size:
+            sim.moments(out=staging[:size].reshape(sim.shape))
+        else:
+            sim.moments()
         sim.close()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
