@@ -11,8 +11,9 @@ bracketed by CUDA events on the simulation's stream, after an L2 flush (the
 256 MiB read of another buffer, so that the flush's own dirty lines are written
 back before the step starts rather than inside it.  Every
 200 steps the state is re-initialised outside the timed events: at omega = 2 the
-weighted set amplifies rounding (see the design notes) and an FP32 run would
-leave the physical range after about 400 steps.
+weighted set amplifies rounding on this vortex (FP64 perturbations grow 25-40x
+per 100 steps) and an FP32 run would leave the physical range after about 400
+steps.
 
 --impl reference times the FP64 CPU oracle (oracle/, test infrastructure) on the
 host cores on a bounded sample of the same workload.

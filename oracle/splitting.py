@@ -10,7 +10,8 @@ weighted (the paper's method, Sec. 3.1):
       alpha(A) = E (E + I)^-1,  E = expm(k A / max_j |lambda_j|).
   This is exact (up to rounding) whatever eigenbasis one would pick, including
   repeated eigenvalues.  max_j |lambda_j| is taken per cell and per direction
-  (reading R1 in the design notes), from the closed-form wave speeds.
+  (the paper leaves this open; this is reading R1 of oracle/vklb.py), from the
+  closed-form wave speeds.
 
 discontinuous (Sec. 2.2, Eqs. (17)-(18)): phi split by the sign of lambda,
   lambda >= 0 -> "+".  Evaluated literally by eigen-decomposition.

@@ -118,8 +118,8 @@ class MHDGLM:
     F^(d) = (rho u_d, rho u u_d + (p + |B|^2/2) e_d - B B_d,
              (E + p + |B|^2/2) u_d - (B.u) B_d,
              u_d B - B_d u + psi e_d,  c_h^2 B_d).
-    c_h is a parameter of the flux (set by the time loop, reading R4 in the
-    design notes: c_h = 6 max c_f over the grid, refreshed every step).
+    c_h is a parameter of the flux (set by the time loop, reading R4 of
+    oracle/vklb.py: c_h = 6 max c_f over the grid, refreshed every step).
     Wave speeds along d: u_d, u_d +- c_a, u_d +- c_s, u_d +- c_f and the two
     cleaning waves +- c_h."""
 

@@ -13,7 +13,7 @@ Initialisation: xi from U(x,0), f_q(x,0) = f_q^eq(U(x,0)) (Eq. 2b, Fig. 5).
 Lattices: D1Q3 v = (xi, 0, -xi) (Sec. 2.2, Fig. 1); D2Q5 v = (xi,0), (-xi,0),
 (0,0), (0,xi), (0,-xi) (Eq. 38).  Distributions are stored f[q, field, (y,) x].
 
-Readings of the paper taken here (listed in the design notes):
+Readings of the paper taken here, where it is silent or ambiguous:
   R1  alpha normaliser max_j|lambda_j| is per cell and direction.
   R2  xi is the max over all cells, both directions and all eigenvalues.
   R3  run_to(T) lands on T with evenly spread steps: every step takes

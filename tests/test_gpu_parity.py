@@ -169,7 +169,9 @@ def test_dam_break_1d_fp32(vk):
 def test_dam_break_config_paper_cfl(vk):
     """The dam break at the paper's CFL 0.9: FP64 parity holds over the first 30
     steps; beyond that the run is ill-conditioned (the weighted set amplifies
-    rounding in the left rest state, see the design notes), so the full run to
+    rounding in the left rest state: at rest its momentum diffusion passes 1/2
+    above a local CFL number of about 0.67, and the left state sits at 0.785,
+    test_weighted_set_rest_state_instability), so the full run to
     t = 0.1 is checked against the exact solution with the spread the oracle
     itself shows under 1e-15 input perturbations."""
     U0 = inputs.dam_break_1d(400)

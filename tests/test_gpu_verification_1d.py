@@ -4,8 +4,9 @@ characteristic (transmissive, reading R12) boundaries, omega = 1, c = 0.05,
 k = 2, and the smooth hump of Eq. (53).
 
 * Parity with the FP64 oracle at the paper's CFL number 0.9 over 30 steps (the
-  weighted set at rest is ill-conditioned at CFL 0.9 over long runs, see the
-  design notes) and to the final time at CFL 0.6.
+  weighted set at rest is ill-conditioned at CFL 0.9 over long runs: its
+  momentum diffusion at rest passes 1/2 above a local CFL number of about 0.67)
+  and to the final time at CFL 0.6.
 * Convergence against the exact Riemann solutions (oracle/riemann.py) at CFL 0.6
   for N = 256 .. 16384, sizes the oracle cannot reach: the L1 error falls at
   every refinement and its order at the finest pair is that of a first-order
@@ -107,7 +108,8 @@ def test_smooth_hump_characteristic_bc(vk, precision, tol):
     """Eq. (53): the smooth hump leaves the domain through the characteristic
     boundaries (Eqs. 33-36).  CFL 0.6: at 0.9 the fluid at rest around the hump
     sits at a local CFL number near 0.8, where the weighted set amplifies
-    rounding (the rest-state finding of the design notes: above about 0.67)."""
+    rounding (at rest its momentum diffusion passes 1/2 above a local CFL
+    number of about 0.67)."""
     n = 200
     U0 = inputs.swe_smooth_hump_1d(n)
     sim = vk.Sim("swe", (n,), (-5.0,), (5.0,), precision=precision, cfl=0.6, g=1.0, **KW)

@@ -114,7 +114,7 @@ def _growth_at_rest(nu_local, k=2.0, c=0.05, g=1.0, h=3.0):
 
 
 def test_weighted_set_rest_state_instability():
-    """Finding recorded in the design notes: for the (non-homogeneous) shallow-water
+    """A finding about the method as printed: for the (non-homogeneous) shallow-water
     flux the split F+ = alpha(A) F has d F+/dU != alpha(A) A, and at rest the
     momentum diffusion c + 0.676 nu_local exceeds 1/2 once the local CFL number
     passes about 0.67: the checkerboard mode grows.  The dam-break left states
