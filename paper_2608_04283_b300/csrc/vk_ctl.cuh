@@ -27,9 +27,13 @@ struct StepScalars {
   bool done;   // t_end reached: nothing to do
 };
 
-// xi of Eq. (29) (or the fixed xi), c_h = ch_factor * max c_f (reading R4) and
-// the landing rule of vklb_step_to (reading R3).  Every thread of every block
-// evaluates it from the same words, so all agree.
+// xi of Eq. (29) (or the fixed xi); c_h = ch_factor * max c_f over the grid,
+// refreshed every step with xi (the paper fixes neither the factor's use nor the
+// refresh); and the landing rule of vklb_step_to, which the paper does not
+// state: every remaining step takes xi_eff = m dx / (t_end - t) with
+// m = ceil((t_end - t) xi / dx), so the steps stay evenly spread and the last
+// ends on t_end.  Every thread of every block evaluates it from the same words,
+// so all agree.
 VK_HD StepScalars step_scalars(const Ctl* ctl, int slot, bool mhd, double ch_factor, double inv_nu,
                                double fixed_xi, double t_end, double dx) {
   StepScalars s;

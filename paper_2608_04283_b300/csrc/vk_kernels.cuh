@@ -1118,7 +1118,8 @@ __global__ void step1d_kernel(StepArgs<T> a, int nsteps) {
       if (a.fixed_xi > 0.0 && bits_to_double(vc->m1[slot]) > a.fixed_xi * (1.0 + 1e-12)) vc->err |= ERR_CFL;
     }
     __syncthreads();
-    // boundary distributions f_q(x_b) = f_q^eq(U_b^{n+1}) with xi_{n+1} (Eq. 36, R11)
+    // boundary distributions f_q(x_b) = f_q^eq(U_b^{n+1}) (Eq. 36), taken with
+    // xi_{n+1}, the lattice speed of the step that streams them
     if (threadIdx.x < 2 && ((threadIdx.x == 0 && cl) || (threadIdx.x == 1 && chi))) {
       const int side = threadIdx.x;
       const int ib = side == 0 ? 0 : nx - 1;

@@ -1,6 +1,6 @@
 """Comparison helpers shared by the GPU parity tests.
 
-max_rel:  per field max_x |a - b| / max_x |b| (reading R16 of the tolerance); a
+max_rel:  per field max_x |a - b| / max_x |b| (the tolerance read per field); a
           field that is identically zero in the reference must be zero to the
           absolute tolerance scaled by the largest field.
 rel_l1:   per field sum |a - b| / sum |b|, with the same rule for zero fields.
