@@ -614,11 +614,20 @@ def main():
                     help="only the warm-up and timed steps (no accuracy check, end-to-end run, extras or CPU "
                          "baseline): the launch list of a profile then holds just the timed region's kernels")
     ap.add_argument("--served-requests", type=int, default=40)
+    ap.add_argument("--only-batched", type=int, default=0, metavar="N",
+                    help="run only the batched shallow-water leg with the first N instances (and --form), print "
+                         "its JSON and exit: a case small enough to profile")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     wl = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.only_batched > 0:
+        import torch
+        from paper_2608_04283_b300 import build
+        build.build()
+        from paper_2608_04283_b300 import vklb
+        print(json.dumps(batched_swe(torch, vklb, count=args.only_batched, form=args.form)), flush=True)
+    elif args.impl == "reference":
         run_reference(args, wl)
     else:
         run_ours(args, wl)
