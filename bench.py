@@ -500,20 +500,27 @@ def secondary(torch, vklb, wl, prec, flush_buf, steps):
             "tile": [s.info.tile_x, s.info.tile_y], "variant": s.info.variant, "steps": steps}
 
 
+# Launch shape of the batched shallow-water leg, measured on B300 over the
+# 256-instance batch (sides 64..1024): distributions 128 x 8 (47.4 G cell
+# updates/s; 64 x fitted: 36.8 G, its x-ring reads doubling the DRAM reads),
+# moments 64 x fitted (98.1 G; 128 x 8: 83.5 G).
+BATCH_TILES = {"distributions": (128, 8), "moments": (64, -1)}
+
+
 def batched_swe(torch, vklb, count=256, steps=500, form="distributions"):
     """Batched form: 256 seeded SWE instances (sides 64..1024, Gaussian humps),
     500 steps each, one launch per step over all instances (CUDA graph), against
-    the same instances launched one at a time, each at its own wave-fit tiling.
-    Reports solves/s."""
+    the same instances launched one at a time, each at the autotuned tiling of
+    its nearest grid side.  Reports solves/s."""
     specs = inputs.swe_humps_batch(count, seed=0)
-    tile = tiling_for("swe", "fp32", (256, 256)) or (64, 16)
+    tile = BATCH_TILES[form]
     stream = torch.cuda.Stream()
     sims = []
     U0s = []
     for sp in specs:
         s = vklb.Sim("swe", (sp.n, sp.n), (0, 0), (1, 1), omega=1.0, cfl=0.3, precision="fp32", stream=stream,
                      form=form)
-        s.set_tiling(*tile)
+        s.set_tiling(*(tiling_for("swe", "fp32", (sp.n, sp.n)) or (128, -1)))
         U0 = torch.from_numpy(inputs.swe_hump_2d(sp.n, sp.amp, sp.x0, sp.y0, sp.sigma)).cuda()
         U0s.append(U0)
         sims.append(s)
@@ -548,7 +555,8 @@ def batched_swe(torch, vklb, count=256, steps=500, form="distributions"):
     b.close()
     for s in sims:
         s.close()
-    return {"instances": count, "steps": steps, "cells_total": cells, "tile": list(tile), "form": form,
+    return {"instances": count, "steps": steps, "cells_total": cells, "tile": list(tile),
+            "plain_tiles": "autotuned per nearest grid side", "form": form,
             "batched_solves_per_s": count / tb, "plain_solves_per_s": count / tp,
             "batched_MLUPS": cells * steps / tb / 1e6, "plain_MLUPS": cells * steps / tp / 1e6,
             "speedup": tp / tb, "batched_vs_plain_rel_l1": diff,
