@@ -87,7 +87,7 @@ class Server:
         self.budget = float(budget_bytes)
         self.tick = int(tick_steps)
         self.precision = precision
-        self.tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (128, 16)}
+        self.tiles = tiles or {"swe": (64, 16), "euler": (64, 16), "mhd_glm": (128, 16)}
         self.keep = keep_results
         self.form = form
         self.streams = {k: torch.cuda.Stream() for k in FAMILY}
@@ -225,15 +225,17 @@ def serve_alone(req, **kw):
 
 def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=None, max_side=2048):
     """Baseline: the same requests one at a time, one launch per step each, the
-    results read back through a pinned buffer as the server reads them."""
+    results read back through a pinned buffer as the server reads them.  Each
+    simulation takes the library's default launch shape for its grid (128 wide,
+    height fitted to whole waves) unless ``tiles`` names one per system."""
     import torch
-    tiles = tiles or {"swe": (128, 8), "euler": (128, 8), "mhd_glm": (128, 16)}
     staging = torch.empty(max(FIELDS.values()) * max_side * max_side, dtype=torch.float64, pin_memory=True).numpy()
     t0 = time.perf_counter()
     for r in requests:
         kw, side = FAMILY[r.system]
         sim = vklb.Sim(r.system, (r.n, r.n), (0.0, 0.0), (side, side), precision=precision, form=form, **kw)
-        sim.set_tiling(*tiles[r.system])
+        if tiles:
+            sim.set_tiling(*tiles[r.system])
         U0 = inputs.request_initial_state(r) if payloads is None else payloads[r.rid]
         sim.set_state(np.ascontiguousarray(U0))
         sim.step(r.steps)
