@@ -103,8 +103,15 @@ typedef struct {
  * (Sec. 5).  eta: 0 for the CFL rule; in (0, 1) the lattice speed follows the
  * centered set's subcharacteristic condition instead (Sec. 2.3),
  * xi = sqrt(3/2) max_j |lambda_j| / eta, as the paper runs the centered set
- * (eta = 0.9, Sec. 5); cfl is then not used. */
+ * (eta = 0.9, Sec. 5); cfl is then not used.
+ * alpha_norm: the normaliser max_j |lambda_j| of the sigmoid weight (Eq. 27),
+ * which the paper does not place: VKLB_ALPHA_LOCAL takes it per cell and
+ * direction; VKLB_ALPHA_GLOBAL takes, for every cell of a step, the grid-wide
+ * maximum over cells, directions and eigenvalues of the state being split (the
+ * quantity Eq. 29 divides by nu; with +-c_h for MHD-GLM), independent of eta,
+ * a fixed dt or the landing rule of vklb_step_to.  Only the weighted set uses it. */
 typedef enum { VKLB_SET_WEIGHTED = 0, VKLB_SET_CENTERED = 1, VKLB_SET_DISCONTINUOUS = 2 } vklb_set;
+typedef enum { VKLB_ALPHA_LOCAL = 0, VKLB_ALPHA_GLOBAL = 1 } vklb_alpha_norm;
 typedef struct {
   int32_t set;
   double c;
@@ -112,6 +119,7 @@ typedef struct {
   double omega;
   double cfl;
   double eta;
+  int32_t alpha_norm;
 } vklb_weight;
 
 /* Arithmetic: FP64 everywhere; FP32 distributions and arithmetic (conservation
@@ -147,7 +155,8 @@ typedef struct {
  * selects the adaptive CFL rule of Eq. (29).  cuda_stream is a cudaStream_t
  * (NULL: the legacy default stream) on which every kernel of this simulation
  * runs.  Parameter checks (returning VKLB_ERR_ARG): omega in (0, 2]
- * (Sec. 2.3); 0 < cfl <= 1 (Eq. 28); eta = 0 or 0 < eta < 1 (Sec. 2.3); dx == dy for D2Q5 (Sec. 3.4); lattice
+ * (Sec. 2.3); 0 < cfl <= 1 (Eq. 28); eta = 0 or 0 < eta < 1 (Sec. 2.3);
+ * alpha_norm one of vklb_alpha_norm; dx == dy for D2Q5 (Sec. 3.4); lattice
  * matches grid->dim; characteristic boundaries only on D1Q3.  On success
  * *out owns two device distribution buffers of q * p * cells values each. */
 int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid,

@@ -9,9 +9,10 @@ weighted (the paper's method, Sec. 3.1):
   A = dF/dU (Eq. 15), the oracle evaluates the matrix function directly:
       alpha(A) = E (E + I)^-1,  E = expm(k A / max_j |lambda_j|).
   This is exact (up to rounding) whatever eigenbasis one would pick, including
-  repeated eigenvalues.  max_j |lambda_j| is taken per cell and per direction
-  (the paper leaves this open; this is reading R1 of oracle/vklb.py), from the
-  closed-form wave speeds.
+  repeated eigenvalues.  The paper leaves open over what max_j |lambda_j| is
+  taken (reading R1 of oracle/vklb.py): by default per cell and per direction,
+  from the closed-form wave speeds; given ``lam_norm``, that one number for
+  every cell (the grid-wide maximum of Eq. 29).
 
 discontinuous (Sec. 2.2, Eqs. (17)-(18)): phi split by the sign of lambda,
   lambda >= 0 -> "+".  Evaluated literally by eigen-decomposition.
@@ -51,15 +52,20 @@ def sigmoid_weight(lam, lam_max, k):
     return 1.0 / (1.0 + np.exp(-k * lam / lam_max))
 
 
-def split_weighted(system, U, d, k):
+def split_weighted(system, U, d, k, lam_norm=None):
     """Weighted upwind splitting (Eqs. 25-27) as alpha(A) F.  U: [p, N].
-    Returns (F+, F-), each [p, N]."""
+    alpha's normaliser max_j |lambda_j| is the cell's own along d, or
+    ``lam_norm`` (a positive number) for every cell.  Returns (F+, F-), each
+    [p, N]."""
     F = np.real(system.flux(U, d))
     if k == 0.0:
         return 0.5 * F, 0.5 * F
     p, N = U.shape
     A = jacobian(system, U, d)
-    lam_max = system.max_speed(U, d)
+    if lam_norm is None:
+        lam_max = system.max_speed(U, d)
+    else:
+        lam_max = np.full(N, float(lam_norm))
     lam_max = np.where(lam_max > 0, lam_max, 1.0)
     E = sla.expm(k * A / lam_max[:, None, None])
     EF = np.einsum("nij,jn->ni", E, F)
@@ -67,16 +73,20 @@ def split_weighted(system, U, d, k):
     return Fp, F - Fp
 
 
-def split_eig(system, U, d, weight):
+def split_eig(system, U, d, weight, lam_norm=None):
     """Literal eigen route (Eqs. 15, 16, 25, 26): A = P Lambda P^-1,
     phi = P^-1 F, F+ = sum_j weight(lambda_j, max|lambda|) phi_j r_j.
-    ``weight(lam, lam_max)`` returns the "+" fraction per eigenvalue.
+    ``weight(lam, lam_max)`` returns the "+" fraction per eigenvalue; lam_max is
+    the largest |eigenvalue| of the cell, or ``lam_norm`` when given.
     Only meaningful where A has a well-conditioned eigenbasis."""
     F = np.real(system.flux(U, d))
     A = jacobian(system, U, d)
     w, P = np.linalg.eig(A)
     lam = np.real(w)                                   # [N, p]
-    lam_max = np.max(np.abs(lam), axis=1)              # [N]
+    if lam_norm is None:
+        lam_max = np.max(np.abs(lam), axis=1)          # [N]
+    else:
+        lam_max = np.full(lam.shape[0], float(lam_norm))
     phi = np.linalg.solve(P, F.T[:, :, None].astype(P.dtype))[:, :, 0]
     wts = weight(lam, lam_max[:, None])
     Fp = np.real(np.einsum("nij,nj->ni", P, wts * phi)).T
@@ -94,9 +104,9 @@ def split_centered(system, U, d):
     return 0.5 * F, 0.5 * F
 
 
-def split(system, U, d, set_kind, k):
+def split(system, U, d, set_kind, k, lam_norm=None):
     if set_kind == "weighted":
-        return split_weighted(system, U, d, k)
+        return split_weighted(system, U, d, k, lam_norm)
     if set_kind == "centered":
         return split_centered(system, U, d)
     if set_kind == "discontinuous":

@@ -14,7 +14,12 @@ Lattices: D1Q3 v = (xi, 0, -xi) (Sec. 2.2, Fig. 1); D2Q5 v = (xi,0), (-xi,0),
 (0,0), (0,xi), (0,-xi) (Eq. 38).  Distributions are stored f[q, field, (y,) x].
 
 Readings of the paper taken here, where it is silent or ambiguous:
-  R1  alpha normaliser max_j|lambda_j| is per cell and direction.
+  R1  alpha normaliser max_j|lambda_j| (Eq. 27): ``alpha_norm="local"`` takes it
+      per cell and direction; ``alpha_norm="global"`` takes one number per
+      step, the grid-wide maximum over cells, directions and eigenvalues of the
+      state being split (the quantity Eq. 29 divides by nu; MHD-GLM includes
+      c_h).  The paper's wording fits either; the two readings give different
+      schemes wherever the wave speeds vary over the grid.
   R2  xi is the max over all cells, both directions and all eigenvalues.
   R3  run_to(T) lands on T with evenly spread steps: every step takes
       xi_eff = m dx / (T - t), m = ceil((T - t) xi / dx) (the number of
@@ -78,10 +83,12 @@ class Sim:
     set_kind : "weighted" (c, k), "centered" (c = 1/Q, F/2), "discontinuous"
     omega    : relaxation parameter, 0 < omega <= 2 (Sec. 2.3)
     nu       : CFL number (Eq. 29);  dt > 0 fixes xi = dx / dt instead
+    alpha_norm: "local" or "global", reading R1 of alpha's normaliser
     """
 
     def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted",
-                 c=0.05, k=2.0, omega=1.0, nu=0.9, dt=None, ch_factor=6.0, eta=None):
+                 c=0.05, k=2.0, omega=1.0, nu=0.9, dt=None, ch_factor=6.0, eta=None,
+                 alpha_norm="local"):
         self.sys = system
         self.dim = system.dim
         self.n = tuple(int(v) for v in n)
@@ -114,6 +121,9 @@ class Sim:
         self.eta = None if eta is None else float(eta)
         self.fixed_xi = None if dt is None or dt <= 0 else self.dx / float(dt)
         self.ch_factor = float(ch_factor)
+        if alpha_norm not in ("local", "global"):
+            raise ValueError(alpha_norm)
+        self.alpha_norm = alpha_norm
         self.f = None
         self.t = 0.0
         self.steps = 0
@@ -123,17 +133,24 @@ class Sim:
     def _flat(self, U):
         return U.reshape(U.shape[0], -1)
 
-    def split(self, U, d):
+    def split(self, U, d, lam_norm=None):
         Uf = self._flat(U)
-        Fp, Fm = splitting.split(self.sys, Uf, d, self.set_kind, self.k)
+        Fp, Fm = splitting.split(self.sys, Uf, d, self.set_kind, self.k, lam_norm)
         return Fp.reshape(U.shape), Fm.reshape(U.shape)
 
-    def equilibrium(self, U, xi):
+    def equilibrium(self, U, xi, lam_grid=None):
+        """Equilibria of the states U.  With the global reading of R1, alpha is
+        normalised by ``lam_grid``, the grid-wide max |lambda| (default: that of
+        U itself; the boundary states of the characteristic condition pass the
+        whole grid's)."""
+        lam = None
+        if self.alpha_norm == "global":
+            lam = self.max_lambda(U) if lam_grid is None else float(lam_grid)
         if self.dim == 1:
-            Fp, Fm = self.split(U, 0)
+            Fp, Fm = self.split(U, 0, lam)
             return equilibrium_1d(U, Fp, Fm, xi, self.c)
-        Fp1, Fm1 = self.split(U, 0)
-        Fp2, Fm2 = self.split(U, 1)
+        Fp1, Fm1 = self.split(U, 0, lam)
+        Fp2, Fm2 = self.split(U, 1, lam)
         return equilibrium_2d(U, Fp1, Fm1, Fp2, Fm2, xi, self.c)
 
     def refresh_ch(self, U):
@@ -231,7 +248,8 @@ class Sim:
         self.refresh_ch(Un)
         xin = self.cfl_xi(Un)                                 # Eq. (29)
         if self.bc == "characteristic":
-            fb = self.equilibrium(np.stack([Un[:, 0], Un[:, -1]], axis=1), xin)
+            fb = self.equilibrium(np.stack([Un[:, 0], Un[:, -1]], axis=1), xin,
+                                  self.max_lambda(Un))
             fn[:, :, 0] = fb[:, :, 0]                         # Eq. (36), R11
             fn[:, :, -1] = fb[:, :, 1]
         self.f = fn

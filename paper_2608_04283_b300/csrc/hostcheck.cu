@@ -27,21 +27,21 @@ void run(const Sys& sys, int d, int set, double k, double ch, const double* U, i
 }
 
 template <class R>
-int dispatch(int kind, int dim, int d, int set, double k, double ch, double gamma, double g,
+int dispatch(int kind, int dim, int d, int set, double k, double lg, double ch, double gamma, double g,
              double ax, double ay, const double* U, int64_t n, double* Fp, double* F, double* m1,
              double* m2) {
   if (kind == 0) {
-    if (dim == 1) { vk::Advect<R, 1> s; s.a[0] = (R)ax; s.a[1] = (R)ay; run<vk::Advect<R, 1>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
-    else { vk::Advect<R, 2> s; s.a[0] = (R)ax; s.a[1] = (R)ay; run<vk::Advect<R, 2>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
+    if (dim == 1) { vk::Advect<R, 1> s; s.lg = (R)lg; s.a[0] = (R)ax; s.a[1] = (R)ay; run<vk::Advect<R, 1>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
+    else { vk::Advect<R, 2> s; s.lg = (R)lg; s.a[0] = (R)ax; s.a[1] = (R)ay; run<vk::Advect<R, 2>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
   } else if (kind == 1) {
-    if (dim == 1) { vk::SWE<R, 1> s; s.g = (R)g; run<vk::SWE<R, 1>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
-    else { vk::SWE<R, 2> s; s.g = (R)g; run<vk::SWE<R, 2>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
+    if (dim == 1) { vk::SWE<R, 1> s; s.lg = (R)lg; s.g = (R)g; run<vk::SWE<R, 1>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
+    else { vk::SWE<R, 2> s; s.lg = (R)lg; s.g = (R)g; run<vk::SWE<R, 2>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
   } else if (kind == 2) {
-    if (dim == 1) { vk::Euler<R, 1> s; s.gamma = (R)gamma; run<vk::Euler<R, 1>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
-    else { vk::Euler<R, 2> s; s.gamma = (R)gamma; run<vk::Euler<R, 2>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
+    if (dim == 1) { vk::Euler<R, 1> s; s.lg = (R)lg; s.gamma = (R)gamma; run<vk::Euler<R, 1>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
+    else { vk::Euler<R, 2> s; s.lg = (R)lg; s.gamma = (R)gamma; run<vk::Euler<R, 2>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2); }
   } else if (kind == 3) {
     if (dim != 2) return -8;
-    vk::MHDGLM<R> s; s.gamma = (R)gamma; run<vk::MHDGLM<R>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2);
+    vk::MHDGLM<R> s; s.lg = (R)lg; s.gamma = (R)gamma; run<vk::MHDGLM<R>, R>(s, d, set, k, ch, U, n, Fp, F, m1, m2);
   } else {
     return -1;
   }
@@ -49,11 +49,12 @@ int dispatch(int kind, int dim, int d, int set, double k, double ch, double gamm
 }
 }  // namespace
 
-extern "C" int vklb_hc_split(int kind, int dim, int d, int precision, int set, double k, double ch,
+// lg: alpha's normaliser, 0 for the cell's own max |lambda|, else this grid-wide value.
+extern "C" int vklb_hc_split(int kind, int dim, int d, int precision, int set, double k, double lg, double ch,
                              double gamma, double g, double ax, double ay, const double* U,
                              int64_t n, double* Fp, double* F, double* m1, double* m2) {
-  if (precision == 0) return dispatch<double>(kind, dim, d, set, k, ch, gamma, g, ax, ay, U, n, Fp, F, m1, m2);
-  return dispatch<float>(kind, dim, d, set, k, ch, gamma, g, ax, ay, U, n, Fp, F, m1, m2);
+  if (precision == 0) return dispatch<double>(kind, dim, d, set, k, lg, ch, gamma, g, ax, ay, U, n, Fp, F, m1, m2);
+  return dispatch<float>(kind, dim, d, set, k, lg, ch, gamma, g, ax, ay, U, n, Fp, F, m1, m2);
 }
 
 // Characteristic-boundary right-hand side P diag(lambda_j outgoing) P^-1 dU of the
@@ -75,9 +76,10 @@ void run_bc(const Sys& sys, const double* U, const double* dU, int side, int64_t
 template <class R>
 int bc_dispatch(int kind, int side, double gamma, double g, double ax, const double* U, const double* dU, int64_t n,
                 double* out) {
-  if (kind == 0) { vk::Advect<R, 1> s; s.a[0] = (R)ax; s.a[1] = 0; run_bc<vk::Advect<R, 1>, R>(s, U, dU, side, n, out); }
-  else if (kind == 1) { vk::SWE<R, 1> s; s.g = (R)g; run_bc<vk::SWE<R, 1>, R>(s, U, dU, side, n, out); }
-  else if (kind == 2) { vk::Euler<R, 1> s; s.gamma = (R)gamma; run_bc<vk::Euler<R, 1>, R>(s, U, dU, side, n, out); }
+  const double lg = 0.0;
+  if (kind == 0) { vk::Advect<R, 1> s; s.lg = (R)lg; s.a[0] = (R)ax; s.a[1] = 0; run_bc<vk::Advect<R, 1>, R>(s, U, dU, side, n, out); }
+  else if (kind == 1) { vk::SWE<R, 1> s; s.lg = (R)lg; s.g = (R)g; run_bc<vk::SWE<R, 1>, R>(s, U, dU, side, n, out); }
+  else if (kind == 2) { vk::Euler<R, 1> s; s.lg = (R)lg; s.gamma = (R)gamma; run_bc<vk::Euler<R, 1>, R>(s, U, dU, side, n, out); }
   else return -8;
   return 0;
 }
@@ -113,20 +115,21 @@ void run2(const Sys& sys, int set, double k, double ch, const double* U, int64_t
   }
 }
 template <class R>
-int dispatch2(int kind, int set, double k, double ch, double gamma, double g, double ax, double ay, const double* U,
-              int64_t n, double* Fp1, double* F1, double* Fp2, double* F2, double* m1, double* m2, int* ok) {
-  if (kind == 0) { vk::Advect<R, 2> s; s.a[0] = (R)ax; s.a[1] = (R)ay; run2<vk::Advect<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
-  else if (kind == 1) { vk::SWE<R, 2> s; s.g = (R)g; run2<vk::SWE<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
-  else if (kind == 2) { vk::Euler<R, 2> s; s.gamma = (R)gamma; run2<vk::Euler<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
-  else if (kind == 3) { vk::MHDGLM<R> s; s.gamma = (R)gamma; run2<vk::MHDGLM<R>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
+int dispatch2(int kind, int set, double k, double lg, double ch, double gamma, double g, double ax, double ay,
+              const double* U, int64_t n, double* Fp1, double* F1, double* Fp2, double* F2, double* m1, double* m2, int* ok) {
+  if (kind == 0) { vk::Advect<R, 2> s; s.lg = (R)lg; s.a[0] = (R)ax; s.a[1] = (R)ay; run2<vk::Advect<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
+  else if (kind == 1) { vk::SWE<R, 2> s; s.lg = (R)lg; s.g = (R)g; run2<vk::SWE<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
+  else if (kind == 2) { vk::Euler<R, 2> s; s.lg = (R)lg; s.gamma = (R)gamma; run2<vk::Euler<R, 2>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
+  else if (kind == 3) { vk::MHDGLM<R> s; s.lg = (R)lg; s.gamma = (R)gamma; run2<vk::MHDGLM<R>, R>(s, set, k, ch, U, n, Fp1, F1, Fp2, F2, m1, m2, ok); }
   else return -1;
   return 0;
 }
 }  // namespace
 
-extern "C" int vklb_hc_split2(int kind, int precision, int set, double k, double ch, double gamma, double g, double ax,
-                              double ay, const double* U, int64_t n, double* Fp1, double* F1, double* Fp2, double* F2,
-                              double* m1, double* m2, int* ok) {
-  if (precision == 0) return dispatch2<double>(kind, set, k, ch, gamma, g, ax, ay, U, n, Fp1, F1, Fp2, F2, m1, m2, ok);
-  return dispatch2<float>(kind, set, k, ch, gamma, g, ax, ay, U, n, Fp1, F1, Fp2, F2, m1, m2, ok);
+extern "C" int vklb_hc_split2(int kind, int precision, int set, double k, double lg, double ch, double gamma,
+                              double g, double ax, double ay, const double* U, int64_t n, double* Fp1, double* F1,
+                              double* Fp2, double* F2, double* m1, double* m2, int* ok) {
+  if (precision == 0)
+    return dispatch2<double>(kind, set, k, lg, ch, gamma, g, ax, ay, U, n, Fp1, F1, Fp2, F2, m1, m2, ok);
+  return dispatch2<float>(kind, set, k, lg, ch, gamma, g, ax, ay, U, n, Fp1, F1, Fp2, F2, m1, m2, ok);
 }

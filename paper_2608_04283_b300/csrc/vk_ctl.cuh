@@ -24,6 +24,7 @@ struct StepScalars {
   double xi;   // lattice speed of this step
   double xinv; // 1 / xi
   double ch;   // cleaning speed of this step (MHD-GLM)
+  double lam;  // max over the grid of max_j |lambda_j(U^n)| (with +-c_h for MHD-GLM)
   bool done;   // t_end reached: nothing to do
 };
 
@@ -41,6 +42,7 @@ VK_HD StepScalars step_scalars(const Ctl* ctl, int slot, bool mhd, double ch_fac
   double m2 = bits_to_double(ctl->m2[slot]);
   s.ch = mhd ? ch_factor * m2 : 0.0;
   double lam = mhd ? fmax(m1, s.ch) : m1;
+  s.lam = lam;
   s.xi = fixed_xi > 0.0 ? fixed_xi : lam * inv_nu;
   s.done = false;
   if (t_end > 0.0) {

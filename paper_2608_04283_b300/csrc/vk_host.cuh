@@ -44,6 +44,7 @@ struct vklb_sim {
   double dx, ch_factor;
   SysParams sp;
   int set;
+  int anorm;               // alpha's normaliser: 0 per cell, 1 grid-wide (vklb_alpha_norm)
   double c, k, omega, cfl, fixed_xi;
   double inv_nu;   // xi = inv_nu max|lambda|: 1 / cfl, or sqrt(3/2) / eta
   int bc_lo, bc_hi;
@@ -125,6 +126,7 @@ StepArgs<T> make_args(const vklb_sim* s, double t_end) {
   a.t_end = t_end;
   a.ch_factor = s->ch_factor;
   a.set = s->set;
+  a.anorm = s->anorm;
   a.bc_lo = s->bc_lo;
   a.bc_hi = s->bc_hi;
   a.ctl = s->ctl;

@@ -36,20 +36,20 @@ struct SysParams {
 };
 
 template <class Sys> VK_HD Sys make_sys(const SysParams& s);
-template <> VK_HD Advect<float, 1> make_sys(const SysParams& s) { Advect<float, 1> r; r.a[0] = (float)s.ax; r.a[1] = (float)s.ay; return r; }
-template <> VK_HD Advect<double, 1> make_sys(const SysParams& s) { Advect<double, 1> r; r.a[0] = s.ax; r.a[1] = s.ay; return r; }
-template <> VK_HD Advect<float, 2> make_sys(const SysParams& s) { Advect<float, 2> r; r.a[0] = (float)s.ax; r.a[1] = (float)s.ay; return r; }
-template <> VK_HD Advect<double, 2> make_sys(const SysParams& s) { Advect<double, 2> r; r.a[0] = s.ax; r.a[1] = s.ay; return r; }
-template <> VK_HD SWE<float, 1> make_sys(const SysParams& s) { SWE<float, 1> r; r.g = (float)s.g; return r; }
-template <> VK_HD SWE<double, 1> make_sys(const SysParams& s) { SWE<double, 1> r; r.g = s.g; return r; }
-template <> VK_HD SWE<float, 2> make_sys(const SysParams& s) { SWE<float, 2> r; r.g = (float)s.g; return r; }
-template <> VK_HD SWE<double, 2> make_sys(const SysParams& s) { SWE<double, 2> r; r.g = s.g; return r; }
-template <> VK_HD Euler<float, 1> make_sys(const SysParams& s) { Euler<float, 1> r; r.gamma = (float)s.gamma; return r; }
-template <> VK_HD Euler<double, 1> make_sys(const SysParams& s) { Euler<double, 1> r; r.gamma = s.gamma; return r; }
-template <> VK_HD Euler<float, 2> make_sys(const SysParams& s) { Euler<float, 2> r; r.gamma = (float)s.gamma; return r; }
-template <> VK_HD Euler<double, 2> make_sys(const SysParams& s) { Euler<double, 2> r; r.gamma = s.gamma; return r; }
-template <> VK_HD MHDGLM<float> make_sys(const SysParams& s) { MHDGLM<float> r; r.gamma = (float)s.gamma; return r; }
-template <> VK_HD MHDGLM<double> make_sys(const SysParams& s) { MHDGLM<double> r; r.gamma = s.gamma; return r; }
+template <> VK_HD Advect<float, 1> make_sys(const SysParams& s) { Advect<float, 1> r; r.a[0] = (float)s.ax; r.a[1] = (float)s.ay; r.lg = 0.0f; return r; }
+template <> VK_HD Advect<double, 1> make_sys(const SysParams& s) { Advect<double, 1> r; r.a[0] = s.ax; r.a[1] = s.ay; r.lg = 0.0; return r; }
+template <> VK_HD Advect<float, 2> make_sys(const SysParams& s) { Advect<float, 2> r; r.a[0] = (float)s.ax; r.a[1] = (float)s.ay; r.lg = 0.0f; return r; }
+template <> VK_HD Advect<double, 2> make_sys(const SysParams& s) { Advect<double, 2> r; r.a[0] = s.ax; r.a[1] = s.ay; r.lg = 0.0; return r; }
+template <> VK_HD SWE<float, 1> make_sys(const SysParams& s) { SWE<float, 1> r; r.g = (float)s.g; r.lg = 0.0f; return r; }
+template <> VK_HD SWE<double, 1> make_sys(const SysParams& s) { SWE<double, 1> r; r.g = s.g; r.lg = 0.0; return r; }
+template <> VK_HD SWE<float, 2> make_sys(const SysParams& s) { SWE<float, 2> r; r.g = (float)s.g; r.lg = 0.0f; return r; }
+template <> VK_HD SWE<double, 2> make_sys(const SysParams& s) { SWE<double, 2> r; r.g = s.g; r.lg = 0.0; return r; }
+template <> VK_HD Euler<float, 1> make_sys(const SysParams& s) { Euler<float, 1> r; r.gamma = (float)s.gamma; r.lg = 0.0f; return r; }
+template <> VK_HD Euler<double, 1> make_sys(const SysParams& s) { Euler<double, 1> r; r.gamma = s.gamma; r.lg = 0.0; return r; }
+template <> VK_HD Euler<float, 2> make_sys(const SysParams& s) { Euler<float, 2> r; r.gamma = (float)s.gamma; r.lg = 0.0f; return r; }
+template <> VK_HD Euler<double, 2> make_sys(const SysParams& s) { Euler<double, 2> r; r.gamma = s.gamma; r.lg = 0.0; return r; }
+template <> VK_HD MHDGLM<float> make_sys(const SysParams& s) { MHDGLM<float> r; r.gamma = (float)s.gamma; r.lg = 0.0f; return r; }
+template <> VK_HD MHDGLM<double> make_sys(const SysParams& s) { MHDGLM<double> r; r.gamma = s.gamma; r.lg = 0.0; return r; }
 
 // Everything one step of one simulation needs.  The buffer pair is selected
 // with src() / dst(), not indexed by the parity: an indexed member array would
@@ -62,6 +62,7 @@ struct StepArgs {
   int pitch;       // cells per padded row (a multiple of 32 in 2D: pitch / 32 bricks per row)
   double dx, c, omega, k, inv_nu, fixed_xi, t_end, ch_factor;
   int set;
+  int anorm;       // alpha's normaliser: 0 per cell and direction, 1 grid-wide max |lambda| of the step
   int bc_lo, bc_hi;  // 1D: 0 periodic, 1 characteristic
   Ctl* ctl;
   int slot;        // n % 3
@@ -262,6 +263,7 @@ template <class Sys, class R, class T>
 __device__ __forceinline__ BlockConsts<Sys, R> block_consts(const StepArgs<T>& a, const StepScalars& sc) {
   BlockConsts<Sys, R> b;
   b.sys = make_sys<Sys>(a.sp);
+  if (a.anorm) b.sys.lg = (R)sc.lam;
   b.xinv = (R)sc.xinv;
   b.ch = (R)sc.ch;
   b.c = (R)a.c;
@@ -1014,7 +1016,7 @@ __device__ __forceinline__ void feq_d1q3(const Sys& sys, const R* U, R xinv, R c
 template <class Sys, class T, class R>
 __global__ void step1d_kernel(StepArgs<T> a, int nsteps) {
   constexpr int P = Sys::P;
-  const Sys sys = make_sys<Sys>(a.sp);
+  Sys sys = make_sys<Sys>(a.sp);
   const int nx = a.nx;
   const size_t plane = (size_t)nx;
   const bool cl = a.bc_lo == 1, chi = a.bc_hi == 1;
@@ -1028,6 +1030,7 @@ __global__ void step1d_kernel(StepArgs<T> a, int nsteps) {
     const T* fin = a.f[par];
     T* fout = a.f[par ^ 1];
     const R xinv = (R)(1.0 / sc.xi), c = (R)a.c, om = (R)a.omega, kk = (R)a.k;
+    sys.lg = a.anorm ? (R)sc.lam : R(0);
     // collide (Eq. 42) and push-stream (Eq. 43)
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       R f[3][P], U[P], e[3][P];
@@ -1123,9 +1126,12 @@ __global__ void step1d_kernel(StepArgs<T> a, int nsteps) {
     if (threadIdx.x < 2 && ((threadIdx.x == 0 && cl) || (threadIdx.x == 1 && chi))) {
       const int side = threadIdx.x;
       const int ib = side == 0 ? 0 : nx - 1;
-      const double xn = a.fixed_xi > 0.0 ? a.fixed_xi : bits_to_double(vc->m1[(slot + 1) % 3]) * a.inv_nu;
+      const double ln = bits_to_double(vc->m1[(slot + 1) % 3]);
+      const double xn = a.fixed_xi > 0.0 ? a.fixed_xi : ln * a.inv_nu;
+      Sys sb = sys;
+      if (a.anorm) sb.lg = (R)ln;   // the grid-wide max |lambda| of U^{n+1}
       R e[3][P];
-      feq_d1q3<Sys, R>(sys, Ub[side], (R)(1.0 / xn), c, a.set, kk, e);
+      feq_d1q3<Sys, R>(sb, Ub[side], (R)(1.0 / xn), c, a.set, kk, e);
 #pragma unroll
       for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -1166,8 +1172,9 @@ __global__ void init_max_kernel(const double* __restrict__ U, size_t cells, SysP
 template <class Sys, class T, class R, int DIM, int FORM = 0>
 __global__ void init_feq_kernel(const double* __restrict__ U, size_t cells, StepArgs<T> a) {
   constexpr int P = Sys::P;
-  const Sys sys = make_sys<Sys>(a.sp);
   const StepScalars sc = step_scalars(a.ctl, 0, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, -1.0, a.dx);
+  Sys sys = make_sys<Sys>(a.sp);
+  if (a.anorm) sys.lg = (R)sc.lam;
   const R xinv = (R)(1.0 / sc.xi), ch = (R)sc.ch, c = (R)a.c, kk = (R)a.k;
   T* f = a.f[a.parity];
   constexpr int Q = DIM == 1 ? 3 : (FORM == 0 ? 5 : 1);

@@ -2,8 +2,11 @@
 //
 // For each system, split(U, d) returns the physical flux F = F^(d)(U) and
 //     F+ = sum_j alpha(lambda_j) phi_j r_j,   phi = P^-1 F          (Eqs. 16, 25, 26)
-// with alpha of Eq. (27) normalised by max_j |lambda_j| of the cell and direction;
-// F- = F - F+ (Eq. 11).  The eigen-structures are written in closed form:
+// with alpha of Eq. (27) normalised by max_j |lambda_j|; F- = F - F+ (Eq. 11).
+// Over what that maximum runs the paper leaves open: each system carries `lg`,
+// 0 for the cell's own maximum along the direction, or the grid-wide maximum of
+// the step (the number Eq. 29 divides by nu) for every cell.  The
+// eigen-structures are written in closed form:
 //   * shallow water (Eq. 52): r = (1, u -+ c, v), phi_{1,3} = h (u -+ c/2) / 2, and
 //     the shear wave carries no flux (phi_2 = 0);
 //   * Euler (Eq. 54): homogeneous of degree one, so phi_j = lambda_j l_j.U and
@@ -20,16 +23,23 @@
 
 namespace vk {
 
+// alpha's normaliser: the grid-wide lg when set, else the cell's own maximum
+template <class R>
+VK_HD R lam_norm(R lg, R local) {
+  return lg > R(0) ? lg : local;
+}
+
 // ----------------------------------------------------------------- advection
 template <class R, int DIM>
 struct Advect {
   static constexpr int P = 1;
   static constexpr bool MHD = false;
   R a[2];
+  R lg;   // alpha's normaliser: 0 = per cell and direction, else this grid-wide value
   VK_HD void split(const R* U, int d, int set, R k, R ch, R* Fp, R* F) const {
     R ad = a[d];
     F[0] = ad * U[0];
-    R lm = vabs(ad);
+    R lm = lam_norm(lg, vabs(ad));
     R al = lm > R(0) ? alpha_w(ad, k / lm, set) : R(0.5);
     Fp[0] = al * F[0];
   }
@@ -60,6 +70,7 @@ struct SWE {
   static constexpr int P = DIM + 1;
   static constexpr bool MHD = false;
   R g;
+  R lg;   // alpha's normaliser: 0 = per cell and direction, else this grid-wide value
   VK_HD void split(const R* U, int d, int set, R k, R ch, R* Fp, R* F) const {
     const int in = 1 + d;           // normal momentum
     const int it = 2 - d;           // tangential momentum (2D)
@@ -78,7 +89,7 @@ struct SWE {
       for (int i = 0; i < P; ++i) Fp[i] = R(0.5) * F[i];
       return;
     }
-    R lmax = vabs(un) + c;
+    R lmax = lam_norm(lg, vabs(un) + c);
     R kl = k * vrcp(lmax);
     R a1 = alpha_w(un - c, kl, set);
     R a3 = alpha_w(un + c, kl, set);
@@ -116,7 +127,7 @@ struct SWE {
     const R hc = R(0.25) * h * c;   // h c / 4
     const R hu2 = R(0.5) * U[1], hv2 = R(0.5) * U[2];
     {
-      const R kl = k * vrcp(vabs(u) + c);
+      const R kl = k * vrcp(lam_norm(lg, vabs(u) + c));
       const R p1 = alpha_w(u - c, kl, set) * (hu2 - hc);
       const R p3 = alpha_w(u + c, kl, set) * (hu2 + hc);
       const R ps = p1 + p3;
@@ -125,7 +136,7 @@ struct SWE {
       Fp1[2] = ps * v;
     }
     {
-      const R kl = k * vrcp(vabs(v) + c);
+      const R kl = k * vrcp(lam_norm(lg, vabs(v) + c));
       const R p1 = alpha_w(v - c, kl, set) * (hv2 - hc);
       const R p3 = alpha_w(v + c, kl, set) * (hv2 + hc);
       const R ps = p1 + p3;
@@ -161,6 +172,7 @@ struct Euler {
   static constexpr int P = DIM + 2;
   static constexpr bool MHD = false;
   R gamma;
+  R lg;   // alpha's normaliser: 0 = per cell and direction, else this grid-wide value
   // Both directions with shared primitives (2D); w_j = alpha_j lambda_j as in split().
   VK_HD void split2(const R* U, int set, R k, R ch, R* Fp1, R* F1, R* Fp2, R* F2) const {
     const R rho = U[0], ir = vrcp(rho);
@@ -191,7 +203,7 @@ struct Euler {
     const R g2 = R(2) * gm1;
     const R hq = R(0.5) * q2;
     {
-      const R kl = k * vrcp(vabs(u) + a);
+      const R kl = k * vrcp(lam_norm(lg, vabs(u) + a));
       const R l1 = u - a, l3 = u + a;
       const R w1 = alpha_w(l1, kl, set) * l1, w2 = alpha_w(u, kl, set) * u * g2, w3 = alpha_w(l3, kl, set) * l3;
       const R ws = s * (w1 + w2 + w3);
@@ -201,7 +213,7 @@ struct Euler {
       Fp1[3] = s * ((w1 + w3) * H + (w3 - w1) * u * a + w2 * hq);
     }
     {
-      const R kl = k * vrcp(vabs(v) + a);
+      const R kl = k * vrcp(lam_norm(lg, vabs(v) + a));
       const R l1 = v - a, l3 = v + a;
       const R w1 = alpha_w(l1, kl, set) * l1, w2 = alpha_w(v, kl, set) * v * g2, w3 = alpha_w(l3, kl, set) * l3;
       const R ws = s * (w1 + w2 + w3);
@@ -238,7 +250,7 @@ struct Euler {
     }
     R a = vsqrt(gamma * p * ir);
     R H = (E + p) * ir;
-    R lmax = vabs(un) + a;
+    R lmax = lam_norm(lg, vabs(un) + a);
     R kl = k * vrcp(lmax);
     R l1 = un - a, l3 = un + a;
     R w1 = alpha_w(l1, kl, set) * l1;
@@ -324,6 +336,7 @@ struct MHDGLM {
   static constexpr int P = 9;
   static constexpr bool MHD = true;
   R gamma;
+  R lg;   // alpha's normaliser: 0 = per cell and direction, else this grid-wide value
 
   // Fast speed c_f along the normal whose field component is bn.
   VK_HD R fast(R rho, R p, R bn, R bb) const {
@@ -465,8 +478,9 @@ struct MHDGLM {
     }
     const R s = bx >= R(0) ? R(1) : R(-1);
 
-    // sigmoid weights, normalised by the largest |lambda| of the cell (R1)
-    const R lmax = vmax(vabs(u) + cf, ch);
+    // sigmoid weights, normalised by the largest |lambda| of the cell (with
+    // the cleaning waves), or by the grid-wide lg
+    const R lmax = lam_norm(lg, vmax(vabs(u) + cf, ch));
     const R kl = k * vrcp(lmax);
     const R lam[7] = {u - cf, u - ca, u - cs, u, u + cs, u + ca, u + cf};
     R al[7];

@@ -149,6 +149,7 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   if (!(weight->cfl > 0.0 && weight->cfl <= 1.0)) return VKLB_ERR_ARG;       // Eq. (28)
   if (!(weight->eta == 0.0 || (weight->eta > 0.0 && weight->eta < 1.0))) return VKLB_ERR_ARG;   // Sec. 2.3
   if (!(weight->k >= 0.0)) return VKLB_ERR_ARG;
+  if (weight->alpha_norm != VKLB_ALPHA_LOCAL && weight->alpha_norm != VKLB_ALPHA_GLOBAL) return VKLB_ERR_ARG;
   const int64_t nx = grid->n[0], ny = dim == 2 ? grid->n[1] : 1;
   if (nx < 1 || ny < 1 || nx > (1 << 30) || ny > (1 << 30)) return VKLB_ERR_ARG;
   if (nx < 3 && dim == 1) return VKLB_ERR_ARG;
@@ -197,6 +198,7 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   // centered set: c = 1/Q (Eqs. 8-10, 39); discontinuous set: c = 0 (Eqs. 12-14)
   s->c = weight->set == VKLB_SET_CENTERED ? 1.0 / s->Q : (weight->set == VKLB_SET_DISCONTINUOUS ? 0.0 : weight->c);
   s->k = weight->k;
+  s->anorm = weight->alpha_norm;
   s->omega = weight->omega;
   s->cfl = weight->cfl;
   // Eq. (29), or the centered set's subcharacteristic condition (Sec. 2.3)

@@ -29,6 +29,7 @@ FP64, FP32, BF16_STORE = 0, 1, 2
 
 SYSTEM_KIND = {"advection": ADVECT, "swe": SWE, "euler": EULER, "mhd_glm": MHD_GLM}
 SET_KIND = {"weighted": SET_WEIGHTED, "centered": SET_CENTERED, "discontinuous": SET_DISCONTINUOUS}
+ALPHA_NORM = {"local": 0, "global": 1}   # vklb_alpha_norm
 PRECISION = {"fp64": FP64, "fp32": FP32, "bf16": BF16_STORE}
 
 
@@ -47,7 +48,7 @@ class BC(C.Structure):
 
 class Weight(C.Structure):
     _fields_ = [("set", C.c_int32), ("c", C.c_double), ("k", C.c_double), ("omega", C.c_double),
-                ("cfl", C.c_double), ("eta", C.c_double)]
+                ("cfl", C.c_double), ("eta", C.c_double), ("alpha_norm", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -130,11 +131,12 @@ class Sim:
     mhd_glm; ``n`` = (nx,) or (nx, ny); ``lo``/``hi`` domain corners; ``form``
     "moments" keeps U instead of f as the state (D2Q5, omega = 1; vklb_set_form);
     ``eta`` > 0 takes the subcharacteristic lattice speed of the centered set
-    instead of the CFL rule (vklb_weight.eta)."""
+    instead of the CFL rule (vklb_weight.eta); ``alpha_norm`` "local" or
+    "global" places the sigmoid weight's normaliser (vklb_weight.alpha_norm)."""
 
     def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted", c=0.05, k=2.0, omega=1.0,
                  cfl=0.9, dt=0.0, precision="fp32", gamma=1.4, g=9.81, ch_factor=6.0, adv_speed=(1.0, 0.0),
-                 stream=None, form="distributions", eta=0.0):
+                 stream=None, form="distributions", eta=0.0, alpha_norm="local"):
         n = tuple(int(v) for v in n)
         dim = len(n)
         lo = tuple(float(v) for v in np.atleast_1d(lo))
@@ -146,7 +148,8 @@ class Sim:
                     (C.c_double * 2)(hi[0], hi[1] if dim == 2 else 1.0))
         kind = BC_PERIODIC if bc == "periodic" else BC_CHARACTERISTIC
         b = BC((C.c_int32 * 2)(kind, kind), (C.c_int32 * 2)(kind, kind))
-        w = Weight(SET_KIND[set_kind], float(c), float(k), float(omega), float(cfl), float(eta))
+        w = Weight(SET_KIND[set_kind], float(c), float(k), float(omega), float(cfl), float(eta),
+                   ALPHA_NORM[alpha_norm])
         self._h = _P()
         self.system, self.n, self.dim = system, n, dim
         self.precision = precision

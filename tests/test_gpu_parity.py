@@ -43,7 +43,8 @@ def _run_pair(vk, name, U0, n, lo, hi, steps, precision, tile=None, oracle_kw=No
     sim.set_state(U0)
     ref = ovklb.Sim(sysm, n, lo, hi, bc=kw.get("bc", "periodic"), set_kind=kw.get("set_kind", "weighted"),
                     c=kw.get("c", 0.05), k=kw.get("k", 2.0), omega=kw.get("omega", 1.0), nu=kw.get("cfl", 0.9),
-                    dt=kw.get("dt", None), ch_factor=kw.get("ch_factor", 6.0))
+                    dt=kw.get("dt", None), ch_factor=kw.get("ch_factor", 6.0),
+                    alpha_norm=kw.get("alpha_norm", "local"))
     ref.set_state(U0)
     if isinstance(steps, float):
         sim.step_to(steps)

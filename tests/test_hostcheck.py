@@ -15,12 +15,13 @@ _PD = C.POINTER(C.c_double)
 KIND = {"advection": 0, "swe": 1, "euler": 2, "mhd_glm": 3}
 
 
-def hc_split(kind, dim, d, prec, set_kind, k, ch, gamma, g, U, ax=1.0, ay=-0.5):
+def hc_split(kind, dim, d, prec, set_kind, k, ch, gamma, g, U, ax=1.0, ay=-0.5, lg=0.0):
     U = np.ascontiguousarray(U, dtype=np.float64)
     p, n = U.shape
     Fp, F = np.zeros_like(U), np.zeros_like(U)
     m1, m2 = np.zeros(n), np.zeros(n)
-    st = _lib.vklb_hc_split(KIND[kind], dim, d, prec, set_kind, C.c_double(k), C.c_double(ch), C.c_double(gamma),
+    st = _lib.vklb_hc_split(KIND[kind], dim, d, prec, set_kind, C.c_double(k), C.c_double(lg), C.c_double(ch),
+                            C.c_double(gamma),
                             C.c_double(g), C.c_double(ax), C.c_double(ay), U.ctypes.data_as(_PD), C.c_int64(n),
                             Fp.ctypes.data_as(_PD), F.ctypes.data_as(_PD), m1.ctypes.data_as(_PD),
                             m2.ctypes.data_as(_PD))
@@ -48,6 +49,30 @@ def test_weighted_split_matches_oracle(name, dim, kw, prec, tol):
         assert np.max(np.abs(Fp - Fo) / scale) < tol
         lam = s.max_speed(U, d) if name != "mhd_glm" else np.abs(U[1 + d] / U[0]) + s.fast_speed(U, d)
         assert np.allclose(m1, lam, rtol=10 * tol)
+
+
+@pytest.mark.parametrize("name,dim,kw", CASES)
+@pytest.mark.parametrize("prec,tol", [(0, 2e-13), (1, 2e-5)])
+def test_weighted_split_global_normaliser_matches_oracle(name, dim, kw, prec, tol):
+    """alpha normalised by one grid-wide max |lambda| (the global reading of the
+    weight's normaliser): the device split given lg = that maximum equals the
+    oracle's split with the same lam_norm, in both directions."""
+    s = systems.make(name, dim, **kw)
+    gamma, g, ch = kw.get("gamma", 1.4), kw.get("g", 9.81), kw.get("ch", 0.0)
+    U = inputs.random_states(name, 600, seed=33, dim=dim, gamma=gamma)
+    lam = max(float(np.max(s.max_speed(U, d))) for d in range(dim))
+    for d in range(dim):
+        Fp, F, _, _ = hc_split(name, dim, d, prec, 0, 2.0, ch, gamma, g, U, lg=lam)
+        Fo, _ = splitting.split_weighted(s, U, d, 2.0, lam_norm=lam)
+        scale = np.abs(s.flux(U, d)).max(axis=0) + 1.0
+        assert np.max(np.abs(Fp - Fo) / scale) < tol
+        # where the cells' own maxima differ it is not the per-cell split
+        # (MHD-GLM with c_h above every fast speed normalises by c_h either way)
+        Fl, _ = splitting.split_weighted(s, U, d, 2.0)
+        if np.ptp(s.max_speed(U, d)) > 1e-3 * lam:
+            assert np.max(np.abs(Fp - Fl) / scale) > 100 * tol
+        else:
+            assert np.max(np.abs(Fp - Fl) / scale) < tol
 
 
 @pytest.mark.parametrize("name,dim,kw", CASES)
@@ -127,7 +152,8 @@ def test_split2_and_epilogue_match_oracle(name, kw, prec, tol, set_kind):
     out = [np.zeros_like(U) for _ in range(4)]
     m1, m2 = np.zeros(n), np.zeros(n)
     ok = np.zeros(n, dtype=np.int32)
-    st = _lib.vklb_hc_split2(KIND[name], prec, set_kind, C.c_double(2.0), C.c_double(ch), C.c_double(gamma),
+    st = _lib.vklb_hc_split2(KIND[name], prec, set_kind, C.c_double(2.0), C.c_double(0.0), C.c_double(ch),
+                             C.c_double(gamma),
                              C.c_double(g), C.c_double(1.0), C.c_double(-0.5), U.ctypes.data_as(_PD), C.c_int64(n),
                              *[o.ctypes.data_as(_PD) for o in out], m1.ctypes.data_as(_PD), m2.ctypes.data_as(_PD),
                              ok.ctypes.data_as(C.POINTER(C.c_int)))
