@@ -283,7 +283,10 @@ int vklb_batch_destroy(vklb_batch* b);
  * written earlier in the same call, so nothing needs clearing, but calls that
  * overlap on the GPU (other streams, other host threads) race on that array.
  * The first call on a device resolves the array's address (cudaGetSymbolAddress)
- * and should come before any stream capture.  No cudaMalloc or cudaFree. */
+ * and should come before any stream capture; that address is kept for the life
+ * of the process, so a caller that tears the device's primary context down
+ * (cudaDeviceReset) must not call this entry point on that device afterwards.
+ * No cudaMalloc or cudaFree. */
 int vklb_conservation_totals_noalloc(const void* f_dev, int32_t precision, int32_t q, int32_t p, int64_t nx,
                                      int64_t ny, int64_t pitch, double cell_volume, double* totals,
                                      int32_t totals_on_device, void* cuda_stream);

@@ -169,10 +169,18 @@ class Sim:
     def handle(self):
         return self._h
 
+    def _check_device_array(self, U, what):
+        """A torch CUDA tensor handed to the library as a device pointer of
+        p * cells doubles: float64, contiguous, of the state's shape (the
+        library cannot check a device pointer's extent)."""
+        if str(U.dtype) != "torch.float64" or not U.is_contiguous() or tuple(U.shape) != self.shape:
+            raise ValueError(f"{what}: need a contiguous float64 CUDA tensor of shape {self.shape}, "
+                             f"got {U.dtype} {tuple(U.shape)} contiguous={U.is_contiguous()}")
+
     def set_state(self, U):
         """U: numpy float64 [p, (ny,) nx] on the host, or a torch CUDA float64 tensor."""
         if hasattr(U, "is_cuda") and U.is_cuda:
-            assert U.dtype.__str__() == "torch.float64" and U.is_contiguous() and tuple(U.shape) == self.shape
+            self._check_device_array(U, "set_state")
             _check(_lib.vklb_set_state(self._h, _P(U.data_ptr()), 1), "vklb_set_state")
             return
         U = np.ascontiguousarray(U, dtype=np.float64)
@@ -209,10 +217,12 @@ class Sim:
     def moments(self, out=None):
         """U = sum_q f_q as float64: numpy on the host, or into a torch CUDA tensor ``out``."""
         if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            self._check_device_array(out, "moments")
             _check(_lib.vklb_moments(self._h, _P(out.data_ptr()), 1), "vklb_moments")
             return out
         if out is not None:
-            assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == self.shape
+            if not (out.dtype == np.float64 and out.flags.c_contiguous and out.shape == self.shape):
+                raise ValueError(f"moments: need a C-contiguous float64 array of shape {self.shape}")
             _check(_lib.vklb_moments(self._h, out.ctypes.data_as(_P), 0), "vklb_moments")
             return out
         U = np.empty(self.shape, dtype=np.float64)

@@ -61,3 +61,46 @@ def test_null_handles(vk):
     assert lib.vklb_create(None, vk.D2Q5, None, None, None, 0.0, 1, None, None) == vk.ERR_ARG
     for st in (vk.OK, vk.ERR_ARG, vk.ERR_TIMEOUT, vk.ERR_LIMIT):
         assert lib.vklb_strerror(st)
+
+
+def test_create_rejects_unknown_alpha_norm(vk):
+    """vklb_weight.alpha_norm must be VKLB_ALPHA_LOCAL or VKLB_ALPHA_GLOBAL."""
+    s = vk.System(vk.EULER, 1.4, 9.81, 6.0, (C.c_double * 2)(1.0, 0.0))
+    g = vk.Grid(2, (C.c_int64 * 2)(32, 32), (C.c_double * 2)(0.0, 0.0), (C.c_double * 2)(1.0, 1.0))
+    b = vk.BC((C.c_int32 * 2)(0, 0), (C.c_int32 * 2)(0, 0))
+    h = vk._P()
+    for bad in (2, -1):
+        w = vk.Weight(vk.SET_WEIGHTED, 0.05, 2.0, 1.0, 0.9, 0.0, bad)
+        assert vk._lib.vklb_create(C.byref(s), vk.D2Q5, C.byref(g), C.byref(b), C.byref(w), 0.0, vk.FP32, None,
+                                   C.byref(h)) == vk.ERR_ARG
+
+
+class _FakeCuda:
+    """Stands in for a torch CUDA tensor (attributes only, no device memory)."""
+
+    def __init__(self, shape, dtype="torch.float64", contiguous=True):
+        self.is_cuda = True
+        self.shape = shape
+        self.dtype = dtype
+        self._c = contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        raise AssertionError("the library was reached with an unchecked device buffer")
+
+
+@pytest.mark.parametrize("bad", [dict(shape=(4, 32, 31)), dict(shape=(4, 32, 32), dtype="torch.float32"),
+                                 dict(shape=(4, 32, 32), contiguous=False)])
+def test_device_buffers_checked_before_the_library(vk, bad):
+    """moments(out=...) and set_state(...) with a CUDA tensor hand the library a
+    bare device pointer it cannot bound-check: a wrong shape, dtype or layout is
+    rejected in the binding, before any call into the library."""
+    stub = vk.Sim.__new__(vk.Sim)
+    stub.shape = (4, 32, 32)
+    stub._h = vk._P()
+    with pytest.raises(ValueError):
+        vk.Sim.moments(stub, out=_FakeCuda(**bad))
+    with pytest.raises(ValueError):
+        vk.Sim.set_state(stub, _FakeCuda(**bad))

@@ -13,7 +13,7 @@ import pytest
 
 from oracle import systems, vklb as ovklb
 from paper_2608_04283_b300 import inputs
-from parity_util import max_rel, rel_l1, rel_l1_coupled
+from parity_util import max_rel, rel_l1, rel_l1_mhd
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +72,7 @@ def test_moment_form_parity(vk, name, precision, tile):
         assert max_rel(got, want).max() <= 1e-11
         assert abs(t - ref.t) <= 1e-12 * ref.t and abs(xi - ref.xi) <= 1e-11 * ref.xi
     else:
-        err = rel_l1_coupled(got, want) if name == "mhd_glm" else rel_l1(got, want)
+        err = rel_l1_mhd(got, want) if name == "mhd_glm" else rel_l1(got, want)
         assert err.max() <= 1e-5
     assert nsteps == 15
 

@@ -5,7 +5,7 @@ import pytest
 
 from oracle import systems, vklb as ovklb
 from paper_2608_04283_b300 import inputs
-from parity_util import max_rel, rel_l1_coupled
+from parity_util import max_rel, rel_l1_mhd
 
 pytestmark = pytest.mark.gpu
 
@@ -70,8 +70,8 @@ def test_mhd_bounded_kernel_parity(vk):
     """The register-bounded FP32 MHD-GLM step against the oracle on a ragged grid
     (128-thread tiles take the bounded kernel, 256-thread tiles the unbounded one;
     both must agree with the oracle).  The strip of the Orszag-Tang state is not
-    periodic in y, so the seam makes a small psi; the FP32 comparison scales
-    it by the largest field (rel_l1_coupled)."""
+    periodic in y, so the seam makes a small psi; the FP32 comparison measures
+    psi against c_h |B| (rel_l1_mhd)."""
     n = (300, 36)
     L = 2 * np.pi
     U0 = np.ascontiguousarray(inputs.orszag_tang(300)[:, :36, :])
@@ -85,5 +85,5 @@ def test_mhd_bounded_kernel_parity(vk):
         sim.set_tiling(*tile)
         sim.set_state(U0)
         sim.step(10)
-        assert rel_l1_coupled(sim.moments(), want).max() <= 1e-5
+        assert rel_l1_mhd(sim.moments(), want).max() <= 1e-5
         sim.close()
