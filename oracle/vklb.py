@@ -14,12 +14,16 @@ Lattices: D1Q3 v = (xi, 0, -xi) (Sec. 2.2, Fig. 1); D2Q5 v = (xi,0), (-xi,0),
 (0,0), (0,xi), (0,-xi) (Eq. 38).  Distributions are stored f[q, field, (y,) x].
 
 Readings of the paper taken here, where it is silent or ambiguous:
-  R1  alpha normaliser max_j|lambda_j| (Eq. 27): ``alpha_norm="local"`` takes it
-      per cell and direction; ``alpha_norm="global"`` takes one number per
-      step, the grid-wide maximum over cells, directions and eigenvalues of the
-      state being split (the quantity Eq. 29 divides by nu; MHD-GLM includes
-      c_h).  The paper's wording fits either; the two readings give different
-      schemes wherever the wave speeds vary over the grid.
+  R1  alpha normaliser max_j|lambda_j| (Eq. 27): ``alpha_norm="global"`` (the
+      default) takes one number per step, the grid-wide maximum over cells,
+      directions and eigenvalues of the state being split (the quantity Eq. 29
+      divides by nu; MHD-GLM includes c_h); ``alpha_norm="local"`` takes it per
+      cell and direction.  The paper's wording fits either; the two readings
+      give different schemes wherever the wave speeds vary over the grid.  The
+      global one reproduces the paper's omega = 2 vortex study (second order to
+      N = 1024, Sec. 5.2) and its Table 1 dam break at CFL 0.9 to N = 4096
+      (Sec. 5.1); the local one diverges at N >= 512 there and degrades from
+      N = 1024 respectively.
   R2  xi is the max over all cells, both directions and all eigenvalues.
   R3  run_to(T) lands on T with evenly spread steps: every step takes
       xi_eff = m dx / (T - t), m = ceil((T - t) xi / dx) (the number of
@@ -88,7 +92,7 @@ class Sim:
 
     def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted",
                  c=0.05, k=2.0, omega=1.0, nu=0.9, dt=None, ch_factor=6.0, eta=None,
-                 alpha_norm="local"):
+                 alpha_norm="global"):
         self.sys = system
         self.dim = system.dim
         self.n = tuple(int(v) for v in n)

@@ -198,7 +198,7 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   // centered set: c = 1/Q (Eqs. 8-10, 39); discontinuous set: c = 0 (Eqs. 12-14)
   s->c = weight->set == VKLB_SET_CENTERED ? 1.0 / s->Q : (weight->set == VKLB_SET_DISCONTINUOUS ? 0.0 : weight->c);
   s->k = weight->k;
-  s->anorm = weight->alpha_norm;
+  s->anorm = weight->alpha_norm == VKLB_ALPHA_GLOBAL ? 1 : 0;
   s->omega = weight->omega;
   s->cfl = weight->cfl;
   // Eq. (29), or the centered set's subcharacteristic condition (Sec. 2.3)

@@ -29,7 +29,7 @@ FP64, FP32, BF16_STORE = 0, 1, 2
 
 SYSTEM_KIND = {"advection": ADVECT, "swe": SWE, "euler": EULER, "mhd_glm": MHD_GLM}
 SET_KIND = {"weighted": SET_WEIGHTED, "centered": SET_CENTERED, "discontinuous": SET_DISCONTINUOUS}
-ALPHA_NORM = {"local": 0, "global": 1}   # vklb_alpha_norm
+ALPHA_NORM = {"global": 0, "local": 1}   # vklb_alpha_norm
 PRECISION = {"fp64": FP64, "fp32": FP32, "bf16": BF16_STORE}
 
 
@@ -131,12 +131,12 @@ class Sim:
     mhd_glm; ``n`` = (nx,) or (nx, ny); ``lo``/``hi`` domain corners; ``form``
     "moments" keeps U instead of f as the state (D2Q5, omega = 1; vklb_set_form);
     ``eta`` > 0 takes the subcharacteristic lattice speed of the centered set
-    instead of the CFL rule (vklb_weight.eta); ``alpha_norm`` "local" or
-    "global" places the sigmoid weight's normaliser (vklb_weight.alpha_norm)."""
+    instead of the CFL rule (vklb_weight.eta); ``alpha_norm`` "global" (default) or
+    "local" places the sigmoid weight's normaliser (vklb_weight.alpha_norm)."""
 
     def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted", c=0.05, k=2.0, omega=1.0,
                  cfl=0.9, dt=0.0, precision="fp32", gamma=1.4, g=9.81, ch_factor=6.0, adv_speed=(1.0, 0.0),
-                 stream=None, form="distributions", eta=0.0, alpha_norm="local"):
+                 stream=None, form="distributions", eta=0.0, alpha_norm="global"):
         n = tuple(int(v) for v in n)
         dim = len(n)
         lo = tuple(float(v) for v in np.atleast_1d(lo))

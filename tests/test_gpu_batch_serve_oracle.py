@@ -91,5 +91,5 @@ def test_served_fp64_against_oracle(vk):
         r = job.req
         kw, side = serve.FAMILY[r.system]
         ref = _oracle(mk[r.system](), (r.n, r.n), side, inputs.request_initial_state(r), r.steps,
-                      omega=kw["omega"], nu=kw["cfl"], alpha_norm=kw.get("alpha_norm", "local"))
+                      omega=kw["omega"], nu=kw["cfl"], alpha_norm=kw.get("alpha_norm", "global"))
         assert max_rel(job.result, ref.moments()).max() <= 1e-11, r

@@ -61,7 +61,9 @@ def _samples():
     return pts
 
 
-def _oracle_at(U0, pts, xi0):
+def _oracle_at(U0, pts, xi0, lam0):
+    """5 x 5 periodic patches with the full grid's xi_0 (fixed dt) and the full
+    grid's max |lambda|, alpha's normaliser under the global reading."""
     dx = L / N
     sysm = systems.Euler(GAMMA, 2)
     out = np.empty((U0.shape[0], len(pts)))
@@ -71,6 +73,7 @@ def _oracle_at(U0, pts, xi0):
         patch = U0[:, ys][:, :, xs]
         ref = ovklb.Sim(sysm, (5, 5), (0.0, 0.0), (5 * dx, 5 * dx), omega=KW["omega"], nu=KW["cfl"], c=KW["c"],
                         k=KW["k"], dt=dx / xi0)
+        ref.max_lambda = lambda U: lam0
         ref.set_state(patch)
         ref.step()
         out[:, i] = ref.moments()[:, 2, 2]
@@ -90,13 +93,14 @@ def test_fullsize_one_step_sampled(vk, U0, precision, tol):
     sim.close()
 
     full = ovklb.Sim(systems.Euler(GAMMA, 2), (N, N), (0.0, 0.0), (L, L), omega=KW["omega"], nu=KW["cfl"])
-    xi0 = full.max_lambda(U0) / KW["cfl"]                   # Eq. (29) over the full grid
+    lam0 = full.max_lambda(U0)
+    xi0 = lam0 / KW["cfl"]                                  # Eq. (29) over the full grid
     dx = L / N
     assert nsteps == 1
     assert abs(t - dx / xi0) <= (1e-6 if precision == "fp32" else 1e-13) * (dx / xi0)
 
     pts = _samples()
-    want = _oracle_at(U0, pts, xi0)
+    want = _oracle_at(U0, pts, xi0, lam0)
     have = np.stack([got[:, y, x] for x, y in pts], axis=1)
     err = max_rel(have, want)
     assert err.max() <= tol, err
@@ -146,7 +150,8 @@ def test_fullsize_mhd_one_step_sampled(vk, precision, tol):
     full = ovklb.Sim(sysm, (MN, MN), (0.0, 0.0), (ML, ML), omega=1.0, nu=MKW["cfl"], ch_factor=MKW["ch_factor"])
     full.refresh_ch(U0)
     ch = full.sys.ch
-    xi0 = full.max_lambda(U0) / MKW["cfl"]
+    lam0 = full.max_lambda(U0)
+    xi0 = lam0 / MKW["cfl"]
     dx = ML / MN
     assert nsteps == 1
     assert abs(t - dx / xi0) <= (1e-6 if precision == "fp32" else 1e-13) * (dx / xi0)
@@ -162,6 +167,7 @@ def test_fullsize_mhd_one_step_sampled(vk, precision, tol):
         ref = ovklb.Sim(systems.MHDGLM(MKW["gamma"]), (5, 5), (0.0, 0.0), (5 * dx, 5 * dx), omega=1.0,
                         nu=MKW["cfl"], c=MKW["c"], k=MKW["k"], dt=dx / xi0, ch_factor=MKW["ch_factor"])
         ref.refresh_ch = lambda U, r=ref: setattr(r.sys, "ch", ch)      # the full grid's c_h
+        ref.max_lambda = lambda U: lam0                                  # and max |lambda|
         ref.set_state(patch)
         ref.step()
         want[:, i] = ref.moments()[:, 2, 2]

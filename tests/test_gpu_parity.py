@@ -44,7 +44,7 @@ def _run_pair(vk, name, U0, n, lo, hi, steps, precision, tile=None, oracle_kw=No
     ref = ovklb.Sim(sysm, n, lo, hi, bc=kw.get("bc", "periodic"), set_kind=kw.get("set_kind", "weighted"),
                     c=kw.get("c", 0.05), k=kw.get("k", 2.0), omega=kw.get("omega", 1.0), nu=kw.get("cfl", 0.9),
                     dt=kw.get("dt", None), ch_factor=kw.get("ch_factor", 6.0),
-                    alpha_norm=kw.get("alpha_norm", "local"))
+                    alpha_norm=kw.get("alpha_norm", "global"))
     ref.set_state(U0)
     if isinstance(steps, float):
         sim.step_to(steps)
@@ -170,11 +170,10 @@ def test_dam_break_1d_fp32(vk):
 def test_dam_break_config_paper_cfl(vk):
     """The dam break at the paper's CFL 0.9: FP64 parity holds over the first 30
     steps; beyond that the run is ill-conditioned (the weighted set amplifies
-    rounding in the left rest state: at rest its momentum diffusion passes 1/2
-    above a local CFL number of about 0.67, and the left state sits at 0.785,
-    test_weighted_set_rest_state_instability), so the full run to
-    t = 0.1 is checked against the exact solution with the spread the oracle
-    itself shows under 1e-15 input perturbations."""
+    rounding in the left rest state: linearised there, its checkerboard mode
+    grows by 1.20 a step with the grid-wide normaliser, 1.32 with the per-cell
+    one), so the full run to t = 0.1 is checked against the exact solution with
+    the spread the oracle itself shows under 1e-15 input perturbations."""
     U0 = inputs.dam_break_1d(400)
     got, want, _, _, _ = _run_pair(vk, "swe", U0, (400,), (0.0,), (1.0,), 30, "fp64", bc="characteristic",
                                    omega=1.0, cfl=0.9)
@@ -186,9 +185,9 @@ def test_dam_break_config_paper_cfl(vk):
     x = inputs.cell_centers(400, 0.0, 1.0)
     h, u = riemann.swe_sample(2.0, 0.0, 1.0, 0.0, 9.81, x, 0.1, x0=0.5)
     e_gpu = np.abs(U[0] - h).sum() / 400
-    assert 1.0e-2 < e_gpu < 3.0e-2      # oracle: 1.60e-2 .. 2.12e-2 over 6 perturbed runs
+    assert 4.0e-3 < e_gpu < 1.3e-2      # oracle: 5.45e-3 .. 9.83e-3 over 8 runs, 7 of them perturbed
     right = x > 0.3
-    assert np.abs(U[0] - h)[right].sum() / 400 < 5e-3
+    assert np.abs(U[0] - h)[right].sum() / 400 < 2.5e-3     # oracle: 1.23e-3 .. 1.34e-3
 
 
 def test_sod_1d_fp64(vk):

@@ -78,20 +78,23 @@ def test_advection_exact_shift(a):
     assert sim.t == pytest.approx(5 * (1 / 16) / abs(a))
 
 
-def test_thm42_finite_difference_form_omega1():
+@pytest.mark.parametrize("norm", ["global", "local"])
+def test_thm42_finite_difference_form_omega1(norm):
     """Thm 4.2 (Eq. 46): with omega = 1, U^{n+1}_i = U_i + c (U_{i-1} - 2U_i + U_{i+1})
     - (F+_i - F+_{i-1})/xi - (F-_{i+1} - F-_i)/xi, and Thm 4.3 (Eq. 49): the same
-    as U_i - (G_{i+1/2} - G_{i-1/2})/xi with G_{i+1/2} = F+_i + F-_{i+1} - c xi (U_{i+1} - U_i)."""
+    as U_i - (G_{i+1/2} - G_{i-1/2})/xi with G_{i+1/2} = F+_i + F-_{i+1} - c xi (U_{i+1} - U_i).
+    Under either reading of alpha's normaliser (the split takes the same one)."""
     s = systems.ShallowWater(9.81, 1)
     x = inputs.cell_centers(32, 0.0, 1.0)
     h = 1.0 + 0.2 * np.sin(2 * np.pi * x)
     U = np.stack([h, 0.3 * h * np.cos(2 * np.pi * x)])
-    sim = vklb.Sim(s, (32,), (0,), (1,), omega=1.0, c=0.05, k=2.0, nu=0.9)
+    sim = vklb.Sim(s, (32,), (0,), (1,), omega=1.0, c=0.05, k=2.0, nu=0.9, alpha_norm=norm)
     sim.set_state(U)
     for _ in range(3):
         Un = sim.moments()
         xi = sim.xi
-        Fp, Fm = splitting.split_weighted(s, Un, 0, 2.0)
+        lam = float(np.max(np.abs(Un[1] / Un[0]) + np.sqrt(9.81 * Un[0]))) if norm == "global" else None
+        Fp, Fm = splitting.split_weighted(s, Un, 0, 2.0, lam_norm=lam)
         sh = lambda a, m: np.roll(a, m, axis=-1)
         fd = Un + 0.05 * (sh(Un, 1) - 2 * Un + sh(Un, -1)) - (Fp - sh(Fp, 1)) / xi - (sh(Fm, -1) - Fm) / xi
         G = Fp + sh(Fm, -1) - 0.05 * xi * (sh(Un, -1) - Un)         # G_{i+1/2}
@@ -101,18 +104,20 @@ def test_thm42_finite_difference_form_omega1():
         assert np.allclose(sim.moments(), fv, rtol=1e-13, atol=1e-13)
 
 
-def test_fv_form_2d_omega1():
+@pytest.mark.parametrize("norm", ["global", "local"])
+def test_fv_form_2d_omega1(norm):
     """2D analogue of Thm 4.3: with omega = 1 the D2Q5 update is the sum of the
     x and y finite-volume flux differences (Eq. 41 substituted in Eq. 6)."""
     e = systems.Euler(1.4, 2)
     U = inputs.entropy_wave_2d(12)
-    sim = vklb.Sim(e, (12, 12), (0, 0), (1, 1), omega=1.0, c=0.05, k=2.0, nu=0.5)
+    sim = vklb.Sim(e, (12, 12), (0, 0), (1, 1), omega=1.0, c=0.05, k=2.0, nu=0.5, alpha_norm=norm)
     sim.set_state(U)
     sim.step()
     Un = sim.moments()
     xi = sim.xi
-    Fp1, Fm1 = splitting.split_weighted(e, Un.reshape(4, -1), 0, 2.0)
-    Fp2, Fm2 = splitting.split_weighted(e, Un.reshape(4, -1), 1, 2.0)
+    lam = sim.max_lambda(Un) if norm == "global" else None
+    Fp1, Fm1 = splitting.split_weighted(e, Un.reshape(4, -1), 0, 2.0, lam_norm=lam)
+    Fp2, Fm2 = splitting.split_weighted(e, Un.reshape(4, -1), 1, 2.0, lam_norm=lam)
     r = lambda a: a.reshape(Un.shape)
     Fp1, Fm1, Fp2, Fm2 = r(Fp1), r(Fm1), r(Fp2), r(Fm2)
     sx = lambda a, m: np.roll(a, m, axis=-1)
@@ -280,25 +285,31 @@ def test_run_to_lands_on_t_end():
     assert 200 < sim.steps < 260
 
 
-def test_one_step_is_local_given_global_xi():
+@pytest.mark.parametrize("norm", ["global", "local"])
+def test_one_step_is_local_given_global_xi(norm):
     """One step at a cell depends only on its 5-point neighbourhood (Eqs. 42-43)
-    and on the global xi (Eq. 29): an oracle run on the 5 x 5 periodic patch with
-    xi fixed at the full grid's xi_0 reproduces the full grid's step at the
-    patch centre.  (The full-size GPU parity test samples cells this way.)"""
+    and on the global xi (Eq. 29) -- and, under the global reading of alpha's
+    normaliser, the grid-wide max |lambda| of the step: an oracle run on the
+    5 x 5 periodic patch with xi fixed at the full grid's xi_0 (and the full
+    grid's max |lambda|) reproduces the full grid's step at the patch centre.
+    (The full-size GPU parity test samples cells this way.)"""
     n = 16
     L = 10.0
     U0 = inputs.isentropic_vortex(n, lo=0.0, hi=L)
     sysm = systems.Euler(1.4, 2)
-    full = vklb.Sim(sysm, (n, n), (0.0, 0.0), (L, L), omega=2.0, nu=0.3)
+    full = vklb.Sim(sysm, (n, n), (0.0, 0.0), (L, L), omega=2.0, nu=0.3, alpha_norm=norm)
     full.set_state(U0)
     xi0 = full.xi
+    lam0 = full.max_lambda(U0)
     full.step()
     Uf = full.moments()
     dx = L / n
     for x, y in [(0, 0), (15, 3), (7, 8), (8, 15)]:
         xs = np.arange(x - 2, x + 3) % n
         ys = np.arange(y - 2, y + 3) % n
-        ref = vklb.Sim(sysm, (5, 5), (0.0, 0.0), (5 * dx, 5 * dx), omega=2.0, nu=0.3, dt=dx / xi0)
+        ref = vklb.Sim(sysm, (5, 5), (0.0, 0.0), (5 * dx, 5 * dx), omega=2.0, nu=0.3, dt=dx / xi0,
+                       alpha_norm=norm)
+        ref.max_lambda = lambda U: lam0        # the full grid's (xi is fixed by dt)
         ref.set_state(U0[:, ys][:, :, xs])
         ref.step()
         np.testing.assert_allclose(ref.moments()[:, 2, 2], Uf[:, y, x], rtol=1e-13, atol=0)
