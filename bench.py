@@ -11,9 +11,9 @@ bracketed by CUDA events on the simulation's stream, after an L2 flush (the
 256 MiB read of another buffer, so that the flush's own dirty lines are written
 back before the step starts rather than inside it.  Every
 200 steps the state is re-initialised outside the timed events: at omega = 2 the
-weighted set amplifies rounding on this vortex (FP64 perturbations grow 25-40x
-per 100 steps) and an FP32 run would leave the physical range after about 400
-steps.
+weighted set amplifies rounding (FP32 stays within 1 % of the FP64 error against
+the exact solution to about 1,000 steps of this vortex, and one period takes
+10^4), so the timed steps always advance a state of the paper's problem.
 
 --impl reference times the FP64 CPU oracle (oracle/, test infrastructure) on the
 host cores on a bounded sample of the same workload.
@@ -52,6 +52,7 @@ WORKLOADS = {
 }
 REINIT_EVERY = 200
 FLUSH_BYTES = 256 << 20
+NOMINAL_HBM_GBS = 8000.0   # nominal B300 HBM3e bandwidth (8 TB/s), beside the measured copy peak
 
 
 # the device code the step kernels compile from: DRAM traffic recorded by a
@@ -343,14 +344,17 @@ def run_ours(args, wl):
     traffic = traffic_record(key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_src + " (burst)",
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "algorithmic_bytes_per_lup": bpl, "kernel": kname}
 
     extras = {}
     acc = None
+    acc_exact = None
     e2e = None
     cpu = None
     if rank == 0 and not args.timed_only:
         acc = accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps=50, form=args.form)
+        acc_exact = accuracy_vs_exact(vklb, prec) if prec != "fp64" else None
         e2e = end_to_end(torch, vklb, wl, prec, tile, steps=min(args.steps, REINIT_EVERY), U0=U0, form=args.form)
         if not args.no_extras and args.workload == "euler_vortex_1024":
             extras["mhd_orszag_tang_2048"] = secondary(torch, vklb, WORKLOADS["mhd_orszag_tang_2048"], prec,
@@ -376,6 +380,7 @@ def run_ours(args, wl):
                            "reinit_every": REINIT_EVERY, "parallelism": "replicas" if world > 1 else "single"},
                 "hbm_gbs": achieved, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(l1 - l0), "clocks": clk, "accuracy_fp32_vs_fp64": acc,
+                "accuracy_fp32_vs_exact": acc_exact,
                 "step_ms": {"median": float(np.median(durs)), "p10": float(np.percentile(durs, 10)),
                             "p90": float(np.percentile(durs, 90))},
                 "extras": extras}
@@ -403,27 +408,75 @@ def accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps, form="distributions"):
         res.append(s.moments())
         s.close()
     a, b = res
+    ch = None
+    if wl["system"] == "mhd_glm":
+        ch = wl["kw"]["ch_factor"] * mhd_max_fast_speed(b, wl["kw"]["gamma"])
+    l1 = rel_norm(a, b, lambda x: np.abs(x).sum(), ch)
+    linf = rel_norm(a, b, lambda x: np.abs(x).max(), ch)
     out["steps"] = steps
-    out["rel_l1_max_field"] = float(rel_norm(a, b, lambda x: np.abs(x).sum()).max())
-    out["rel_linf_max_field"] = float(rel_norm(a, b, lambda x: np.abs(x).max()).max())
-    out["rule"] = ("per field |a - b| / |b|; a field whose reference norm is below 1e-2 of the largest "
-                   "field's (psi, B_z, m_z of Orszag-Tang: zero or at rounding level) is scaled by the largest")
+    out["rel_l1_per_field"] = [float(v) for v in l1]
+    out["rel_linf_per_field"] = [float(v) for v in linf]
+    out["rel_l1_max_field"] = float(l1.max())
+    out["rel_linf_max_field"] = float(linf.max())
+    out["rule"] = ("per field |a - b| / |b|; MHD-GLM's m_z, B_z and psi (zero or at rounding level in "
+                   "Orszag-Tang) against the terms that carry them: |m|, |B| and c_h |B|")
     return out
 
 
-def rel_norm(a, b, norm, small=1e-2):
-    """Per-field norm of a - b relative to b's; a field whose norm is below
-    ``small`` of the largest field's is measured against the largest instead
-    (MHD-GLM's psi stays at rounding level in Orszag-Tang, 1e-7 of the energy,
-    and the divergence errors that feed it differ from FP32 to FP64 run)."""
-    big = max(norm(b[k]) for k in range(b.shape[0]))
-    out = []
-    for k in range(b.shape[0]):
-        s = norm(b[k])
-        if s <= small * big:
-            s = big
-        out.append(norm(a[k] - b[k]) / s)
-    return np.array(out)
+def mhd_max_fast_speed(U, gamma):
+    """Largest fast magnetosonic speed over the grid and both directions."""
+    rho = U[0]
+    bb = U[5] ** 2 + U[6] ** 2 + U[7] ** 2
+    p = (gamma - 1.0) * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / rho - 0.5 * bb)
+    a2, b2 = gamma * p / rho, bb / rho
+    best = 0.0
+    for d in (0, 1):
+        bn2 = U[5 + d] ** 2 / rho
+        cf = np.sqrt(0.5 * (a2 + b2 + np.sqrt(np.maximum((a2 + b2) ** 2 - 4.0 * a2 * bn2, 0.0))))
+        best = max(best, float(cf.max()))
+    return best
+
+
+def rel_norm(a, b, norm, ch=None):
+    """Per-field norm of a - b relative to b's.  For MHD-GLM (ch given) the
+    fields Orszag-Tang keeps at zero or at rounding level take the scale of the
+    terms that carry them: m_z that of |m|, B_z that of |B|, psi that of c_h |B|
+    (its distribution components carry the cleaning waves' c_h B_n / 2)."""
+    scale = [norm(b[k]) for k in range(b.shape[0])]
+    if ch is not None:
+        m = np.sqrt(b[1] ** 2 + b[2] ** 2 + b[3] ** 2)
+        B = np.sqrt(b[5] ** 2 + b[6] ** 2 + b[7] ** 2)
+        scale[3] = max(scale[3], norm(m))
+        scale[7] = max(scale[7], norm(B))
+        scale[8] = max(scale[8], ch * norm(B))
+    return np.array([norm(a[k] - b[k]) / scale[k] for k in range(b.shape[0])])
+
+
+def accuracy_vs_exact(vklb, prec, n=128, T=2.0):
+    """Error against the exact solution (the vortex translated by (T, T), Eq. 57)
+    of the benchmarked precision and of the FP64 path, L1 and L-infinity per
+    field, at the paper's vortex setting (omega 2, CFL 0.3, T = 2) and the
+    largest side at which FP32 can meet 1 % of FP64's error (omega = 2 amplifies
+    rounding; tests/test_gpu_accuracy_exact.py)."""
+    wl = WORKLOADS["euler_vortex_1024"]
+    ex = inputs.isentropic_vortex(n, shift=(T, T))
+    out = {"workload": f"Euler vortex {n}x{n}, omega 2, CFL 0.3, T = {T}"}
+    errs = {}
+    for p in (prec, "fp64"):
+        s = vklb.Sim("euler", (n, n), wl["lo"], wl["hi"], precision=p, **wl["kw"])
+        s.set_state(inputs.isentropic_vortex(n))
+        s.step_to(T)
+        d = np.abs(s.moments() - ex).reshape(4, -1)
+        s.close()
+        errs[p] = (d.mean(axis=1), d.max(axis=1))
+    out[f"{prec}_l1"] = [float(v) for v in errs[prec][0]]
+    out[f"{prec}_linf"] = [float(v) for v in errs[prec][1]]
+    out["fp64_l1"] = [float(v) for v in errs["fp64"][0]]
+    out["fp64_linf"] = [float(v) for v in errs["fp64"][1]]
+    out["max_rel_diff_l1"] = float(np.max(np.abs(errs[prec][0] - errs["fp64"][0]) / errs["fp64"][0]))
+    out["max_rel_diff_linf"] = float(np.max(np.abs(errs[prec][1] - errs["fp64"][1]) / errs["fp64"][1]))
+    out["within_1pct"] = bool(max(out["max_rel_diff_l1"], out["max_rel_diff_linf"]) <= 0.01)
+    return out
 
 
 def end_to_end(torch, vklb, wl, prec, tile, steps, U0, form="distributions"):

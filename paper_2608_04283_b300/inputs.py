@@ -222,6 +222,34 @@ def request_initial_state(req, gamma_euler=1.4, gamma_mhd=5.0 / 3.0):
     return orszag_tang(req.n, gamma=gamma_mhd, phase=req.phase)
 
 
+def request_initial_state_torch(req, torch, device="cuda", gamma_euler=1.4, gamma_mhd=5.0 / 3.0):
+    """request_initial_state evaluated by torch in float64 on ``device``: the
+    server builds a request's analytic initial data (system, side, phases) where
+    the state will live instead of copying it from the host."""
+    n = req.n
+    L = 2.0 * math.pi if req.system == "mhd_glm" else 1.0
+    x = (torch.arange(n, dtype=torch.float64, device=device) + 0.5) * (L / n)
+    Y, X = torch.meshgrid(x, x, indexing="ij")          # [ny, nx], x fastest
+    two_pi = 2.0 * math.pi
+    if req.system == "swe":
+        h = 1.0 + 0.1 * torch.sin(two_pi * X + req.phase[0]) + 0.1 * torch.sin(two_pi * Y + req.phase[1])
+        z = torch.zeros_like(h)
+        return torch.stack([h, z, z]).contiguous()
+    if req.system == "euler":
+        g = gamma_euler
+        rho = 1.0 + 0.1 * torch.sin(two_pi * (X + Y) + req.phase[0])
+        E = 1.0 / (g - 1.0) + 0.5 * rho * 2.0
+        return torch.stack([rho, rho, rho, E]).contiguous()
+    g = gamma_mhd
+    Xs, Ys = X + req.phase[0], Y + req.phase[1]
+    rho = torch.full_like(X, g * g)
+    u, v = -torch.sin(Ys), torch.sin(Xs)
+    bx, by = -torch.sin(Ys), torch.sin(2.0 * Xs)
+    z = torch.zeros_like(X)
+    E = g / (g - 1.0) + 0.5 * rho * (u * u + v * v) + 0.5 * (bx * bx + by * by)
+    return torch.stack([rho, rho * u, rho * v, z, E, bx, by, z, z]).contiguous()
+
+
 def random_states(system, count, seed=0, dim=2, gamma=1.4, g=9.81):
     """Seeded random admissible states (positive depth / density / pressure),
     shape [p, count], for point-wise checks of fluxes and splittings."""

@@ -3,8 +3,9 @@
 Requests (system, grid side, step count, initial data) arrive over time.  The
 server admits them first-in first-out while their device memory fits under an
 HBM budget, keeps every simulation in the moment form (all families run at
-omega = 1, where U alone is the state: 2p instead of 10p values a cell), keeps every admitted simulation's distributions resident on the
-GPU, and advances all active simulations of one system family together with a
+omega = 1, where U alone is the state: 2p instead of 10p values a cell), keeps
+every admitted simulation's state resident on the GPU, and advances all active
+simulations of one system family together with a
 single batched launch per step (``vklb_batch_step``); the three families run on
 their own CUDA streams, so their work overlaps on the device.  A tick advances
 a family by K steps, K = min(tick_steps, fewest steps any member still needs);
@@ -81,7 +82,7 @@ class Server:
     pageable array."""
 
     def __init__(self, budget_bytes=120e9, tick_steps=50, precision="fp32", tiles=None, keep_results=False,
-                 clock=None, form="moments", max_side=2048):
+                 clock=None, form="moments", max_side=2048, device_ic=False):
         import torch
         self.torch = torch
         self.budget = float(budget_bytes)
@@ -90,6 +91,7 @@ class Server:
         self.tiles = tiles or {"swe": (64, 16), "euler": (64, 16), "mhd_glm": (128, 16)}
         self.keep = keep_results
         self.form = form
+        self.device_ic = device_ic
         self.streams = {k: torch.cuda.Stream() for k in FAMILY}
         self.clock = clock or time.perf_counter
         self.staging = {k: torch.empty(FIELDS[k] * max_side * max_side, dtype=torch.float64,
@@ -110,6 +112,12 @@ class Server:
         sim = vklb.Sim(req.system, (req.n, req.n), (0.0, 0.0), (side, side), precision=self.precision,
                        stream=self.streams[req.system], form=self.form, **kw)
         sim.set_tiling(*self.tiles[req.system])
+        if U0 is None and self.device_ic:
+            # the request's analytic initial data evaluated on the device, on the
+            # family's stream (the state's copy is ordered after it)
+            with self.torch.cuda.stream(self.streams[req.system]):
+                sim.set_state(inputs.request_initial_state_torch(req, self.torch))
+            return sim
         if U0 is None:
             U0 = inputs.request_initial_state(req)
         sim.set_state(np.ascontiguousarray(U0))
@@ -120,7 +128,8 @@ class Server:
         honoured against the wall clock from the start; otherwise everything is
         available at once.  ``payloads`` optionally maps a request id to its
         initial state U_0 (the data a client sends with the request); without
-        it the server generates U_0 itself.  Returns a Report.
+        it the server generates U_0 itself (on the device with ``device_ic``,
+        from the request's system, side and phases).  Returns a Report.
 
         Each family has at most one tick in flight on its stream, and a family
         is served as soon as its own tick completes (its finished requests read
@@ -223,11 +232,14 @@ def serve_alone(req, **kw):
     return rep.jobs[0].result
 
 
-def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=None, max_side=2048):
+def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=None, max_side=2048,
+              device_ic=False):
     """Baseline: the same requests one at a time, one launch per step each, the
     results read back through a pinned buffer as the server reads them.  Each
     simulation takes the library's default launch shape for its grid (128 wide,
-    height fitted to whole waves) unless ``tiles`` names one per system."""
+    height fitted to whole waves) unless ``tiles`` names one per system.  The
+    initial state comes from ``payloads``, or is built on the device
+    (``device_ic``) or on the host, as the server builds it."""
     import torch
     staging = torch.empty(max(FIELDS.values()) * max_side * max_side, dtype=torch.float64, pin_memory=True).numpy()
     t0 = time.perf_counter()
@@ -236,8 +248,12 @@ def run_plain(requests, precision="fp32", tiles=None, form="moments", payloads=N
         sim = vklb.Sim(r.system, (r.n, r.n), (0.0, 0.0), (side, side), precision=precision, form=form, **kw)
         if tiles:
             sim.set_tiling(*tiles[r.system])
-        U0 = inputs.request_initial_state(r) if payloads is None else payloads[r.rid]
-        sim.set_state(np.ascontiguousarray(U0))
+        if payloads is not None:
+            sim.set_state(np.ascontiguousarray(payloads[r.rid]))
+        elif device_ic:
+            sim.set_state(inputs.request_initial_state_torch(r, torch))
+        else:
+            sim.set_state(np.ascontiguousarray(inputs.request_initial_state(r)))
         sim.step(r.steps)
         size = int(np.prod(sim.shape))
         if size <= staging.size:
