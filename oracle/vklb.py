@@ -5,7 +5,7 @@ One step, in the flow chart's order:
   2. collision  f*_q = f_q - omega (f_q - f_q^eq(U^n))       (Eq. 42)
   3. streaming  f_q(x + v_q Delta t) = f*_q(x); periodic wrap (Eq. 43, Eq. 37)
   4. moments    U^{n+1} = sum_q f_q                          (Eq. 3)
-  5. characteristic boundary conditions (1D, non-periodic)   (Eqs. 33-36)
+  5. characteristic boundary conditions (non-periodic axes)  (Eqs. 33-36)
   6. CFL        xi = max_j |lambda_j| / nu over the grid      (Eq. 29)
   7. equilibria f^eq(U^{n+1}) for the next step              (Eqs. 22-24 / 41)
 Initialisation: xi from U(x,0), f_q(x,0) = f_q^eq(U(x,0)) (Eq. 2b, Fig. 5).
@@ -37,6 +37,16 @@ Readings of the paper taken here, where it is silent or ambiguous:
       towards the interior; incoming waves (lambda < 0 on the right, lambda > 0
       on the left) are dropped; Delta t = dx / xi_n.
   R11 boundary f = f^eq(U_b^{n+1}) uses xi_{n+1}.
+  R19 2D characteristic boundaries (the paper writes Eqs. 33-36 for D1Q3 only):
+      every node on a non-periodic face takes the 1D construction along the
+      face normal d, U_b^{n+1} = U_b^n - (1/xi_n) P_d Lambda_d^out P_d^-1 D_d U^n
+      with A_d = dF^(d)/dU frozen at the node, the one-sided difference D_d
+      towards the interior and the waves leaving through that face kept; a
+      corner node sums the terms of its two faces; tangential derivatives are
+      not added (the construction of Sec. 3.3 applied per face).  Its
+      distributions are f^eq(U_b^{n+1}) with xi_{n+1} (R11), and xi_{n+1}
+      includes the boundary states.  Streaming wraps as on a periodic grid;
+      what wraps lands only in boundary nodes, which are overwritten.
 
 Test infrastructure only.
 
@@ -78,12 +88,39 @@ def equilibrium_2d(U, Fp1, Fm1, Fp2, Fm2, xi, c):
     return np.stack([f1, f2, f3, f4, f5])
 
 
+def outgoing_part(A, v, side):
+    """P Lambda^out P^-1 v for a diagonalisable A with real eigenvalues, the
+    waves leaving through a low face (side 0: lambda < 0) or a high face
+    (side 1: lambda > 0), by Sylvester's formula over A's distinct eigenvalues
+    mu_k: sum over outgoing k of mu_k prod_{l != k} (A - mu_l I) / (mu_k - mu_l)
+    (the spectral projector of each eigenspace, basis-free, so a repeated
+    eigenvalue such as the 2D shear and entropy waves' u_n needs no basis)."""
+    lam = np.sort(np.real(np.linalg.eigvals(A)))
+    tol = 1e-8 * max(1.0, np.abs(lam).max())
+    mu = [lam[0]]
+    for x in lam[1:]:
+        if x - mu[-1] > tol:
+            mu.append(x)
+    out = np.zeros_like(v)
+    eye = np.eye(A.shape[0])
+    for k, mk in enumerate(mu):
+        if not ((mk < 0) if side == 0 else (mk > 0)):
+            continue
+        w = v.copy()
+        for l, ml in enumerate(mu):
+            if l != k:
+                w = (A - ml * eye) @ w / (mk - ml)
+        out += mk * w
+    return out
+
+
 class Sim:
     """One VKLB simulation on a uniform grid.
 
     system   : an ``oracle.systems`` object (its dim selects D1Q3 or D2Q5)
     n        : (nx,) or (nx, ny) cells;  lo, hi: domain corners
-    bc       : "periodic" or "characteristic" (1D only)
+    bc       : "periodic" or "characteristic" (all sides), or in 2D a pair
+               (x axis, y axis) of those
     set_kind : "weighted" (c, k), "centered" (c = 1/Q, F/2), "discontinuous"
     omega    : relaxation parameter, 0 < omega <= 2 (Sec. 2.3)
     nu       : CFL number (Eq. 29);  dt > 0 fixes xi = dx / dt instead
@@ -104,11 +141,11 @@ class Sim:
             raise ValueError("D2Q5 needs dx == dy (Sec. 3.4)")
         self.dx = float(dxs[0])
         self.lo, self.hi = lo, hi
-        if bc not in ("periodic", "characteristic"):
+        axes = (bc,) * self.dim if isinstance(bc, str) else tuple(bc)
+        if len(axes) != self.dim or any(b not in ("periodic", "characteristic") for b in axes):
             raise ValueError(bc)
-        if bc == "characteristic" and self.dim != 1:
-            raise ValueError("characteristic BC is defined in 1D (Sec. 3.3)")
-        self.bc = bc
+        self.bc_axes = axes
+        self.bc = bc if isinstance(bc, str) else ("characteristic" if "characteristic" in axes else "periodic")
         self.set_kind = set_kind
         if set_kind == "centered":
             c = 1.0 / 3.0 if self.dim == 1 else 1.0 / 5.0
@@ -216,6 +253,36 @@ class Sim:
             res.append(ub - rhs / xi_n)          # Delta t / dx = 1 / xi_n
         return res
 
+    def boundary_mask(self):
+        """2D: True at the nodes of the non-periodic faces ([ny, nx])."""
+        ny, nx = self.n[1], self.n[0]
+        m = np.zeros((ny, nx), dtype=bool)
+        if self.bc_axes[0] == "characteristic":
+            m[:, 0] = m[:, -1] = True
+        if self.bc_axes[1] == "characteristic":
+            m[0, :] = m[-1, :] = True
+        return m
+
+    def char_bc_2d(self, Uold, xi_n):
+        """R19: Eqs. (33)-(35) along the normal of every non-periodic face, from
+        U^n; a corner sums its two faces.  Returns U_b^{n+1} on the boundary
+        nodes as a full [p, ny, nx] array (other nodes: U^n, unused)."""
+        rhs = np.zeros_like(Uold)
+        for d, axis in ((0, 2), (1, 1)):
+            if self.bc_axes[d] != "characteristic":
+                continue
+            for side in (0, 1):
+                take = [slice(None)] * 3
+                inner = [slice(None)] * 3
+                take[axis] = 0 if side == 0 else -1
+                inner[axis] = 1 if side == 0 else -2
+                ub = Uold[tuple(take)]                          # [p, face length]
+                dU = (Uold[tuple(inner)] - ub) if side == 0 else (ub - Uold[tuple(inner)])
+                A = splitting.jacobian(self.sys, ub, d)           # [m, p, p]
+                for m in range(A.shape[0]):
+                    rhs[tuple(take)][:, m] += outgoing_part(A[m], dU[:, m], side)
+        return Uold - rhs / xi_n
+
     # ----- public API ---------------------------------------------------------
     def set_state(self, U0):
         U0 = np.array(U0, dtype=np.float64)
@@ -245,17 +312,23 @@ class Sim:
         fs = self.f - self.omega * (self.f - feq)             # Eq. (42)
         fn = self.stream(fs)                                  # Eq. (43)
         Un = fn.sum(axis=0)                                   # Eq. (3)
-        if self.bc == "characteristic":
+        if self.bc == "characteristic" and self.dim == 1:
             ubl, ubr = self.char_bc(U, Un, xi)                # Eqs. (33)-(35)
             Un[:, 0] = ubl
             Un[:, -1] = ubr
+        elif self.bc == "characteristic":
+            mask = self.boundary_mask()
+            Un[:, mask] = self.char_bc_2d(U, xi)[:, mask]     # R19
         self.refresh_ch(Un)
         xin = self.cfl_xi(Un)                                 # Eq. (29)
-        if self.bc == "characteristic":
+        if self.bc == "characteristic" and self.dim == 1:
             fb = self.equilibrium(np.stack([Un[:, 0], Un[:, -1]], axis=1), xin,
                                   self.max_lambda(Un))
             fn[:, :, 0] = fb[:, :, 0]                         # Eq. (36), R11
             fn[:, :, -1] = fb[:, :, 1]
+        elif self.bc == "characteristic":
+            fb = self.equilibrium(Un[:, mask], xin, self.max_lambda(Un))
+            fn[:, :, mask] = fb                               # Eq. (36), R11, R19
         self.f = fn
         self.t = self.t + self.dx / xi
         if t_end is not None and abs(self.t - t_end) <= 1e-13 * max(1.0, abs(t_end)):

@@ -38,3 +38,15 @@ def test_budget_is_respected(srv_mod):
     rep = server.run(trace, realtime=False)
     assert rep.summary()["completed"] == 6
     assert rep.peak_bytes <= 2 * per
+
+
+def test_device_initial_states_match_host(srv_mod):
+    """Initial states built on the device from the request (system, side,
+    phases) serve the same results as the host-built ones, to FP32 rounding
+    (the two evaluations of the analytic data differ by an ulp in a few cells)."""
+    trace = inputs.serving_trace(count=5, rate=1e6, seed=6, nmin=64, nmax=128, nstep=32, smin=10, smax=30)
+    a = srv_mod.Server(tick_steps=8, keep_results=True).run(trace, realtime=False)
+    b = srv_mod.Server(tick_steps=8, keep_results=True, device_ic=True).run(trace, realtime=False)
+    for ja, jb in zip(a.jobs, b.jobs):
+        scale = np.abs(ja.result).max()
+        assert np.abs(ja.result - jb.result).max() <= 1e-5 * scale, ja.req

@@ -1,0 +1,113 @@
+"""Pins for the 2D characteristic boundaries of the oracle (reading R19: the 1D
+construction of Sec. 3.3, Eqs. 33-36, applied along the normal of every
+non-periodic face, corners summing their two faces).  No GPU.
+
+* A uniform state is a fixed point (every one-sided difference vanishes).
+* The boundary state after one step equals U_b^n - (1/xi_n) P Lambda^out P^-1 D U^n
+  written out here with the closed-form shallow-water eigenvectors (r = (1, u -+ c,
+  v) and the shear wave (0, 0, 1) along x; x and y swapped along y), at face
+  nodes of all four faces and at a corner (both faces' terms).
+* A smooth 2D hump (the radial form of the Sec. 5.1 hump, Eq. 53) leaves the box
+  [-5, 5]^2 with small reflections: against a run on a periodic box three times
+  as wide (which the waves do not cross before T), the characteristic box is off
+  by under 1 % of the hump's amplitude and by under a fifth of what the periodic
+  box of the same size is off by.
+"""
+import numpy as np
+import pytest
+
+from oracle import systems, vklb
+from paper_2608_04283_b300 import inputs
+
+
+def _hump(n, L):
+    x = inputs.cell_centers(n, -L, L)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    r = np.sqrt(X * X + Y * Y)
+    h = np.where(r <= 1.0, 1.0 + 0.3 * ((1.0 + np.cos(np.pi * r)) / 2.0) ** 2, 1.0)
+    z = np.zeros_like(h)
+    return np.stack([h, z, z])
+
+
+@pytest.mark.parametrize("bc", ["characteristic", ("characteristic", "periodic"), ("periodic", "characteristic")])
+def test_uniform_state_is_fixed(bc):
+    s = systems.Euler(1.4, 2)
+    U = np.broadcast_to(inputs.euler_conserved(np.array(1.2), np.array(0.4), np.array(-0.3), np.array(0.9),
+                                               1.4)[:, None, None], (4, 12, 16)).copy()
+    sim = vklb.Sim(s, (16, 12), (0, 0), (4 / 3, 1), bc=bc, omega=1.0, nu=0.3)
+    sim.set_state(U)
+    sim.run(15)
+    assert np.abs(sim.moments() - U).max() < 1e-14
+
+
+def _swe_out_term(U, dU, d, side, g):
+    """P Lambda^out P^-1 dU for 2D shallow water along direction d, closed form;
+    side 0: waves with lambda < 0 leave (low face), side 1: lambda > 0."""
+    h = U[0]
+    un, ut = U[1 + d] / h, U[2 - d] / h
+    c = np.sqrt(g * h)
+    dh, dmn, dmt = dU[0], dU[1 + d], dU[2 - d]
+    w1 = ((un + c) * dh - dmn) / (2 * c)           # along r1 = (1, un - c, ut)
+    w3 = ((c - un) * dh + dmn) / (2 * c)           # along r3 = (1, un + c, ut)
+    w2 = dmt - ut * dh                             # along r2 = (0, 0, 1)
+    out = np.zeros(3)
+    for lam, w, r in ((un - c, w1, (1.0, un - c, ut)), (un, w2, (0.0, 0.0, 1.0)), (un + c, w3, (1.0, un + c, ut))):
+        if (lam < 0) if side == 0 else (lam > 0):
+            r = np.array(r)
+            o = np.zeros(3)
+            o[0], o[1 + d], o[2 - d] = r[0], r[1], r[2]
+            out += lam * w * o
+    return out
+
+
+def test_boundary_states_closed_form():
+    g = 9.81
+    s = systems.ShallowWater(g, 2)
+    nx, ny = 14, 10
+    x = inputs.cell_centers(nx, 0, 1.4)
+    y = inputs.cell_centers(ny, 0, 1.0)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    h = 1.0 + 0.2 * np.sin(2.1 * X + 0.3) * np.cos(1.7 * Y)
+    U = np.stack([h, h * (0.4 + 0.3 * np.cos(X + Y)), h * (-0.2 + 0.25 * np.sin(2 * X))])
+    sim = vklb.Sim(s, (nx, ny), (0, 0), (1.4, 1.0), bc="characteristic", omega=1.0, nu=0.3)
+    sim.set_state(U)
+    xi0 = sim.xi
+    sim.step()
+    Un = sim.moments()
+
+    def term(j, i, d, side):
+        ub = U[:, j, i]
+        if d == 0:
+            nb = U[:, j, i + 1] if side == 0 else U[:, j, i - 1]
+        else:
+            nb = U[:, j + 1, i] if side == 0 else U[:, j - 1, i]
+        dU = nb - ub if side == 0 else ub - nb
+        return _swe_out_term(ub, dU, d, side, g)
+
+    for (j, i, faces) in [(4, 0, [(0, 0)]), (6, nx - 1, [(0, 1)]), (0, 5, [(1, 0)]), (ny - 1, 9, [(1, 1)]),
+                          (0, 0, [(0, 0), (1, 0)]), (ny - 1, nx - 1, [(0, 1), (1, 1)])]:
+        want = U[:, j, i] - sum(term(j, i, d, side) for d, side in faces) / xi0
+        assert np.allclose(Un[:, j, i], want, rtol=1e-13, atol=1e-14), (j, i)
+    # the boundary distributions are the equilibria of those states with xi_{n+1}
+    fb = sim.equilibrium(Un[:, [0], [0]], sim.xi, sim.max_lambda(Un))
+    assert np.allclose(sim.f[:, :, 0, 0], fb[:, :, 0], rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.slow
+def test_smooth_hump_leaves_the_box():
+    s = systems.ShallowWater(1.0, 2)
+    n, T = 32, 8.0
+    runs = {}
+    for bc in ("characteristic", "periodic"):
+        sim = vklb.Sim(s, (n, n), (-5, -5), (5, 5), bc=bc, omega=1.0, nu=0.3)
+        sim.set_state(_hump(n, 5.0))
+        sim.run_to(T)
+        runs[bc] = sim.moments()
+    big = vklb.Sim(s, (3 * n, 3 * n), (-15, -15), (15, 15), bc="periodic", omega=1.0, nu=0.3)
+    big.set_state(_hump(3 * n, 15.0))
+    big.run_to(T)
+    ref = big.moments()[:, n:2 * n, n:2 * n]
+    refl = np.abs(runs["characteristic"][0] - ref[0]).max()
+    wrap = np.abs(runs["periodic"][0] - ref[0]).max()
+    assert refl < 0.01 * 0.3, refl          # measured 4.0e-4
+    assert refl < 0.2 * wrap, (refl, wrap)  # measured 0.086
