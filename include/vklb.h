@@ -89,7 +89,15 @@ typedef struct {
 } vklb_grid;
 
 /* Boundary kinds per side: periodic (Eq. 37) or characteristic /
- * non-reflecting (Eqs. 33-36, 1D only). */
+ * non-reflecting (Eqs. 33-36).  1D: both ends alike.  2D (D2Q5): per axis,
+ * lo[i] == hi[i]; a characteristic axis applies the 1D construction of
+ * Eqs. 33-35 along the normal of its two faces (the paper writes it for D1Q3
+ * only): a boundary node takes U_b^{n+1} = U_b^n - (1/xi_n) P Lambda^out P^-1 D U^n
+ * with the one-sided difference D towards the interior, a corner sums its two
+ * faces, and its distributions become f^eq(U_b^{n+1}) with xi_{n+1} (Eq. 36).
+ * 2D characteristic faces are built for shallow water, Euler and advection
+ * (VKLB_ERR_UNSUPPORTED for MHD-GLM), with the plain step kernel in the
+ * distribution form, outside batches; they need 3 or more cells across. */
 typedef enum { VKLB_BC_PERIODIC = 0, VKLB_BC_CHARACTERISTIC = 1 } vklb_bc_kind;
 typedef struct {
   int32_t lo[2];
@@ -160,7 +168,8 @@ typedef struct {
  * runs.  Parameter checks (returning VKLB_ERR_ARG): omega in (0, 2]
  * (Sec. 2.3); 0 < cfl <= 1 (Eq. 28); eta = 0 or 0 < eta < 1 (Sec. 2.3);
  * alpha_norm one of vklb_alpha_norm; dx == dy for D2Q5 (Sec. 3.4); lattice
- * matches grid->dim; characteristic boundaries only on D1Q3.  On success
+ * matches grid->dim; boundary kinds as above (VKLB_ERR_UNSUPPORTED for the
+ * combinations not built).  On success
  * *out owns two device distribution buffers of q * p * cells values each. */
 int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid,
                 const vklb_bc* bc, const vklb_weight* weight, double dt,

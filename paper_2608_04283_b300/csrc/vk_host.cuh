@@ -48,6 +48,9 @@ struct vklb_sim {
   double c, k, omega, cfl, fixed_xi;
   double inv_nu;   // xi = inv_nu max|lambda|: 1 / cfl, or sqrt(3/2) / eta
   int bc_lo, bc_hi;
+  int cbx, cby;            // 2D: characteristic faces normal to x / y (else periodic)
+  int nb;                  // 2D: boundary nodes of those faces (0: fully periodic)
+  void* ub;                // 2D: [p][nb] boundary states U_b^{n+1} between the two boundary passes
   cudaStream_t stream;
   void* f[2];
   int cur;                 // f[cur] holds the current state
@@ -129,6 +132,8 @@ StepArgs<T> make_args(const vklb_sim* s, double t_end) {
   a.anorm = s->anorm;
   a.bc_lo = s->bc_lo;
   a.bc_hi = s->bc_hi;
+  a.cbx = s->cbx;
+  a.cby = s->cby;
   a.ctl = s->ctl;
   a.slot = (int)(s->launched % 3);
   a.sp = s->sp;
@@ -219,6 +224,15 @@ struct Impl {
           launch_lb<0>(grid, TX, sm, s->stream, a, TY);
         else
           step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
+        if constexpr (!Sys::MHD) {
+          if (s->nb > 0) {
+            // the characteristic faces (same step arguments: parity and slot of step n)
+            const int bb = 128, gb = (s->nb + bb - 1) / bb;
+            char2d_state_kernel<Sys, T, R><<<gb, bb, 0, s->stream>>>(a, (R*)s->ub, s->nb);
+            char2d_feq_kernel<Sys, T, R><<<gb, bb, 0, s->stream>>>(a, (const R*)s->ub, s->nb);
+            g_launches += 2;
+          }
+        }
         s->cur ^= 1;
         s->launched += 1;
       }

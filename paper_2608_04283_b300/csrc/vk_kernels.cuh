@@ -64,6 +64,7 @@ struct StepArgs {
   int set;
   int anorm;       // alpha's normaliser: 0 per cell and direction, 1 grid-wide max |lambda| of the step
   int bc_lo, bc_hi;  // 1D: 0 periodic, 1 characteristic
+  int cbx, cby;      // 2D: characteristic boundaries on the x (y) faces, else periodic
   Ctl* ctl;
   int slot;        // n % 3
   SysParams sp;
@@ -302,6 +303,14 @@ __device__ __forceinline__ void cell_post(const Sys& sys, const T* __restrict__ 
   }
 }
 
+// A node on a characteristic (non-periodic) face: the step writes it from the
+// periodic pull, the boundary pass overwrites it, and the CFL maximum of the
+// step leaves it to that pass.
+template <class T>
+__device__ __forceinline__ bool on_char_face(const StepArgs<T>& a, int x, int y) {
+  return (a.cbx && (x == 0 || x == a.nx - 1)) || (a.cby && (y == 0 || y == a.ny - 1));
+}
+
 // ------------------------------------------------------------------ D2Q5 step
 // March over the rows of one tile, up or down.  Tiles of
 // even row index march up and odd ones down, so the two tiles that share a
@@ -442,10 +451,12 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
           U[i] = round_store(u, tp);
         }
       }
-      R e1, e2;
-      bad |= !sys.epilogue(U, e1, e2);
-      m1 = vmax(m1, e1);
-      m2 = vmax(m2, e2);
+      if (!on_char_face(a, x, j)) {
+        R e1, e2;
+        bad |= !sys.epilogue(U, e1, e2);
+        m1 = vmax(m1, e1);
+        m2 = vmax(m2, e2);
+      }
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
@@ -571,10 +582,12 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
             U[i] = round_store(u, tp);
           }
         }
-        R e1, e2;
-        bad |= !sys.epilogue(U, e1, e2);
-        m1 = vmax(m1, e1);
-        m2 = vmax(m2, e2);
+        if (!on_char_face(a, x, j)) {
+          R e1, e2;
+          bad |= !sys.epilogue(U, e1, e2);
+          m1 = vmax(m1, e1);
+          m2 = vmax(m2, e2);
+        }
       }
     }
     if (act) {
@@ -994,6 +1007,118 @@ __global__ void __launch_bounds__(128, MINB)
                            int TX, int TY, int D) {
   extern __shared__ __align__(128) unsigned char smem[];
   step2d_batch_body<Sys, T, R, VARIANT>(desc, work, step_off, TX, TY, D, smem);
+}
+
+// ------------------------------------------------ 2D characteristic faces
+// The construction of Eqs. (33)-(36) applied along the normal of every
+// characteristic face of a D2Q5 grid, after the step kernel: the boundary node
+// takes U_b^{n+1} = U_b^n - (1/xi_n) P Lambda^out P^-1 D U^n with the one-sided
+// difference D towards the interior (a corner sums its two faces), and
+// f^{n+1} = f^eq(U_b^{n+1}) with xi_{n+1}.  Boundary nodes are numbered: the
+// x faces' columns (2 ny nodes) first, then the y faces' rows without the
+// corners already counted.
+VK_HD int char_face_nodes(int nx, int ny, int cbx, int cby) {
+  return (cbx ? 2 * ny : 0) + (cby ? 2 * (nx - (cbx ? 2 : 0)) : 0);
+}
+VK_HD void char_face_node(int id, int nx, int ny, int cbx, int cby, int& x, int& y) {
+  if (cbx) {
+    if (id < 2 * ny) {
+      x = id < ny ? 0 : nx - 1;
+      y = id < ny ? id : id - ny;
+      return;
+    }
+    id -= 2 * ny;
+  }
+  const int w = nx - (cbx ? 2 : 0), x0 = cbx ? 1 : 0;
+  y = id < w ? 0 : ny - 1;
+  x = x0 + (id < w ? id : id - w);
+}
+
+template <class Sys, class T, class R>
+__device__ __forceinline__ void load_U(const T* __restrict__ f, int x, int y, int nxb, R (&U)[Sys::P]) {
+  constexpr int P = Sys::P;
+  const size_t b = brick_base(x, y, nxb, 5 * P);
+#pragma unroll
+  for (int i = 0; i < P; ++i) {
+    R acc = R(0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc += Store<T>::ld(f + b + (size_t)(q * P + i) * kBrick);
+    U[i] = acc;
+  }
+}
+
+// Pass 1: U_b^{n+1} of every boundary node from f^n into Ub ([p][nb]), and its
+// wave-speed maximum into the control slot of step n+1 (after the step kernel
+// has reduced the interior's).
+template <class Sys, class T, class R>
+__global__ void char2d_state_kernel(StepArgs<T> a, R* __restrict__ Ub, int nb) {
+  constexpr int P = Sys::P;
+  const StepScalars sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+  if (sc.done) return;   // the step was a no-op (t_end reached): nothing to replace
+  const Sys sys = make_sys<Sys>(a.sp);
+  const int nxb = a.pitch / kBrick, nx = a.nx, ny = a.ny;
+  const T* __restrict__ fin = a.src();
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  R m1 = R(0), m2 = R(0);
+  bool bad = false;
+  if (id < nb) {
+    int x, y;
+    char_face_node(id, nx, ny, a.cbx, a.cby, x, y);
+    R U[P], rhs[P];
+    load_U<Sys, T, R>(fin, x, y, nxb, U);
+#pragma unroll
+    for (int i = 0; i < P; ++i) rhs[i] = R(0);
+#pragma unroll 1
+    for (int d = 0; d < 2; ++d) {
+      const bool face = d == 0 ? (a.cbx && (x == 0 || x == nx - 1)) : (a.cby && (y == 0 || y == ny - 1));
+      if (!face) continue;
+      const int side = (d == 0 ? x : y) == 0 ? 0 : 1;
+      const int xn = d == 0 ? (side == 0 ? 1 : nx - 2) : x;
+      const int yn = d == 1 ? (side == 0 ? 1 : ny - 2) : y;
+      R Un[P], dU[P], t[P];
+      load_U<Sys, T, R>(fin, xn, yn, nxb, Un);
+#pragma unroll
+      for (int i = 0; i < P; ++i) dU[i] = side == 0 ? Un[i] - U[i] : U[i] - Un[i];
+      sys.char_rhs_d(U, dU, d, side, t);
+#pragma unroll
+      for (int i = 0; i < P; ++i) rhs[i] += t[i];
+    }
+    const R xinv = (R)sc.xinv;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      U[i] = U[i] - rhs[i] * xinv;
+      Ub[(size_t)i * nb + id] = U[i];
+    }
+    bad = !sys.epilogue(U, m1, m2);
+  }
+  commit_max<R>(m1, m2, bad, a.ctl, (a.slot + 1) % 3);
+}
+
+// Pass 2: f^{n+1} = f^eq(U_b^{n+1}) (Eq. 36) at the boundary nodes, with xi_{n+1}
+// (and alpha's grid-wide normaliser) from the completed slot of step n+1.
+template <class Sys, class T, class R>
+__global__ void char2d_feq_kernel(StepArgs<T> a, const R* __restrict__ Ub, int nb) {
+  constexpr int P = Sys::P;
+  const StepScalars sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
+  if (sc.done) return;
+  const StepScalars sn = step_scalars(a.ctl, (a.slot + 1) % 3, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi,
+                                      -1.0, a.dx);
+  Sys sys = make_sys<Sys>(a.sp);
+  if (a.anorm) sys.lg = (R)sn.lam;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= nb) return;
+  int x, y;
+  char_face_node(id, a.nx, a.ny, a.cbx, a.cby, x, y);
+  R U[P], e[5][P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) U[i] = Ub[(size_t)i * nb + id];
+  equilibria_d2q5<Sys, R, C_FULL>(sys, U, (R)sn.xinv, (R)a.c, a.set, (R)a.k, (R)sn.ch, e);
+  T* __restrict__ fout = a.dst();
+  const size_t b = brick_base(x, y, a.pitch / kBrick, 5 * P);
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int i = 0; i < P; ++i) Store<T>::st(fout + b + (size_t)(q * P + i) * kBrick, e[q][i]);
 }
 
 // ------------------------------------------------------------------ D1Q3 steps

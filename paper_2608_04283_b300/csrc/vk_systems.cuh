@@ -62,6 +62,12 @@ struct Advect {
     bool out_going = side == 0 ? l < R(0) : l > R(0);
     out[0] = out_going ? l * dU[0] : R(0);
   }
+  // The same along direction d of a 2D grid (a face normal to d).
+  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R* out) const {
+    R l = a[d];
+    bool out_going = side == 0 ? l < R(0) : l > R(0);
+    out[0] = out_going ? l * dU[0] : R(0);
+  }
 };
 
 // ------------------------------------------------------------- shallow water
@@ -163,6 +169,24 @@ struct SWE {
     R k2 = (side == 0 ? l2 < R(0) : l2 > R(0)) ? l2 * w2 : R(0);
     out[0] = k1 + k2;
     out[1] = k1 * l1 + k2 * l2;
+  }
+  // 2D, along direction d (normal momentum n = 1 + d, tangential t = 2 - d):
+  // r = (1, u_n - c, u_t), (0, 0, 1) (shear, lambda = u_n), (1, u_n + c, u_t);
+  // dual rows ((u_n + c), -1, 0)/(2c), (-u_t, 0, 1), ((c - u_n), 1, 0)/(2c).
+  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R* out) const {
+    const int in = 1 + d, it = 2 - d;
+    const R h = U[0], un = U[in] / h, ut = U[it] / h, c = vsqrt(g * h);
+    const R i2c = R(0.5) / c;
+    const R w1 = ((un + c) * dU[0] - dU[in]) * i2c;
+    const R w2 = dU[it] - ut * dU[0];
+    const R w3 = ((c - un) * dU[0] + dU[in]) * i2c;
+    const R l1 = un - c, l2 = un, l3 = un + c;
+    const R k1 = (side == 0 ? l1 < R(0) : l1 > R(0)) ? l1 * w1 : R(0);
+    const R k2 = (side == 0 ? l2 < R(0) : l2 > R(0)) ? l2 * w2 : R(0);
+    const R k3 = (side == 0 ? l3 < R(0) : l3 > R(0)) ? l3 * w3 : R(0);
+    out[0] = k1 + k3;
+    out[in] = k1 * l1 + k3 * l3;
+    out[it] = (k1 + k3) * ut + k2;
   }
 };
 
@@ -300,6 +324,36 @@ struct Euler {
     out[0] = k[0] + k[1] + k[2];
     out[1] = k[0] * (u - a) + k[1] * u + k[2] * (u + a);
     out[2] = k[0] * (H - u * a) + k[1] * R(0.5) * u * u + k[2] * (H + u * a);
+  }
+  // 2D, along direction d (normal n = 1 + d, tangential t = 2 - d), q^2 = u_n^2 + u_t^2:
+  // r = (1, u_n - a, u_t, H - u_n a), (1, u_n, u_t, q^2/2) (entropy),
+  // (0, 0, 1, u_t) (shear), (1, u_n + a, u_t, H + u_n a); with b1 = (gamma-1)/a^2,
+  // b2 = b1 q^2/2 the dual rows are
+  // ((b2 + u_n/a), -(b1 u_n + 1/a), -b1 u_t, b1)/2, (1 - b2, b1 u_n, b1 u_t, -b1),
+  // (-u_t, 0, 1, 0), ((b2 - u_n/a), -(b1 u_n - 1/a), -b1 u_t, b1)/2.
+  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R* out) const {
+    const int in = 1 + d, it = 2 - d;
+    const R rho = U[0], un = U[in] / rho, ut = U[it] / rho, E = U[3];
+    const R q2 = un * un + ut * ut;
+    const R p = (gamma - R(1)) * (E - R(0.5) * rho * q2);
+    const R a = vsqrt(gamma * p / rho), H = (E + p) / rho;
+    const R b1 = (gamma - R(1)) / (a * a), b2 = R(0.5) * q2 * b1, ia = R(1) / a;
+    const R dr = dU[0], dn = dU[in], dt = dU[it], de = dU[3];
+    R w[4];
+    w[0] = R(0.5) * ((b2 + un * ia) * dr - (b1 * un + ia) * dn - b1 * ut * dt + b1 * de);
+    w[1] = (R(1) - b2) * dr + b1 * un * dn + b1 * ut * dt - b1 * de;
+    w[2] = dt - ut * dr;
+    w[3] = R(0.5) * ((b2 - un * ia) * dr - (b1 * un - ia) * dn - b1 * ut * dt + b1 * de);
+    const R lam[4] = {un - a, un, un, un + a};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool og = side == 0 ? lam[j] < R(0) : lam[j] > R(0);
+      w[j] = og ? lam[j] * w[j] : R(0);
+    }
+    out[0] = w[0] + w[1] + w[3];
+    out[in] = w[0] * (un - a) + w[1] * un + w[3] * (un + a);
+    out[it] = (w[0] + w[1] + w[3]) * ut + w[2];
+    out[3] = w[0] * (H - un * a) + w[1] * R(0.5) * q2 + w[2] * ut + w[3] * (H + un * a);
   }
 };
 

@@ -56,6 +56,7 @@ void free_sim(vklb_sim* s) {
   free_on(s->part, s->stream);
   free_on(s->dvec, s->stream);
   free_on(s->stage, s->stream);
+  free_on(s->ub, s->stream);
   delete s;
 }
 
@@ -161,13 +162,21 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   }
   for (int i = 0; i < dim; ++i)
     if (bc->lo[i] != bc->hi[i] && dim == 2) return VKLB_ERR_ARG;
-  if (dim == 2 && (bc->lo[0] != VKLB_BC_PERIODIC || bc->lo[1] != VKLB_BC_PERIODIC)) return VKLB_ERR_UNSUPPORTED;
+  for (int i = 0; i < dim; ++i)
+    if (bc->lo[i] != VKLB_BC_PERIODIC && bc->lo[i] != VKLB_BC_CHARACTERISTIC) return VKLB_ERR_ARG;
+  // 2D characteristic faces: shallow water, Euler and advection (closed-form
+  // outgoing parts); at least 3 cells across a characteristic axis
+  const bool char2d = dim == 2 && (bc->lo[0] == VKLB_BC_CHARACTERISTIC || bc->lo[1] == VKLB_BC_CHARACTERISTIC);
+  if (char2d && sys->kind == VKLB_MHD_GLM) return VKLB_ERR_UNSUPPORTED;
   if (dim == 1 && ((bc->lo[0] != VKLB_BC_PERIODIC && bc->lo[0] != VKLB_BC_CHARACTERISTIC) ||
                    (bc->hi[0] != VKLB_BC_PERIODIC && bc->hi[0] != VKLB_BC_CHARACTERISTIC)))
     return VKLB_ERR_ARG;
   if (dim == 1 && (bc->lo[0] == VKLB_BC_PERIODIC) != (bc->hi[0] == VKLB_BC_PERIODIC)) return VKLB_ERR_ARG;
   const Ops* ops = pick_ops(sys->kind, dim, precision);
   if (!ops) return VKLB_ERR_UNSUPPORTED;
+  if (char2d && ((bc->lo[0] == VKLB_BC_CHARACTERISTIC && grid->n[0] < 3) ||
+                 (bc->lo[1] == VKLB_BC_CHARACTERISTIC && grid->n[1] < 3)))
+    return VKLB_ERR_ARG;
   if ((sys->kind == VKLB_EULER || sys->kind == VKLB_MHD_GLM) && !(sys->gamma > 1.0)) return VKLB_ERR_ARG;
   if (sys->kind == VKLB_SWE && !(sys->g > 0.0)) return VKLB_ERR_ARG;
   if (sys->kind == VKLB_MHD_GLM && !(sys->ch_factor > 0.0)) return VKLB_ERR_ARG;
@@ -206,6 +215,10 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->fixed_xi = dt > 0.0 ? dx / dt : 0.0;
   s->bc_lo = bc->lo[0];
   s->bc_hi = bc->hi[0];
+  s->cbx = dim == 2 && bc->lo[0] == VKLB_BC_CHARACTERISTIC;
+  s->cby = dim == 2 && bc->lo[1] == VKLB_BC_CHARACTERISTIC;
+  s->nb = dim == 2 ? char_face_nodes((int)nx, (int)ny, s->cbx, s->cby) : 0;
+  s->ub = nullptr;
   s->stream = (cudaStream_t)cuda_stream;
   s->tile_x = 64;
   s->tile_y = 16;
@@ -222,7 +235,8 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
       (e = cudaMallocAsync((void**)&s->ctl, sizeof(Ctl), st)) != cudaSuccess ||
       (e = cudaMallocAsync((void**)&s->part, sizeof(double) * s->P * kRedBlocks, st)) != cudaSuccess ||
       (e = cudaMallocAsync((void**)&s->dvec, sizeof(double) * s->P, st)) != cudaSuccess ||
-      (e = cudaMallocAsync((void**)&s->stage, sizeof(double) * s->P * (size_t)s->cells, st)) != cudaSuccess) {
+      (e = cudaMallocAsync((void**)&s->stage, sizeof(double) * s->P * (size_t)s->cells, st)) != cudaSuccess ||
+      (s->nb > 0 && (e = cudaMallocAsync(&s->ub, sizeof(double) * s->P * (size_t)s->nb, st)) != cudaSuccess)) {
     free_sim(s);
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? VKLB_ERR_NOMEM : VKLB_ERR_CUDA;
@@ -291,6 +305,7 @@ int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
   if (stages == 0) stages = 4;
   if (stages < 2 || stages > 8) return VKLB_ERR_ARG;
   if (s->dim != 2 && variant != 0) return VKLB_ERR_UNSUPPORTED;
+  if (s->nb > 0 && variant != 0) return VKLB_ERR_UNSUPPORTED;   // characteristic faces: plain step only
   if (s->form == 1 && variant != 0) return VKLB_ERR_UNSUPPORTED;
   if (s->ops->smem(variant, s->P, s->tile_x, s->tile_y, stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->variant = variant;
@@ -302,6 +317,7 @@ int vklb_set_form(vklb_sim* s, int32_t form) {
   if (!s || (form != 0 && form != 1)) return VKLB_ERR_ARG;
   if (form == s->form) return VKLB_OK;
   if (form == 1 && s->dim != 2) return VKLB_ERR_UNSUPPORTED;
+  if (form == 1 && s->nb > 0) return VKLB_ERR_UNSUPPORTED;
   if (form == 1 && s->omega != 1.0) return VKLB_ERR_ARG;   // f* = f^eq(U) holds at omega = 1 only
   if (form == 1 && s->variant != 0) return VKLB_ERR_UNSUPPORTED;
   int st = cuda_status(cudaStreamSynchronize(s->stream));
@@ -429,7 +445,7 @@ int vklb_info(const vklb_sim* s, vklb_info_t* info) {
   info->dx = s->dx;
   info->tile_x = s->tile_x;
   info->tile_y = s->tile_y;
-  info->kernels_per_step = 1;
+  info->kernels_per_step = s->nb > 0 ? 3 : 1;
   info->variant = s->variant;
   info->blocks_per_sm = s->dim == 2 ? s->ops->occupancy(kernel_variant(s), s->tile_x, s->tile_y, s->stages) : 0;
   info->form = s->form;
@@ -530,6 +546,7 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
   for (int i = 0; i < n; ++i) {
     const vklb_sim* s = sims[i];
     if (!s || !s->ready) return VKLB_ERR_STATE;
+    if (s->nb > 0) return VKLB_ERR_UNSUPPORTED;   // characteristic faces: single-simulation steps only
     if (s->ops != s0->ops || s->set != s0->set || s->variant != s0->variant || s->stages != s0->stages ||
         s->form != s0->form)
       return VKLB_ERR_ARG;

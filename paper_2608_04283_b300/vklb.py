@@ -128,7 +128,9 @@ def _stream_handle(stream):
 
 class Sim:
     """One simulation (see vklb_create).  ``system`` in advection / swe / euler /
-    mhd_glm; ``n`` = (nx,) or (nx, ny); ``lo``/``hi`` domain corners; ``form``
+    mhd_glm; ``n`` = (nx,) or (nx, ny); ``lo``/``hi`` domain corners; ``bc``
+    "periodic" or "characteristic", or per axis in 2D, e.g. ("characteristic",
+    "periodic") (vklb_bc); ``form``
     "moments" keeps U instead of f as the state (D2Q5, omega = 1; vklb_set_form);
     ``eta`` > 0 takes the subcharacteristic lattice speed of the centered set
     instead of the CFL rule (vklb_weight.eta); ``alpha_norm`` "global" (default) or
@@ -146,8 +148,9 @@ class Sim:
         grid = Grid(dim, (C.c_int64 * 2)(n[0], n[1] if dim == 2 else 1),
                     (C.c_double * 2)(lo[0], lo[1] if dim == 2 else 0.0),
                     (C.c_double * 2)(hi[0], hi[1] if dim == 2 else 1.0))
-        kind = BC_PERIODIC if bc == "periodic" else BC_CHARACTERISTIC
-        b = BC((C.c_int32 * 2)(kind, kind), (C.c_int32 * 2)(kind, kind))
+        axes = (bc,) * 2 if isinstance(bc, str) else tuple(bc) + (bc[-1],) * (2 - len(bc))
+        kinds = [BC_PERIODIC if b_ == "periodic" else BC_CHARACTERISTIC for b_ in axes]
+        b = BC((C.c_int32 * 2)(*kinds), (C.c_int32 * 2)(*kinds))
         w = Weight(SET_KIND[set_kind], float(c), float(k), float(omega), float(cfl), float(eta),
                    ALPHA_NORM[alpha_norm])
         self._h = _P()

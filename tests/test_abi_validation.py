@@ -32,7 +32,7 @@ def _status(vk, fn):
     (dict(k=-1.0), "ERR_ARG"),
     (dict(n=(32, 16), hi=(1.0, 1.0)), "ERR_ARG"),            # dx != dy
     (dict(hi=(0.0, 1.0)), "ERR_ARG"),                          # empty domain
-    (dict(bc="characteristic"), "ERR_UNSUPPORTED"),           # characteristic boundaries are 1D (Sec. 3.3)
+    (dict(bc="characteristic", n=(2, 2)), "ERR_ARG"),          # a characteristic axis needs 3 cells
     (dict(gamma=1.0), "ERR_ARG"),                              # ideal gas needs gamma > 1
 ])
 def test_create_rejects(vk, kw, status):
@@ -46,6 +46,9 @@ def test_create_rejects_system_parameters(vk):
     assert _status(vk, lambda: vk.Sim("swe", (32, 32), (0, 0), (1, 1), g=0.0)) == vk.ERR_ARG
     assert _status(vk, lambda: vk.Sim("mhd_glm", (32, 32), (0, 0), (1, 1), ch_factor=0.0)) == vk.ERR_ARG
     assert _status(vk, lambda: vk.Sim("mhd_glm", (32,), (0.0,), (1.0,))) == vk.ERR_UNSUPPORTED   # MHD-GLM is 2D
+    # 2D characteristic faces are built for shallow water, Euler and advection
+    assert _status(vk, lambda: vk.Sim("mhd_glm", (32, 32), (0, 0), (1, 1), bc="characteristic")) == \
+        vk.ERR_UNSUPPORTED
 
 
 def test_null_handles(vk):

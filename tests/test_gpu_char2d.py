@@ -1,0 +1,135 @@
+"""2D characteristic faces (reading R19: the 1D construction of Eqs. 33-36 along
+each non-periodic face's normal, corners summing both faces) on the GPU
+against the FP64 oracle: <= 1e-11 max relative per field in FP64, <= 1e-5
+relative L1 in FP32, on ragged grids with all four faces characteristic or one
+axis periodic, several tilings; a uniform state is a fixed point; the smooth
+hump leaves the box with reflections under 1 % of its amplitude at a size the
+oracle cannot reach; and the combinations not built are refused."""
+import numpy as np
+import pytest
+
+from oracle import systems, vklb as ovklb
+from paper_2608_04283_b300 import inputs
+from parity_util import max_rel, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vk():
+    from paper_2608_04283_b300 import build
+    build.build()
+    from paper_2608_04283_b300 import vklb
+    return vklb
+
+
+def _hump(nx, ny, L):
+    dx = 2 * L / nx
+    x = -L + (np.arange(nx) + 0.5) * dx
+    y = -L + (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    r = np.sqrt((X - 0.8) ** 2 + (Y + 0.4) ** 2)
+    h = np.where(r <= 1.0, 1.0 + 0.3 * ((1.0 + np.cos(np.pi * r)) / 2.0) ** 2, 1.0)
+    return np.stack([h, 0.2 * h, -0.1 * h])
+
+
+@pytest.mark.parametrize("bc", ["characteristic", ("characteristic", "periodic"), ("periodic", "characteristic")])
+@pytest.mark.parametrize("tile", [(32, 8), (64, 5), None])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_swe_hump_against_oracle(vk, bc, tile, precision):
+    nx, ny = 44, 36
+    L = 3.0
+    U0 = _hump(nx, ny, L)
+    lo, hi = (-L, -L), (L, -L + ny * 2 * L / nx)
+    sim = vk.Sim("swe", (nx, ny), lo, hi, precision=precision, g=1.0, omega=1.0, cfl=0.3, bc=bc)
+    if tile:
+        sim.set_tiling(*tile)
+    sim.set_state(U0)
+    sim.step(40)
+    ref = ovklb.Sim(systems.ShallowWater(1.0, 2), (nx, ny), lo, hi, bc=bc, omega=1.0, nu=0.3)
+    ref.set_state(U0)
+    ref.run(40)
+    got, want = sim.moments(), ref.moments()
+    err = max_rel(got, want) if precision == "fp64" else rel_l1(got, want)
+    assert err.max() <= (1e-11 if precision == "fp64" else 1e-5), err
+    t, steps, xi = sim.time()
+    assert steps == 40
+    if precision == "fp64":
+        assert abs(xi - ref.xi) <= 1e-11 * ref.xi and abs(t - ref.t) <= 1e-12 * ref.t
+    sim.close()
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.6])
+def test_euler_vortex_open_x(vk, omega):
+    """Euler, x faces characteristic, y periodic; the vortex placed off-centre so
+    that its flow crosses the x faces; omega = 1.6 (relaxation, not f = f^eq)."""
+    nx, ny = 40, 48
+    U0 = np.ascontiguousarray(inputs.isentropic_vortex(48, center=(3.5, 5.0))[:, :, :40])
+    lo, hi = (0.0, 0.0), (10.0 * 40 / 48, 10.0)
+    sim = vk.Sim("euler", (nx, ny), lo, hi, precision="fp64", omega=omega, cfl=0.3,
+                 bc=("characteristic", "periodic"))
+    sim.set_state(U0)
+    sim.step_to(0.4)
+    ref = ovklb.Sim(systems.Euler(1.4, 2), (nx, ny), lo, hi, bc=("characteristic", "periodic"), omega=omega, nu=0.3)
+    ref.set_state(U0)
+    ref.run_to(0.4)
+    assert max_rel(sim.moments(), ref.moments()).max() <= 1e-11
+    assert sim.time()[1] == ref.steps
+    sim.close()
+
+
+def test_uniform_state_fixed(vk):
+    U = np.broadcast_to(inputs.euler_conserved(np.array(1.1), np.array(0.5), np.array(-0.3), np.array(0.8),
+                                               1.4)[:, None, None], (4, 40, 72)).copy()
+    sim = vk.Sim("euler", (72, 40), (0, 0), (1.8, 1.0), precision="fp64", omega=1.0, cfl=0.3,
+                 bc="characteristic")
+    sim.set_state(U)
+    sim.step(50)
+    assert np.abs(sim.moments() - U).max() <= 1e-13
+    sim.close()
+
+
+def test_hump_leaves_the_box(vk):
+    """The radial Sec. 5.1 hump (Eq. 53) at N = 256 in [-5, 5]^2 to T = 8 against a
+    periodic box three times as wide (which the waves do not cross before T):
+    the characteristic box is off by under 1 % of the hump's amplitude, and by
+    under a fifth of a periodic box of its own size."""
+    def hump(n, L):
+        x = inputs.cell_centers(n, -L, L)
+        X, Y = np.meshgrid(x, x, indexing="xy")
+        r = np.sqrt(X * X + Y * Y)
+        h = np.where(r <= 1.0, 1.0 + 0.3 * ((1.0 + np.cos(np.pi * r)) / 2.0) ** 2, 1.0)
+        z = np.zeros_like(h)
+        return np.stack([h, z, z])
+    n, T = 256, 8.0
+    out = {}
+    for bc in ("characteristic", "periodic"):
+        s = vk.Sim("swe", (n, n), (-5, -5), (5, 5), precision="fp64", g=1.0, omega=1.0, cfl=0.3, bc=bc)
+        s.set_state(hump(n, 5.0))
+        s.step_to(T)
+        out[bc] = s.moments()
+        s.close()
+    big = vk.Sim("swe", (3 * n, 3 * n), (-15, -15), (15, 15), precision="fp64", g=1.0, omega=1.0, cfl=0.3)
+    big.set_state(hump(3 * n, 15.0))
+    big.step_to(T)
+    ref = big.moments()[:, n:2 * n, n:2 * n]
+    big.close()
+    refl = np.abs(out["characteristic"][0] - ref[0]).max()
+    wrap = np.abs(out["periodic"][0] - ref[0]).max()
+    assert refl < 0.01 * 0.3 and refl < 0.2 * wrap, (refl, wrap)
+
+
+def test_refused_combinations(vk):
+    s = vk.Sim("swe", (64, 64), (0, 0), (1, 1), bc="characteristic")
+    with pytest.raises(vk.VKLBError) as e:
+        s.set_variant(1, 4)
+    assert e.value.status == vk.ERR_UNSUPPORTED
+    with pytest.raises(vk.VKLBError) as e:
+        s.set_form("moments")
+    assert e.value.status == vk.ERR_UNSUPPORTED
+    s.set_state(inputs.swe_sine_2d(64))
+    with pytest.raises(vk.VKLBError) as e:
+        vk.Batch([s])
+    assert e.value.status == vk.ERR_UNSUPPORTED
+    assert s.info.kernels_per_step == 3
+    s.close()

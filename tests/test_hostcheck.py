@@ -173,3 +173,27 @@ def test_split2_and_epilogue_match_oracle(name, kw, prec, tol, set_kind):
         lam = np.maximum(s.max_speed(U, 0), s.max_speed(U, 1))
     assert np.allclose(m1, lam, rtol=10 * tol)
     assert np.all(ok == 1)
+
+
+@pytest.mark.parametrize("name,kw", [("swe", {"g": 9.81}), ("euler", {"gamma": 1.4}), ("advection", {})])
+@pytest.mark.parametrize("d,side", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_char_rhs_2d_matches_oracle(name, kw, d, side):
+    """The 2D characteristic boundary's outgoing part along either face normal
+    (closed-form eigenvectors, vk_systems.cuh) against the oracle's basis-free
+    spectral projection (Sylvester's formula over the complex-step Jacobian)."""
+    from oracle import vklb as ovklb
+    s = systems.make(name, 2, a=(0.7, -0.4), **kw)
+    U = np.ascontiguousarray(inputs.random_states(name, 150, seed=37 + 2 * d + side, dim=2,
+                                                  gamma=kw.get("gamma", 1.4)))
+    rng = np.random.default_rng(5)
+    dU = np.ascontiguousarray(0.1 * rng.standard_normal(U.shape))
+    out = np.zeros_like(U)
+    st = _lib.vklb_hc_char_rhs2d(KIND[name], 0, d, side, C.c_double(kw.get("gamma", 1.4)),
+                                 C.c_double(kw.get("g", 9.81)), C.c_double(0.7), C.c_double(-0.4),
+                                 U.ctypes.data_as(_PD), dU.ctypes.data_as(_PD), C.c_int64(U.shape[1]),
+                                 out.ctypes.data_as(_PD))
+    assert st == 0
+    A = splitting.jacobian(s, U, d)
+    for i in range(U.shape[1]):
+        want = ovklb.outgoing_part(A[i], dU[:, i], side)
+        assert np.allclose(out[:, i], want, rtol=1e-10, atol=1e-12), i
