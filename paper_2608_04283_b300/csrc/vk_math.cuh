@@ -40,6 +40,12 @@ VK_HD float vexp(float x) {
 #endif
 }
 VK_HD double vexp(double x) { return exp(x); }
+// a * b + c in one rounding
+VK_HD float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+VK_HD double vfma(double a, double b, double c) { return fma(a, b, c); }
+// 1 where a >= 0, else 0 (the discontinuous set's Heaviside weight)
+VK_HD float vstep(float a) { return a >= 0.0f ? 1.0f : 0.0f; }
+VK_HD double vstep(double a) { return a >= 0.0 ? 1.0 : 0.0; }
 
 // a / b
 VK_HD float vdiv(float a, float b) {
@@ -89,7 +95,7 @@ VK_HD unsigned long long double_to_bits(double d) {
 template <class R>
 VK_HD R alpha_w(R lam, R k_over_lmax, int set) {
   if (set == SET_WEIGHTED) return vrcp(R(1) + vexp(-k_over_lmax * lam));
-  if (set == SET_DISCONTINUOUS) return lam >= R(0) ? R(1) : R(0);
+  if (set == SET_DISCONTINUOUS) return vstep(lam);
   return R(0.5);
 }
 
