@@ -258,6 +258,13 @@ int vklb_info(const vklb_sim* sim, vklb_info_t* info);
  * Borrowed; valid until the next vklb_step. */
 int vklb_device_state(const vklb_sim* sim, void** f_dev);
 
+/* Checking aid (no counterpart in the paper): fill the buffer that the next
+ * step writes with all-ones bytes (NaN in every precision), enqueued on the
+ * simulation's stream.  After that step every cell of the grid must hold a
+ * finite state again: a cell the step failed to write stays NaN and shows in
+ * vklb_moments.  Cells of the row padding (x >= nx) are never written or read. */
+int vklb_poison_next(vklb_sim* sim);
+
 /* Checkpoint / resume: the blob holds the device state (distributions, or U in
  * the moment form) and the control words (t, steps, xi, c_h).  A blob loads
  * only into a simulation of the same system, grid, precision and form.

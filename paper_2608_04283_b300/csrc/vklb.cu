@@ -468,6 +468,12 @@ int vklb_device_state(const vklb_sim* s, void** f_dev) {
   return VKLB_OK;
 }
 
+int vklb_poison_next(vklb_sim* s) {
+  if (!s) return VKLB_ERR_ARG;
+  const size_t bytes = (size_t)s->QS * s->P * s->pitch * s->ny * s->store_bytes;
+  return cuda_status(cudaMemsetAsync(s->f[s->cur ^ 1], 0xFF, bytes, s->stream));
+}
+
 int vklb_state_bytes(const vklb_sim* s, size_t* bytes) {
   if (!s || !bytes) return VKLB_ERR_ARG;
   *bytes = sizeof(BlobHeader) + sizeof(Ctl) + (size_t)s->QS * s->P * s->pitch * s->ny * s->store_bytes;

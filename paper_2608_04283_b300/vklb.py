@@ -76,6 +76,7 @@ _SIGS = {
     "vklb_time": (C.c_int, [_P, _D, C.POINTER(C.c_int64), _D]),
     "vklb_info": (C.c_int, [_P, C.POINTER(Info)]),
     "vklb_device_state": (C.c_int, [_P, C.POINTER(_P)]),
+    "vklb_poison_next": (C.c_int, [_P]),
     "vklb_state_bytes": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
     "vklb_get_state": (C.c_int, [_P, _P, C.c_size_t]),
     "vklb_put_state": (C.c_int, [_P, _P, C.c_size_t]),
@@ -243,6 +244,10 @@ class Sim:
         xi = C.c_double()
         _check(_lib.vklb_time(self._h, C.byref(t), C.byref(n), C.byref(xi)), "vklb_time")
         return t.value, n.value, xi.value
+
+    def poison_next(self):
+        """Fill the buffer the next step writes with NaN (vklb_poison_next)."""
+        _check(_lib.vklb_poison_next(self._h), "vklb_poison_next")
 
     def device_state(self):
         p = _P()

@@ -356,3 +356,43 @@ def test_fixed_dt_cfl_violation_is_reported(vk):
     with pytest.raises(vk.VKLBError) as e:
         sim.sync()
     assert e.value.status == vk.ERR_CFL
+
+
+@pytest.mark.parametrize("system,variant,tile,bc", [("euler", (0, 0), (32, 8), "periodic"),
+                                                    ("euler", (1, 4), (64, 5), "periodic"),
+                                                    ("euler", (2, 0), (64, 7), "periodic"),
+                                                    ("swe", (0, 0), (32, 6), "characteristic"),
+                                                    ("mhd_glm", (0, 0), (64, 8), "periodic")])
+def test_every_cell_written_each_step(vk, system, variant, tile, bc):
+    """Before every step the destination buffer is filled with NaN
+    (vklb_poison_next); after it the whole grid is finite and equals the oracle:
+    the step writes every cell (ragged tiles, each kernel variant, the
+    characteristic faces' boundary passes)."""
+    n = (45, 38)
+    if system == "euler":
+        U0 = _vortex(*n)
+        lo, hi = _box(n, 10.0)
+        kw, sysm = dict(omega=2.0, cfl=0.3), systems.Euler(1.4, 2)
+    elif system == "swe":
+        U0 = np.ascontiguousarray(inputs.swe_hump_2d(45, 0.4, 0.5, 0.45, 0.08)[:, :38, :])
+        lo, hi = _box(n, 1.0)
+        kw, sysm = dict(omega=1.0, cfl=0.3), systems.ShallowWater(9.81, 2)
+    else:
+        U0 = np.ascontiguousarray(inputs.orszag_tang(45)[:, :38, :])
+        lo, hi = _box(n, 2 * np.pi)
+        kw, sysm = dict(omega=1.0, cfl=0.3, gamma=5 / 3), systems.MHDGLM(5 / 3)
+    sim = vk.Sim(system, n, lo, hi, precision="fp32" if variant[0] == 2 else "fp64", bc=bc, **kw)
+    sim.set_tiling(64, 8)              # a shape every variant accepts
+    sim.set_variant(*variant)
+    sim.set_tiling(*tile)
+    sim.set_state(U0)
+    for _ in range(6):
+        sim.poison_next()
+        sim.step(1)
+        assert np.all(np.isfinite(sim.moments()))
+    ref = ovklb.Sim(sysm, n, lo, hi, bc=bc, omega=kw["omega"], nu=0.3)
+    ref.set_state(U0)
+    ref.run(6)
+    err = max_rel(sim.moments(), ref.moments()) if variant[0] != 2 else rel_l1(sim.moments(), ref.moments())
+    assert err.max() <= (1e-11 if variant[0] != 2 else 1e-5), err
+    sim.close()
