@@ -109,14 +109,8 @@ const Ops* vk_ops_mhd(int dim, int prec);
 namespace {
 
 // Kernel selector: 0 plain distribution step, 1 bulk-copy distribution step,
-// 2 moment-form step, 3 paired distribution step (API variant 2), 4 plain step
-// with the rows copied ahead (API variant 3).
-int kernel_variant(const vklb_sim* s) {
-  if (s->form == 1) return 2;
-  if (s->variant == 2) return 3;
-  if (s->variant == 3) return 4;
-  return s->variant;
-}
+// 2 moment-form step, 3 paired distribution step (API variant 2).
+int kernel_variant(const vklb_sim* s) { return s->form == 1 ? 2 : (s->variant == 2 ? 3 : s->variant); }
 
 template <class T>
 StepArgs<T> make_args(const vklb_sim* s, double t_end) {
@@ -184,19 +178,7 @@ struct Impl {
   static size_t smem_bytes_v(int variant, int tx, int ty, int d) {
     if (variant == 1) return TmaLayout<T>::template make<R, P>(tx, ty, d).bytes;
     if (variant == 3) return (size_t)(6 * P * (tx / 2) + 2 * P * ty) * sizeof(float);
-    if (variant == 4) return pf_offset<T, R>(P, tx, ty) + (size_t)2 * 5 * P * tx * sizeof(T);
     return smem_bytes(tx, ty);
-  }
-  // the prefetching march exists for 4- and 8-byte storage of the short systems
-  static constexpr bool kPrefetch = DIM == 2 && P <= 4 && (sizeof(T) == 4 || sizeof(T) == 8);
-  static void launch_pf(dim3 grid, int TX, size_t sm, cudaStream_t st, const StepArgs<T>& a, int TY) {
-    if constexpr (kPrefetch) step2d_pf_kernel<Sys, T, R><<<grid, TX, sm, st>>>(a, TX, TY);
-  }
-  static cudaError_t occupancy_pf(int* nb, int tx, size_t sm) {
-    if constexpr (kPrefetch)
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_pf_kernel<Sys, T, R>, tx, sm);
-    else
-      return cudaErrorInvalidValue;
   }
   // the paired march exists for FP32 distributions of the systems PairOf names
   static constexpr bool kPaired =
@@ -244,8 +226,6 @@ struct Impl {
           step2d_tma_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY, D);
         else if (kv == 3)
           launch_pair(grid, TX, sm, s->stream, a, TY);
-        else if (kv == 4)
-          launch_pf(grid, TX, sm, s->stream, a, TY);
         else if (kv == 2 && bounded(TX))
           launch_lb<1>(grid, TX, sm, s->stream, a, TY);
         else if (kv == 2)
@@ -291,8 +271,6 @@ struct Impl {
       cudaFuncSetAttribute(step2d_u_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if constexpr (kPaired)
         cudaFuncSetAttribute(step2d_pair_kernel<Sys>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if constexpr (kPrefetch)
-        cudaFuncSetAttribute(step2d_pf_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if constexpr (kBounded) {
         cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
@@ -329,8 +307,6 @@ struct Impl {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_tma_kernel<Sys, T, R>, tx, sm);
       else if (variant == 3)
         e = occupancy_pair(&nb, tx, sm);
-      else if (variant == 4)
-        e = occupancy_pf(&nb, tx, sm);
       else if (variant == 2 && bounded(tx))
         e = occupancy_lb<1>(&nb, tx, sm);
       else if (variant == 2)

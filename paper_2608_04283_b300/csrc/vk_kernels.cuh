@@ -312,45 +312,6 @@ __device__ __forceinline__ bool on_char_face(const StepArgs<T>& a, int x, int y)
   return (a.cbx && (x == 0 || x == a.nx - 1)) || (a.cby && (y == 0 || y == a.ny - 1));
 }
 
-// Shared-memory address of a generic pointer into shared memory.
-__device__ __forceinline__ uint32_t smem_u32_of(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// Byte offset of the prefetching march's row stages in its dynamic shared
-// memory: after the row exchange buffers and the x ring (R values), aligned to
-// 16 bytes.
-template <class T, class R>
-VK_HD size_t pf_offset(int P, int TX, int TY) {
-  return (((size_t)(6 * P * TX + 2 * P * TY) * sizeof(R)) + 15) & ~(size_t)15;
-}
-
-// Post-collision components of a cell whose stored values sit at p, p + stride,
-// ... (a row staged in shared memory by the prefetching march).
-template <class Sys, class T, class R, int MODE, int FORM>
-__device__ __forceinline__ void cell_post_at(const Sys& sys, const T* p, size_t stride, R xinv, R c, R om, int set,
-                                             R k, R ch, R (&o)[5][Sys::P]) {
-  constexpr int P = Sys::P;
-  if constexpr (FORM == 0) {
-    collide_d2q5<Sys, T, R, MODE>(sys, p, stride, 0, xinv, c, om, set, k, ch, o);
-  } else {
-    R U[P];
-#pragma unroll
-    for (int i = 0; i < P; ++i) U[i] = Store<T>::ld(p + (size_t)i * stride);
-    equilibria_d2q5<Sys, R, MODE>(sys, U, xinv, c, set, k, ch, o);
-  }
-}
-
-// Asynchronous copies global -> shared of one thread's own values (cp.async,
-// 4 or 8 bytes each), grouped per row; wait_group<N> returns once at most N of
-// this thread's groups are still in flight.
-template <class T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
-  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async copies 4, 8 or 16 bytes");
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32_of(dst)), "l"(src), "n"(sizeof(T))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // ------------------------------------------------------------------ D2Q5 step
 // March over the rows of one tile, up or down.  Tiles of
 // even row index march up and odd ones down, so the two tiles that share a
@@ -360,11 +321,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // down the two roles swap.
 // DIR = +1 / -1 fixes the direction at compile time (two bodies; the small
 // systems, whose code fits the instruction cache either way).
-// PF: each thread copies its column's values of the row after next into shared
-// memory asynchronously (cp.async, two row stages) while it works on the
-// current ones, so that a row's loads are in flight during the previous row's
-// arithmetic; the rows are then read from shared memory.
-template <class Sys, class T, class R, int DIR, int FORM, bool PF = false>
+template <class Sys, class T, class R, int DIR, int FORM>
 __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const BlockConsts<Sys, R>& bc, int bx,
                                                 int by, int TX, int TY, unsigned char* smem) {
   constexpr int P = Sys::P;
@@ -390,32 +347,6 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   R* ringL = rb2 + 3 * P * TX;           // [P][TY]     f*_1 at x0 - 1, by tile row
   R* ringR = ringL + P * TY;             // [P][TY]     f*_2 at x0 + w
 
-  // PF: the march reads rows k = 0 (ring row behind), 1 .. h (tile rows in
-  // march order), h + 1 (ring row ahead); row k goes to stage k % 2
-  T* pf = reinterpret_cast<T*>(smem + pf_offset<T, R>(P, TX, TY));   // [2][NS][TX]
-  auto krow = [&](int k) -> int {
-    if (k == 0) return ((up ? y0 - 1 : y0 + h) + ny) % ny;
-    if (k == h + 1) return ((up ? y0 + h : y0 - 1) + ny) % ny;
-    return row_of(k - 1);
-  };
-  auto issue = [&](int k) {   // one group per row, empty past the last row
-    if constexpr (PF) {
-      if (act && k <= h + 1) {
-        const T* src = fin + brick_base(x, krow(k), nxb, NS);
-        T* dst = pf + (size_t)(k & 1) * NS * TX + tx;
-#pragma unroll
-        for (int cpt = 0; cpt < NS; ++cpt) cp_async_elem(dst + (size_t)cpt * TX, src + (size_t)cpt * kBrick);
-      }
-      cp_async_commit();
-    }
-  };
-  auto staged = [&](int k) -> const T* {   // row k, once its copies have landed
-    cp_async_wait<1>();
-    return pf + (size_t)(k & 1) * NS * TX + tx;
-  };
-  issue(0);
-  issue(1);
-
   // x ring: only the component that streams into the tile, from the x split.
   // Read up front for all rows, long before the neighbouring tile reaches the
   // later rows; the step streams more bytes than L2 holds, so these loads ask
@@ -439,39 +370,18 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   R fbp[P], f3c[P], fbc[P];
 #pragma unroll
   for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
-  if constexpr (PF) {
-    const T* st = staged(0);
-    if (act) {
-      R o[5][P];
-      if (up) {
-        cell_post_at<Sys, T, R, C_Q4, FORM>(sys, st, TX, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-        for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
-      } else {
-        cell_post_at<Sys, T, R, C_Q5, FORM>(sys, st, TX, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-        for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
-      }
-    }
-    issue(2);   // into stage 0, consumed just now
-  }
   if (act) {
     R o[5][P];
-    if constexpr (!PF) {
-      if (up) {
-        cell_post<Sys, T, R, C_Q4, FORM>(sys, fin, x, (y0 - 1 + ny) % ny, nxb, xinv, c, om, set, kk, ch, o);
+    if (up) {
+      cell_post<Sys, T, R, C_Q4, FORM>(sys, fin, x, (y0 - 1 + ny) % ny, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
-        for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
-      } else {
-        cell_post<Sys, T, R, C_Q5, FORM>(sys, fin, x, (y0 + h) % ny, nxb, xinv, c, om, set, kk, ch, o);
+      for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
+    } else {
+      cell_post<Sys, T, R, C_Q5, FORM>(sys, fin, x, (y0 + h) % ny, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
-        for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
-      }
+      for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
     }
-    if constexpr (PF)
-      cell_post_at<Sys, T, R, C_FULL, FORM>(sys, staged(1), TX, xinv, c, om, set, kk, ch, o);
-    else
-      cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, row_of(0), nxb, xinv, c, om, set, kk, ch, o);
+    cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, row_of(0), nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       rb1[i * TX + tx] = o[0][i];
@@ -480,7 +390,6 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
       fbc[i] = up ? o[3][i] : o[4][i];
     }
   }
-  issue(3);   // into stage 1, consumed just now
 
   R m1 = R(0), m2 = R(0);
   bool bad = false;
@@ -491,10 +400,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     if (act) {
       R o[5][P];
       if (r + 1 < h) {
-        if constexpr (PF)
-          cell_post_at<Sys, T, R, C_FULL, FORM>(sys, staged(r + 2), TX, xinv, c, om, set, kk, ch, o);
-        else
-          cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, row_of(r + 1), nxb, xinv, c, om, set, kk, ch, o);
+        cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, row_of(r + 1), nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
           rb1[(nb * P + i) * TX + tx] = o[0][i];
@@ -505,17 +411,11 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
         }
       } else {
         if (up) {
-          if constexpr (PF)
-            cell_post_at<Sys, T, R, C_Q5, FORM>(sys, staged(r + 2), TX, xinv, c, om, set, kk, ch, o);
-          else
-            cell_post<Sys, T, R, C_Q5, FORM>(sys, fin, x, (y0 + h) % ny, nxb, xinv, c, om, set, kk, ch, o);
+          cell_post<Sys, T, R, C_Q5, FORM>(sys, fin, x, (y0 + h) % ny, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[4][i];
         } else {
-          if constexpr (PF)
-            cell_post_at<Sys, T, R, C_Q4, FORM>(sys, staged(r + 2), TX, xinv, c, om, set, kk, ch, o);
-          else
-            cell_post<Sys, T, R, C_Q4, FORM>(sys, fin, x, (y0 - 1 + ny) % ny, nxb, xinv, c, om, set, kk, ch, o);
+          cell_post<Sys, T, R, C_Q4, FORM>(sys, fin, x, (y0 - 1 + ny) % ny, nxb, xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[3][i];
         }
@@ -523,7 +423,6 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
         for (int i = 0; i < P; ++i) f3n[i] = fbn[i] = R(0);
       }
     }
-    issue(r + 4);   // into the stage of row r + 2, consumed just now
     __syncthreads();
     if (act) {
       const size_t base = brick_base(x, j, nxb, NS);
@@ -704,7 +603,7 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
   commit_max<R>(m1, m2, bad, a.ctl, s1);
 }
 
-template <class Sys, class T, class R, int FORM = 0, bool PF = false>
+template <class Sys, class T, class R, int FORM = 0>
 __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by, int TX, int TY,
                                             unsigned char* smem) {
   constexpr int NS = StateForm<Sys, FORM>::NS;
@@ -742,9 +641,9 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
   if (bx == 0 && by == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, s_sc, a.dx, a.fixed_xi, Sys::MHD);
   if constexpr (Sys::P <= 4) {
     if (by & 1)
-      step2d_tile_dir<Sys, T, R, -1, FORM, PF>(a, s_bc, bx, by, TX, TY, smem);
+      step2d_tile_dir<Sys, T, R, -1, FORM>(a, s_bc, bx, by, TX, TY, smem);
     else
-      step2d_tile_dir<Sys, T, R, +1, FORM, PF>(a, s_bc, bx, by, TX, TY, smem);
+      step2d_tile_dir<Sys, T, R, +1, FORM>(a, s_bc, bx, by, TX, TY, smem);
   } else {
     step2d_tile_one<Sys, T, R, FORM>(a, s_bc, bx, by, TX, TY, smem);
   }
@@ -1312,15 +1211,6 @@ template <class Sys, class T, class R>
 __global__ void step2d_kernel(StepArgs<T> a, int TX, int TY) {
   extern __shared__ __align__(128) unsigned char smem[];
   step2d_tile<Sys, T, R>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
-}
-
-// The plain march with each thread's next rows copied ahead into shared memory
-// (systems of at most four fields, FP32 or FP64 storage).
-// Register bound: the plain march's occupancy (7 blocks of 128 threads for FP32).
-template <class Sys, class T, class R>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 2) step2d_pf_kernel(StepArgs<T> a, int TX, int TY) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  step2d_tile<Sys, T, R, 0, true>(a, blockIdx.x, blockIdx.y, TX, TY, smem);
 }
 
 // The moment form (omega = 1): U in, U out, p components a cell.

@@ -302,7 +302,7 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
 }
 
 int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
-  if (!s || variant < 0 || variant > 3) return VKLB_ERR_ARG;
+  if (!s || variant < 0 || variant > 2) return VKLB_ERR_ARG;
   if (stages == 0) stages = 4;
   if (stages < 2 || stages > 8) return VKLB_ERR_ARG;
   if (s->dim != 2 && variant != 0) return VKLB_ERR_UNSUPPORTED;
@@ -312,9 +312,7 @@ int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
   if (variant == 2 && (s->prec != VKLB_FP32 || (s->kind != VKLB_SWE && s->kind != VKLB_EULER)))
     return VKLB_ERR_UNSUPPORTED;
   if (variant == 2 && s->tile_x % 64 != 0) return VKLB_ERR_ARG;
-  // rows copied ahead: systems of at most four fields, 4- or 8-byte storage
-  if (variant == 3 && (s->P > 4 || s->prec == VKLB_BF16_STORE)) return VKLB_ERR_UNSUPPORTED;
-  const int kv = variant == 2 ? 3 : (variant == 3 ? 4 : variant);
+  const int kv = variant == 2 ? 3 : variant;
   if (s->ops->smem(kv, s->P, s->tile_x, s->tile_y, stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->variant = variant;
   s->stages = stages;
@@ -561,7 +559,7 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
     const vklb_sim* s = sims[i];
     if (!s || !s->ready) return VKLB_ERR_STATE;
     if (s->nb > 0) return VKLB_ERR_UNSUPPORTED;   // characteristic faces: single-simulation steps only
-    if (s->variant >= 2) return VKLB_ERR_UNSUPPORTED;   // the paired / prefetching marches have no batched form
+    if (s->variant == 2) return VKLB_ERR_UNSUPPORTED;   // the paired march has no batched form
     if (s->ops != s0->ops || s->set != s0->set || s->variant != s0->variant || s->stages != s0->stages ||
         s->form != s0->form)
       return VKLB_ERR_ARG;
