@@ -688,13 +688,6 @@ __device__ __forceinline__ f2 ld_pair(const float* p) {
   return f2(v.x, v.y);
 }
 __device__ __forceinline__ void st_pair(float* p, f2 v) { *reinterpret_cast<float2*>(p) = make_float2(v.x, v.y); }
-// A second read of a pair this thread loaded moments before (an L1 hit), as its
-// own instruction, so that the first load's registers need not stay live.
-__device__ __forceinline__ f2 ld_pair_again(const float* p) {
-  f2 v;
-  asm volatile("ld.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-  return v;
-}
 
 // Post-collision components (MODE) of the cells x, x + 1 (x even) of row y.
 template <class S2, int MODE>
@@ -703,16 +696,14 @@ __device__ __forceinline__ void cell_post_pair(const S2& sys2, const float* __re
                                                f2 (&o)[5][S2::P]) {
   constexpr int P = S2::P;
   const size_t b = brick_base(x, y, nxb, 5 * P);
-  // U = sum_q f_q (Eq. 3); f is not held across the split (two cells of f are
-  // 40 registers): at omega != 1 the relaxation reads it again (L1 hits)
+  f2 f[5][P];
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int i = 0; i < P; ++i) f[q][i] = ld_pair(fin + b + (size_t)(q * P + i) * kBrick);
   f2 U[P];
 #pragma unroll
-  for (int i = 0; i < P; ++i) {
-    f2 acc = ld_pair(fin + b + (size_t)i * kBrick);
-#pragma unroll
-    for (int q = 1; q < 5; ++q) acc = acc + ld_pair(fin + b + (size_t)(q * P + i) * kBrick);
-    U[i] = acc;
-  }
+  for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
   f2 e[5][P];
   equilibria_d2q5<S2, f2, MODE>(sys2, U, xinv, c, set, k, ch, e);
 #pragma unroll
@@ -721,14 +712,7 @@ __device__ __forceinline__ void cell_post_pair(const S2& sys2, const float* __re
     for (int q = 0; q < 5; ++q) {
       const bool need = MODE == C_FULL || ((MODE == C_Q1 || MODE == C_Q2 || MODE == C_QX) && q < 2) ||
                         ((MODE == C_Q4 || MODE == C_Q5) && q >= 3);
-      if (need) {
-        if (om1) {
-          o[q][i] = e[q][i];
-        } else {
-          const f2 f = ld_pair_again(fin + b + (size_t)(q * P + i) * kBrick);
-          o[q][i] = vfma(om, e[q][i] - f, f);
-        }
-      }
+      if (need) o[q][i] = om1 ? e[q][i] : vfma(om, e[q][i] - f[q][i], f[q][i]);
     }
 }
 
