@@ -110,14 +110,11 @@ def configure(sim, shape):
 
 
 def step_kernel_name(system, prec, tile_x, variant, form=0):
-    """The step kernel the library launches: the bulk-copy or the paired
-    variant, or the plain one (moment form: step2d_u_kernel), which FP32-compute
-    MHD-GLM with blocks of at most 128 threads takes in its register-bounded
-    instantiation."""
+    """The step kernel the library launches: the bulk-copy variant, or the plain
+    one (moment form: step2d_u_kernel), which FP32-compute MHD-GLM with blocks
+    of at most 128 threads takes in its register-bounded instantiation."""
     if variant == 1:
         return "step2d_tma_kernel"
-    if variant == 2:
-        return "step2d_pair_kernel"
     if system == "mhd_glm" and prec != "fp64" and tile_x <= 128:
         return "step2d_lb_kernel"
     return "step2d_u_kernel" if form == 1 else "step2d_kernel"

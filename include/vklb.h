@@ -195,15 +195,10 @@ int vklb_set_tiling(vklb_sim* sim, int32_t tile_x, int32_t tile_y);
 /* Step-kernel variant for D2Q5: 0 = plain coalesced loads, rows exchanged
  * through shared memory with one block barrier per row; 1 = rows streamed into
  * shared memory by bulk asynchronous copies (TMA) with `stages` rows in flight
- * (2..8); 2 = the plain march with two neighbouring cells a thread, their
- * arithmetic in packed two-lane FP32 instructions and their loads and stores
- * 8 bytes wide (FP32 shallow water and Euler only; tile_x a multiple of 64,
- * tile_x / 2 threads a block).  All compute the same arithmetic (variant 2 to
- * FP32 rounding).  Default: 0 (4 stages kept for 1).  ERR_ARG for an unknown
- * variant, a stage count outside 2..8 or a tiling whose shared memory does not
- * fit; ERR_UNSUPPORTED for variants 1-2 on a 1D grid or in the moment form,
- * variant 1 with characteristic faces, variant 2 for other systems or
- * precisions.  Batches refuse members of variant 2. */
+ * (2..8).  Both compute the same arithmetic.  Default: 0 (4 stages kept for
+ * 1).  ERR_ARG for an unknown variant, a stage count outside 2..8 or a tiling
+ * whose shared memory does not fit; ERR_UNSUPPORTED for variant 1 on a 1D
+ * grid, in the moment form or with characteristic faces. */
 int vklb_set_variant(vklb_sim* sim, int32_t variant, int32_t stages);
 
 /* State form.  0 (default): the 5p distributions of Eq. (38)-(43) are the

@@ -2,8 +2,7 @@
 
 For a system, precision and grid side it times the step kernel over candidate
 tiles (cells along x per block x rows per block) and both kernel variants
-(plain loads; bulk-copy row pipeline with 2 to 4 stages; two cells a thread in
-packed FP32, for FP32 shallow water and Euler) with CUDA events on the
+(plain loads; bulk-copy row pipeline with 2 to 4 stages) with CUDA events on the
 simulation's stream, after warm-up, on a synthetic state of that size, and
 records the fastest in tuning.json (looked up by bench.py and the server by the
 nearest side).  Usage (GPU):
@@ -24,7 +23,7 @@ TABLE = os.path.join(HERE, "tuning.json")
 # (tx, -1): the height that fills whole waves of resident blocks
 TILES = [(32, 8), (32, 16), (64, 4), (64, 8), (64, 16), (64, 32), (128, 4), (128, 8), (128, 16), (128, 32),
          (128, 64), (256, 4), (256, 8), (64, -1), (128, -1), (256, -1)]
-VARIANTS = [(0, 0), (1, 2), (1, 3), (1, 4), (2, 0)]
+VARIANTS = [(0, 0), (1, 2), (1, 3), (1, 4)]
 
 
 def _state(system, n):

@@ -5,7 +5,6 @@
 // the library compiles in parallel; vklb.cu holds the C ABI.
 #pragma once
 #include <atomic>
-#include <type_traits>
 #include <cmath>
 #include <mutex>
 #include <cstdio>
@@ -109,8 +108,8 @@ const Ops* vk_ops_mhd(int dim, int prec);
 namespace {
 
 // Kernel selector: 0 plain distribution step, 1 bulk-copy distribution step,
-// 2 moment-form step, 3 paired distribution step (API variant 2).
-int kernel_variant(const vklb_sim* s) { return s->form == 1 ? 2 : (s->variant == 2 ? 3 : s->variant); }
+// 2 moment-form step.
+int kernel_variant(const vklb_sim* s) { return s->form == 1 ? 2 : s->variant; }
 
 template <class T>
 StepArgs<T> make_args(const vklb_sim* s, double t_end) {
@@ -177,14 +176,7 @@ struct Impl {
   }
   static size_t smem_bytes_v(int variant, int tx, int ty, int d) {
     if (variant == 1) return TmaLayout<T>::template make<R, P>(tx, ty, d).bytes;
-    if (variant == 3) return (size_t)(6 * P * (tx / 2) + 2 * P * ty) * sizeof(float);
     return smem_bytes(tx, ty);
-  }
-  // the paired march exists for FP32 distributions of the systems PairOf names
-  static constexpr bool kPaired =
-      DIM == 2 && PairOf<Sys>::ok && std::is_same<T, float>::value && std::is_same<R, float>::value;
-  static void launch_pair(dim3 grid, int TX, size_t sm, cudaStream_t st, const StepArgs<T>& a, int TY) {
-    if constexpr (kPaired) step2d_pair_kernel<Sys><<<grid, TX / 2, sm, st>>>(a, TX, TY);
   }
 
   static int step(vklb_sim* s, int64_t n, double t_end) {
@@ -224,8 +216,7 @@ struct Impl {
         StepArgs<T> a = make_args<T>(s, t_end);
         if (kv == 1)
           step2d_tma_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY, D);
-        else if (kv == 3)
-          launch_pair(grid, TX, sm, s->stream, a, TY);
+
         else if (kv == 2 && bounded(TX))
           launch_lb<1>(grid, TX, sm, s->stream, a, TY);
         else if (kv == 2)
@@ -269,8 +260,7 @@ struct Impl {
       cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_u_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if constexpr (kPaired)
-        cudaFuncSetAttribute(step2d_pair_kernel<Sys>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+
       if constexpr (kBounded) {
         cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
@@ -280,12 +270,6 @@ struct Impl {
     }
   }
 
-  static cudaError_t occupancy_pair(int* nb, int tx, size_t sm) {
-    if constexpr (kPaired)
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_pair_kernel<Sys>, tx / 2, sm);
-    else
-      return cudaErrorInvalidValue;
-  }
   template <int FORM>
   static cudaError_t occupancy_lb(int* nb, int tx, size_t sm) {
     if constexpr (kBounded)
@@ -305,8 +289,7 @@ struct Impl {
       cudaError_t e;
       if (variant == 1)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_tma_kernel<Sys, T, R>, tx, sm);
-      else if (variant == 3)
-        e = occupancy_pair(&nb, tx, sm);
+
       else if (variant == 2 && bounded(tx))
         e = occupancy_lb<1>(&nb, tx, sm);
       else if (variant == 2)

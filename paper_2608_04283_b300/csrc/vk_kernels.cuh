@@ -27,7 +27,6 @@
 // bound), with the characteristic boundary (Eqs. 33-36) or periodic wrap.
 #pragma once
 #include "vk_ctl.cuh"
-#include "vk_pair.cuh"
 #include "vk_systems.cuh"
 
 namespace vk {
@@ -647,281 +646,6 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
   } else {
     step2d_tile_one<Sys, T, R, FORM>(a, s_bc, bx, by, TX, TY, smem);
   }
-}
-
-// ------------------------------------------------------ D2Q5 step, paired
-// The plain march with two cells a thread (FP32 distributions, systems of at
-// most four fields): thread t of a block owns cells x0 + 2t and x0 + 2t + 1 of
-// every row of its tile and carries both as the two lanes of f2 (vk_pair.cuh),
-// so the split, the equilibria and the relaxation issue one packed instruction
-// for the two cells, and each load and store moves a pair (cells 2t, 2t + 1 of a
-// 32-cell brick are adjacent: one 8-byte access).  Of the x-neighbour exchange
-// only the two outer values cross threads (through shared memory); the inner
-// ones stay in the thread.  The x ring and the epilogue's wave speeds run one
-// cell at a time, as in the plain march.
-template <class Sys> struct PairOf {
-  static constexpr bool ok = false;
-};
-template <> struct PairOf<Euler<float, 2>> {
-  static constexpr bool ok = true;
-  typedef Euler<f2, 2> type;
-  static VK_HD type make(const Euler<float, 2>& s) {
-    type r;
-    r.gamma = f2(s.gamma);
-    r.lg = f2(s.lg);
-    return r;
-  }
-};
-template <> struct PairOf<SWE<float, 2>> {
-  static constexpr bool ok = true;
-  typedef SWE<f2, 2> type;
-  static VK_HD type make(const SWE<float, 2>& s) {
-    type r;
-    r.g = f2(s.g);
-    r.lg = f2(s.lg);
-    return r;
-  }
-};
-
-__device__ __forceinline__ f2 ld_pair(const float* p) {
-  const float2 v = *reinterpret_cast<const float2*>(p);
-  return f2(v.x, v.y);
-}
-__device__ __forceinline__ void st_pair(float* p, f2 v) { *reinterpret_cast<float2*>(p) = make_float2(v.x, v.y); }
-
-// Post-collision components (MODE) of the cells x, x + 1 (x even) of row y.
-template <class S2, int MODE>
-__device__ __forceinline__ void cell_post_pair(const S2& sys2, const float* __restrict__ fin, int x, int y, int nxb,
-                                               f2 xinv, f2 c, f2 om, bool om1, int set, f2 k, f2 ch,
-                                               f2 (&o)[5][S2::P]) {
-  constexpr int P = S2::P;
-  const size_t b = brick_base(x, y, nxb, 5 * P);
-  f2 f[5][P];
-#pragma unroll
-  for (int q = 0; q < 5; ++q)
-#pragma unroll
-    for (int i = 0; i < P; ++i) f[q][i] = ld_pair(fin + b + (size_t)(q * P + i) * kBrick);
-  f2 U[P];
-#pragma unroll
-  for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
-  f2 e[5][P];
-  equilibria_d2q5<S2, f2, MODE>(sys2, U, xinv, c, set, k, ch, e);
-#pragma unroll
-  for (int i = 0; i < P; ++i)
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const bool need = MODE == C_FULL || ((MODE == C_Q1 || MODE == C_Q2 || MODE == C_QX) && q < 2) ||
-                        ((MODE == C_Q4 || MODE == C_Q5) && q >= 3);
-      if (need) o[q][i] = om1 ? e[q][i] : vfma(om, e[q][i] - f[q][i], f[q][i]);
-    }
-}
-
-template <class Sys, int DIR>
-__device__ __forceinline__ void step2d_tile_pair_dir(const StepArgs<float>& a, const BlockConsts<Sys, float>& bc,
-                                                     int bx, int by, int TX, int TY, unsigned char* smem) {
-  typedef typename PairOf<Sys>::type S2;
-  constexpr int P = Sys::P;
-  const bool up = DIR > 0;
-  const Sys sys = bc.sys;
-  const S2 sys2 = PairOf<Sys>::make(sys);
-  const int t = threadIdx.x, nt = blockDim.x;   // nt = TX / 2
-  const int x0 = bx * TX, y0 = by * TY;
-  const int nx = a.nx, ny = a.ny;
-  const int w = min(TX, nx - x0), h = min(TY, ny - y0);
-  const int x = x0 + 2 * t;
-  const bool act = 2 * t < w, act2 = 2 * t + 1 < w;
-  const int nxb = a.pitch / kBrick;
-  const float* __restrict__ fin = a.src();
-  float* __restrict__ fout = a.dst();
-  const int s1 = (a.slot + 1) % 3;
-  const float xinv = bc.xinv, ch = bc.ch, c = bc.c, om = bc.om, kk = bc.k;
-  const f2 xinv2(xinv), ch2(ch), c2(c), om2(om), kk2(kk);
-  const bool om1 = om == 1.0f;
-  const int set = a.set;
-  auto row_of = [&](int r) -> int { return up ? y0 + r : y0 + h - 1 - r; };
-
-  float* rb1 = reinterpret_cast<float*>(smem);   // [3][P][nt]  f*_1 of each thread's second cell
-  float* rb2 = rb1 + 3 * P * nt;                 // [3][P][nt]  f*_2 of each thread's first cell
-  float* ringL = rb2 + 3 * P * nt;               // [P][TY]     f*_1 at x0 - 1, by tile row
-  float* ringR = ringL + P * TY;                 // [P][TY]     f*_2 at x0 + w
-
-  // x ring, one cell at a time, read up front with the L2 keep policy
-  for (int r2 = t; r2 < 2 * h; r2 += nt) {
-    const int side = r2 >= h;
-    const int r = side ? r2 - h : r2;
-    const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
-    float o[5][P];
-    if (!side) {
-      cell_post<Sys, float, float, C_Q1, 0, true>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-      for (int i = 0; i < P; ++i) ringL[i * TY + r] = o[0][i];
-    } else {
-      cell_post<Sys, float, float, C_Q2, 0, true>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-      for (int i = 0; i < P; ++i) ringR[i * TY + r] = o[1][i];
-    }
-  }
-
-  // march state: behind / current / ahead components along y, f*_3, and the
-  // inner x exchange (f*_1 of the first cell, f*_2 of the second) of the row
-  // being streamed and of the next one
-  f2 fbp[P], f3c[P], fbc[P];
-  float in1c[P], in2c[P];
-#pragma unroll
-  for (int i = 0; i < P; ++i) {
-    fbp[i] = f3c[i] = fbc[i] = f2(0.0f);
-    in1c[i] = in2c[i] = 0.0f;
-  }
-  if (act) {
-    f2 o[5][P];
-    if (up) {
-      cell_post_pair<S2, C_Q4>(sys2, fin, x, (y0 - 1 + ny) % ny, nxb, xinv2, c2, om2, om1, set, kk2, ch2, o);
-#pragma unroll
-      for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
-    } else {
-      cell_post_pair<S2, C_Q5>(sys2, fin, x, (y0 + h) % ny, nxb, xinv2, c2, om2, om1, set, kk2, ch2, o);
-#pragma unroll
-      for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
-    }
-    cell_post_pair<S2, C_FULL>(sys2, fin, x, row_of(0), nxb, xinv2, c2, om2, om1, set, kk2, ch2, o);
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      rb1[i * nt + t] = o[0][i].y;
-      rb2[i * nt + t] = o[1][i].x;
-      in1c[i] = o[0][i].x;
-      in2c[i] = o[1][i].y;
-      f3c[i] = o[2][i];
-      fbc[i] = up ? o[3][i] : o[4][i];
-    }
-  }
-
-  float m1 = 0.0f, m2 = 0.0f;
-  bool bad = false;
-  for (int r = 0; r < h; ++r) {
-    const int j = row_of(r);
-    f2 fan[P], f3n[P], fbn[P];
-    float in1n[P], in2n[P];
-    const int nb = (r + 1) % 3, cb = r % 3;
-    if (act) {
-      f2 o[5][P];
-      if (r + 1 < h) {
-        cell_post_pair<S2, C_FULL>(sys2, fin, x, row_of(r + 1), nxb, xinv2, c2, om2, om1, set, kk2, ch2, o);
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          rb1[(nb * P + i) * nt + t] = o[0][i].y;
-          rb2[(nb * P + i) * nt + t] = o[1][i].x;
-          in1n[i] = o[0][i].x;
-          in2n[i] = o[1][i].y;
-          f3n[i] = o[2][i];
-          fbn[i] = up ? o[3][i] : o[4][i];
-          fan[i] = up ? o[4][i] : o[3][i];
-        }
-      } else {
-        if (up) {
-          cell_post_pair<S2, C_Q5>(sys2, fin, x, (y0 + h) % ny, nxb, xinv2, c2, om2, om1, set, kk2, ch2, o);
-#pragma unroll
-          for (int i = 0; i < P; ++i) fan[i] = o[4][i];
-        } else {
-          cell_post_pair<S2, C_Q4>(sys2, fin, x, (y0 - 1 + ny) % ny, nxb, xinv2, c2, om2, om1, set, kk2, ch2, o);
-#pragma unroll
-          for (int i = 0; i < P; ++i) fan[i] = o[3][i];
-        }
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          f3n[i] = fbn[i] = f2(0.0f);
-          in1n[i] = in2n[i] = 0.0f;
-        }
-      }
-    }
-    __syncthreads();
-    if (act) {
-      const size_t base = brick_base(x, j, nxb, 5 * P);
-      const int rt = j - y0;
-      const bool last1 = 2 * t + 1 == w - 1;   // the second cell is the tile's last
-      f2 U[P];
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        f2 g[5];
-        const float left = t == 0 ? ringL[i * TY + rt] : rb1[(cb * P + i) * nt + t - 1];
-        const float right = act2 ? (last1 ? ringR[i * TY + rt] : rb2[(cb * P + i) * nt + t + 1]) : 0.0f;
-        g[0] = f2(left, in1c[i]);
-        g[1] = f2(act2 ? in2c[i] : ringR[i * TY + rt], right);
-        g[2] = f3c[i];
-        g[3] = up ? fbp[i] : fan[i];
-        g[4] = up ? fan[i] : fbp[i];
-        if (act2) {
-#pragma unroll
-          for (int q = 0; q < 5; ++q) st_pair(fout + (size_t)(q * P + i) * kBrick + base, g[q]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 5; ++q) fout[(size_t)(q * P + i) * kBrick + base] = g[q].x;
-        }
-        U[i] = g[0] + g[1] + g[2] + g[3] + g[4];
-      }
-      float Ua[P], e1, e2;
-#pragma unroll
-      for (int i = 0; i < P; ++i) Ua[i] = U[i].x;
-      if (!on_char_face(a, x, j)) {
-        bad |= !sys.epilogue(Ua, e1, e2);
-        m1 = fmaxf(m1, e1);
-        m2 = fmaxf(m2, e2);
-      }
-      if (act2 && !on_char_face(a, x + 1, j)) {
-#pragma unroll
-        for (int i = 0; i < P; ++i) Ua[i] = U[i].y;
-        bad |= !sys.epilogue(Ua, e1, e2);
-        m1 = fmaxf(m1, e1);
-        m2 = fmaxf(m2, e2);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      fbp[i] = fbc[i];
-      f3c[i] = f3n[i];
-      fbc[i] = fbn[i];
-      in1c[i] = in1n[i];
-      in2c[i] = in2n[i];
-    }
-  }
-  commit_max<float>(m1, m2, bad, a.ctl, s1);
-}
-
-template <class Sys>
-__global__ void step2d_pair_kernel(StepArgs<float> a, int TX, int TY) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int tx = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  __shared__ StepScalars s_sc;
-  __shared__ BlockConsts<Sys, float> s_bc;
-  if (tx == 0) {
-    s_sc = step_scalars(a.ctl, a.slot, Sys::MHD, a.ch_factor, a.inv_nu, a.fixed_xi, a.t_end, a.dx);
-    s_bc = block_consts<Sys, float>(a, s_sc);
-  }
-  __syncthreads();
-  if (s_sc.done) {
-    constexpr int NS = 5 * Sys::P;
-    const int w = min(TX, a.nx - x0), h = min(TY, a.ny - y0);
-    for (int cx = tx; cx < w; cx += blockDim.x)
-      for (int r = 0; r < h; ++r)
-        for (int i = 0; i < NS; ++i) {
-          const size_t o = brick_base(x0 + cx, y0 + r, a.pitch / kBrick, NS) + (size_t)i * kBrick;
-          a.dst()[o] = a.src()[o];
-        }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tx == 0) {
-      const int s1 = (a.slot + 1) % 3, s2 = (a.slot + 2) % 3;
-      a.ctl->t[s1] = a.ctl->t[a.slot];
-      a.ctl->m1[s1] = a.ctl->m1[a.slot];
-      a.ctl->m2[s1] = a.ctl->m2[a.slot];
-      a.ctl->m1[s2] = 0ull;
-      a.ctl->m2[s2] = 0ull;
-    }
-    return;
-  }
-  if (blockIdx.x == 0 && blockIdx.y == 0 && tx == 0) step_bookkeeping(a.ctl, a.slot, s_sc, a.dx, a.fixed_xi, false);
-  if (blockIdx.y & 1)
-    step2d_tile_pair_dir<Sys, -1>(a, s_bc, blockIdx.x, blockIdx.y, TX, TY, smem);
-  else
-    step2d_tile_pair_dir<Sys, +1>(a, s_bc, blockIdx.x, blockIdx.y, TX, TY, smem);
 }
 
 // ------------------------------------------------- D2Q5 step, bulk-copy rows

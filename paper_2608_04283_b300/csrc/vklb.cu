@@ -289,12 +289,11 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
   if (!s) return VKLB_ERR_ARG;
   if (tx == 0) tx = 128;
   if (ty == 0) ty = -1;
-  if (ty == -1 && s->dim == 2 && tx >= 32 && tx <= 256 && tx % 32 == 0 && (s->variant != 2 || tx % 64 == 0)) {
+  if (ty == -1 && s->dim == 2 && tx >= 32 && tx <= 256 && tx % 32 == 0) {
     int st = wave_fit_rows(s, tx, &ty);
     if (st) return st;
   }
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
-  if (s->variant == 2 && tx % 64 != 0) return VKLB_ERR_ARG;   // paired march: whole warps of cell pairs
   if (s->ops->smem(kernel_variant(s), s->P, tx, ty, s->stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->tile_x = tx;
   s->tile_y = ty;
@@ -302,18 +301,13 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
 }
 
 int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
-  if (!s || variant < 0 || variant > 2) return VKLB_ERR_ARG;
+  if (!s || variant < 0 || variant > 1) return VKLB_ERR_ARG;
   if (stages == 0) stages = 4;
   if (stages < 2 || stages > 8) return VKLB_ERR_ARG;
   if (s->dim != 2 && variant != 0) return VKLB_ERR_UNSUPPORTED;
   if (s->nb > 0 && variant == 1) return VKLB_ERR_UNSUPPORTED;   // characteristic faces: not the bulk-copy step
   if (s->form == 1 && variant != 0) return VKLB_ERR_UNSUPPORTED;
-  // the paired march: FP32 distributions of shallow water or Euler, whole warps of pairs
-  if (variant == 2 && (s->prec != VKLB_FP32 || (s->kind != VKLB_SWE && s->kind != VKLB_EULER)))
-    return VKLB_ERR_UNSUPPORTED;
-  if (variant == 2 && s->tile_x % 64 != 0) return VKLB_ERR_ARG;
-  const int kv = variant == 2 ? 3 : variant;
-  if (s->ops->smem(kv, s->P, s->tile_x, s->tile_y, stages) > 200 * 1024) return VKLB_ERR_ARG;
+  if (s->ops->smem(variant, s->P, s->tile_x, s->tile_y, stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->variant = variant;
   s->stages = stages;
   return VKLB_OK;
@@ -559,7 +553,6 @@ int vklb_batch_create(int32_t n, vklb_sim* const* sims, vklb_batch** out) {
     const vklb_sim* s = sims[i];
     if (!s || !s->ready) return VKLB_ERR_STATE;
     if (s->nb > 0) return VKLB_ERR_UNSUPPORTED;   // characteristic faces: single-simulation steps only
-    if (s->variant == 2) return VKLB_ERR_UNSUPPORTED;   // the paired march has no batched form
     if (s->ops != s0->ops || s->set != s0->set || s->variant != s0->variant || s->stages != s0->stages ||
         s->form != s0->form)
       return VKLB_ERR_ARG;
