@@ -356,6 +356,8 @@ def run_ours(args, wl):
         acc = accuracy_vs_fp64(torch, vklb, wl, prec, tile, steps=50, form=args.form)
         acc_exact = accuracy_vs_exact(vklb, prec) if prec != "fp64" else None
         e2e = end_to_end(torch, vklb, wl, prec, tile, steps=min(args.steps, REINIT_EVERY), U0=U0, form=args.form)
+        if not args.no_extras:
+            extras["copy_same_bytes"] = copy_same_bytes(torch, bpl * cells, flush_buf)
         if not args.no_extras and args.workload == "euler_vortex_1024":
             extras["mhd_orszag_tang_2048"] = secondary(torch, vklb, WORKLOADS["mhd_orszag_tang_2048"], prec,
                                                        flush_buf, steps=100)
@@ -502,6 +504,28 @@ def end_to_end(torch, vklb, wl, prec, tile, steps, U0, form="distributions"):
             "h2d_bytes_per_step": int(U0.nbytes / steps), "d2h_bytes_per_step": int(U0.nbytes / steps),
             "steps_per_solve": steps,
             "note": "one solve = H2D of U0 (pinned), the steps, D2H of U (pinned); bytes amortised per step"}
+
+
+def copy_same_bytes(torch, nbytes, flush_buf, reps=50):
+    """A plain device copy moving the step's bytes (nbytes / 2 read, nbytes / 2
+    written), L2 flushed before each copy as before each step: the bandwidth a
+    streaming kernel of this size reaches, beside the large-copy peak."""
+    n = nbytes // 2 // 4
+    a = torch.ones(n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    st = torch.cuda.current_stream()
+    for i in range(5):
+        b.copy_(a)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for i in range(reps):
+        flush_buf(i)
+        ev[i][0].record(st)
+        b.copy_(a)
+        ev[i][1].record(st)
+    torch.cuda.synchronize()
+    ms = float(np.mean([x.elapsed_time(y) for x, y in ev]))
+    return {"bytes": int(2 * n * 4), "ms": ms, "gbs": 2 * n * 4 / (ms * 1e-3) / 1e9,
+            "note": "torch copy of the step's algorithmic bytes, L2 flushed before each copy"}
 
 
 def moment_form(torch, vklb, flush_buf, steps=100):

@@ -4,7 +4,19 @@
 // type of its precision), one Ctl block of control words and small scratch
 // buffers for reductions.  Every kernel runs on the simulation's stream; no call
 // synchronises except those documented as synchronising.
+#include <nvtx3/nvToolsExt.h>
+
 #include "vk_host.cuh"
+
+namespace {
+// An NVTX range over one call of the C ABI (named after the call), so that a
+// timeline profiler shows the host calls beside the kernels they enqueue; free
+// when no tool is attached.
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 std::atomic<long long> g_launches{0};
 
@@ -268,6 +280,7 @@ int vklb_destroy(vklb_sim* s) {
 }
 
 int vklb_set_state(vklb_sim* s, const double* U, int32_t on_device) {
+  CallRange range("vklb_set_state");
   if (!s || !U) return VKLB_ERR_ARG;
   const size_t bytes = sizeof(double) * s->P * (size_t)s->cells;
   int st = cuda_status(cudaMemcpyAsync(s->stage, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -353,6 +366,7 @@ int vklb_set_form(vklb_sim* s, int32_t form) {
 }
 
 int vklb_step(vklb_sim* s, int64_t n) {
+  CallRange range("vklb_step");
   if (!s || n < 0) return VKLB_ERR_ARG;
   if (!s->ready) return VKLB_ERR_STATE;
   if (n == 0) return VKLB_OK;
@@ -360,6 +374,7 @@ int vklb_step(vklb_sim* s, int64_t n) {
 }
 
 int vklb_step_to(vklb_sim* s, double t_end) {
+  CallRange range("vklb_step_to");
   if (!s || !(t_end > 0.0)) return VKLB_ERR_ARG;
   if (!s->ready) return VKLB_ERR_STATE;
   for (int iter = 0; iter < 1000; ++iter) {
@@ -399,6 +414,7 @@ int vklb_sync(vklb_sim* s) {
 }
 
 int vklb_moments(vklb_sim* s, double* U, int32_t on_device) {
+  CallRange range("vklb_moments");
   if (!s || !U) return VKLB_ERR_ARG;
   if (!s->ready) return VKLB_ERR_STATE;
   int st = s->ops->moments(s, s->stage);
@@ -411,6 +427,7 @@ int vklb_moments(vklb_sim* s, double* U, int32_t on_device) {
 }
 
 int vklb_conservation_totals(vklb_sim* s, double* totals) {
+  CallRange range("vklb_conservation_totals");
   if (!s || !totals) return VKLB_ERR_ARG;
   if (!s->ready) return VKLB_ERR_STATE;
   int st = s->ops->totals(s, totals);
@@ -633,6 +650,7 @@ int vklb_batch_set_tiling(vklb_batch* b, int32_t tx, int32_t ty) {
 }
 
 int vklb_batch_step(vklb_batch* b, int64_t n, int32_t use_graph) {
+  CallRange range("vklb_batch_step");
   if (!b || n < 0) return VKLB_ERR_ARG;
   if (n == 0) return VKLB_OK;
   // a member whose form, kernel variant or state changed since the batch was

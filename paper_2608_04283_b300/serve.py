@@ -19,6 +19,7 @@ All arithmetic runs in libvklb.so; this module only schedules.
 """
 from __future__ import annotations
 
+import json
 import time
 from dataclasses import dataclass, field
 
@@ -79,10 +80,12 @@ class Server:
     """``max_side``: grids up to this side have their results read back through a
     pinned host buffer per family (allocated here, one direct copy per result;
     the result a caller keeps is copied out of it); larger ones through a fresh
-    pageable array."""
+    pageable array.  ``log``: a text stream that receives one JSON line per
+    finished request (id, system, side, steps, arrival, admission and finish
+    times, status)."""
 
     def __init__(self, budget_bytes=120e9, tick_steps=50, precision="fp32", tiles=None, keep_results=False,
-                 clock=None, form="moments", max_side=2048, device_ic=False):
+                 clock=None, form="moments", max_side=2048, device_ic=False, log=None):
         import torch
         self.torch = torch
         self.budget = float(budget_bytes)
@@ -92,6 +95,7 @@ class Server:
         self.keep = keep_results
         self.form = form
         self.device_ic = device_ic
+        self.log = log
         self.streams = {k: torch.cuda.Stream() for k in FAMILY}
         self.clock = clock or time.perf_counter
         self.staging = {k: torch.empty(FIELDS[k] * max_side * max_side, dtype=torch.float64,
@@ -213,6 +217,11 @@ class Server:
                     except vklb.VKLBError:
                         j.status = "failed"
                     j.t_done = now()
+                    if self.log is not None:
+                        r = j.req
+                        self.log.write(json.dumps({"rid": r.rid, "system": r.system, "n": r.n, "steps": r.steps,
+                                                   "arrival_s": r.arrival, "admitted_s": j.t_admit,
+                                                   "done_s": j.t_done, "status": j.status}) + "\n")
                     j.sim.close()
                     j.sim = None
                     used -= j.need

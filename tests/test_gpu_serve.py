@@ -32,12 +32,18 @@ def test_mix_equals_alone_and_reports_latency(srv_mod):
 
 
 def test_budget_is_respected(srv_mod):
+    import io
+    import json
     trace = inputs.serving_trace(count=6, rate=1e6, seed=4, nmin=128, nmax=128, nstep=32, smin=10, smax=10)
     per = max(srv_mod.device_bytes(r.system, r.n) for r in trace)
-    server = srv_mod.Server(budget_bytes=2 * per, tick_steps=5)
+    log = io.StringIO()
+    server = srv_mod.Server(budget_bytes=2 * per, tick_steps=5, log=log)
     rep = server.run(trace, realtime=False)
     assert rep.summary()["completed"] == 6
     assert rep.peak_bytes <= 2 * per
+    lines = [json.loads(x) for x in log.getvalue().splitlines()]
+    assert sorted(x["rid"] for x in lines) == [r.rid for r in trace]
+    assert all(x["status"] == "done" and x["done_s"] >= x["admitted_s"] for x in lines)
 
 
 def test_device_initial_states_match_host(srv_mod):
