@@ -4,6 +4,7 @@
 // forms that the step kernels use (vk_systems.cuh) on the CPU so that tests can
 // compare them with the FP64 oracle without a GPU.  It is not part of the
 // simulation path: libvklb.so never calls it.
+#include "vk_ctl.cuh"
 #include "vk_systems.cuh"
 
 namespace {
@@ -166,4 +167,13 @@ extern "C" int vklb_hc_char_rhs2d(int kind, int precision, int d, int side, doub
                                   double ay, const double* U, const double* dU, int64_t n, double* out) {
   if (precision == 0) return bc2_dispatch<double>(kind, d, side, gamma, g, ax, ay, U, dU, n, out);
   return bc2_dispatch<float>(kind, d, side, gamma, g, ax, ay, U, dU, n, out);
+}
+
+// The enumeration of the characteristic faces' nodes that the boundary passes
+// use (one thread a node): xs, ys receive char_face_nodes() coordinates.
+extern "C" int vklb_hc_char_faces(int nx, int ny, int cbx, int cby, int* xs, int* ys, int cap) {
+  const int nb = vk::char_face_nodes(nx, ny, cbx, cby);
+  if (nb > cap) return -1;
+  for (int id = 0; id < nb; ++id) vk::char_face_node(id, nx, ny, cbx, cby, xs[id], ys[id]);
+  return nb;
 }

@@ -59,4 +59,24 @@ VK_HD StepScalars step_scalars(const Ctl* ctl, int slot, bool mhd, double ch_fac
   return s;
 }
 
+// Nodes of the characteristic faces of a 2D grid (cbx: the two x faces, cby:
+// the two y faces), numbered for one thread each: the x faces' columns first
+// (2 ny nodes, corners included), then the y faces' rows without those corners.
+VK_HD int char_face_nodes(int nx, int ny, int cbx, int cby) {
+  return (cbx ? 2 * ny : 0) + (cby ? 2 * (nx - (cbx ? 2 : 0)) : 0);
+}
+VK_HD void char_face_node(int id, int nx, int ny, int cbx, int cby, int& x, int& y) {
+  if (cbx) {
+    if (id < 2 * ny) {
+      x = id < ny ? 0 : nx - 1;
+      y = id < ny ? id : id - ny;
+      return;
+    }
+    id -= 2 * ny;
+  }
+  const int w = nx - (cbx ? 2 : 0), x0 = cbx ? 1 : 0;
+  y = id < w ? 0 : ny - 1;
+  x = x0 + (id < w ? id : id - w);
+}
+
 }  // namespace vk

@@ -1016,23 +1016,7 @@ __global__ void __launch_bounds__(128, MINB)
 // difference D towards the interior (a corner sums its two faces), and
 // f^{n+1} = f^eq(U_b^{n+1}) with xi_{n+1}.  Boundary nodes are numbered: the
 // x faces' columns (2 ny nodes) first, then the y faces' rows without the
-// corners already counted.
-VK_HD int char_face_nodes(int nx, int ny, int cbx, int cby) {
-  return (cbx ? 2 * ny : 0) + (cby ? 2 * (nx - (cbx ? 2 : 0)) : 0);
-}
-VK_HD void char_face_node(int id, int nx, int ny, int cbx, int cby, int& x, int& y) {
-  if (cbx) {
-    if (id < 2 * ny) {
-      x = id < ny ? 0 : nx - 1;
-      y = id < ny ? id : id - ny;
-      return;
-    }
-    id -= 2 * ny;
-  }
-  const int w = nx - (cbx ? 2 : 0), x0 = cbx ? 1 : 0;
-  y = id < w ? 0 : ny - 1;
-  x = x0 + (id < w ? id : id - w);
-}
+// corners already counted (char_face_nodes / char_face_node, vk_ctl.cuh).
 
 template <class Sys, class T, class R>
 __device__ __forceinline__ void load_U(const T* __restrict__ f, int x, int y, int nxb, R (&U)[Sys::P]) {

@@ -197,3 +197,21 @@ def test_char_rhs_2d_matches_oracle(name, kw, d, side):
     for i in range(U.shape[1]):
         want = ovklb.outgoing_part(A[i], dU[:, i], side)
         assert np.allclose(out[:, i], want, rtol=1e-10, atol=1e-12), i
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (4, 7), (37, 5), (64, 64)])
+@pytest.mark.parametrize("cbx,cby", [(1, 0), (0, 1), (1, 1)])
+def test_char_face_enumeration(nx, ny, cbx, cby):
+    """The boundary passes give one thread to each node of the characteristic
+    faces: the enumeration covers exactly those nodes, each once, in range."""
+    cap = 2 * (nx + ny)
+    xs = np.zeros(cap, dtype=np.int32)
+    ys = np.zeros(cap, dtype=np.int32)
+    P = C.POINTER(C.c_int)
+    nb = _lib.vklb_hc_char_faces(nx, ny, cbx, cby, xs.ctypes.data_as(P), ys.ctypes.data_as(P), cap)
+    assert nb >= 0
+    got = set(zip(xs[:nb].tolist(), ys[:nb].tolist()))
+    assert len(got) == nb
+    want = {(x, y) for x in range(nx) for y in range(ny)
+            if (cbx and x in (0, nx - 1)) or (cby and y in (0, ny - 1))}
+    assert got == want
