@@ -215,6 +215,17 @@ def blas_threads():
                 return int(os.environ[var])
         return os.cpu_count() or 1
 
+L2_NOTE = "GPU arm: L2 flushed before every timed step (256 MiB write, then 256 MiB read of another buffer)"
+
+
+def workload_config(args, wl, world):
+    """The workload both arms run, identical in their lines; each arm's own
+    details (launch shape and precision, or the oracle's sample) sit beside it."""
+    return {"workload": args.workload, "description": wl["name"], "cells": wl["n"][0] * wl["n"][1],
+            "form": args.form, "l2": L2_NOTE, "reinit_every": REINIT_EVERY,
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def oracle_mlups(wl, rows, steps, warmup):
     """The FP64 oracle as it stands on a bounded sample: a strip of ``rows`` rows
     of the workload grid (periodic), one oracle step per bench step."""
@@ -253,7 +264,8 @@ def run_reference(args, wl):
     line = {"metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "description": wl["name"], "parallelism": "host cores"},
+            "config": workload_config(args, wl, world),
+            "launch": {"where": "host cores", "threads": threads, "precision": "fp64", "sample": sample},
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -375,11 +387,9 @@ def run_ours(args, wl):
                 "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-store/f32"}[prec],
                 "data": "synthetic",
-                "config": {"workload": args.workload, "description": wl["name"], "cells": cells,
-                           "precision": prec, "tile": [sim.info.tile_x, sim.info.tile_y],
-                           "variant": sim.info.variant, "form": args.form,
-                           "l2": "flushed before every timed step: 256 MiB write, then 256 MiB read of another buffer",
-                           "reinit_every": REINIT_EVERY, "parallelism": "replicas" if world > 1 else "single"},
+                "config": workload_config(args, wl, world),
+                "launch": {"where": "cuda", "precision": prec, "tile": [sim.info.tile_x, sim.info.tile_y],
+                           "variant": sim.info.variant},
                 "hbm_gbs": achieved, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(l1 - l0), "clocks": clk, "accuracy_fp32_vs_fp64": acc,
                 "accuracy_fp32_vs_exact": acc_exact,
@@ -685,7 +695,7 @@ def served_paced(count=24, rate=3.0):
     return out
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10000)
@@ -705,9 +715,14 @@ def main():
     ap.add_argument("--only-batched", type=int, default=0, metavar="N",
                     help="run only the batched shallow-water leg with the first N instances (and --form), print "
                          "its JSON and exit: a case small enough to profile")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
+    return args
+
+
+def main():
+    args = parse_args()
     wl = WORKLOADS[args.workload]
     if args.only_batched > 0:
         import torch

@@ -47,6 +47,12 @@ Readings of the paper taken here, where it is silent or ambiguous:
       distributions are f^eq(U_b^{n+1}) with xi_{n+1} (R11), and xi_{n+1}
       includes the boundary states.  Streaming wraps as on a periodic grid;
       what wraps lands only in boundary nodes, which are overwritten.
+  R20 storage="bf16" models distributions kept in bfloat16 (the precision form
+      of the GPU path; the paper computes in FP64 throughout): every stored f
+      (the initial f^eq, and after each step the streamed f including the
+      boundary nodes) is rounded to the nearest bfloat16, ties to even; U, the
+      next lattice speed and the equilibria are formed from the rounded f, the
+      arithmetic itself stays FP64.
 
 Test infrastructure only.
 
@@ -114,6 +120,15 @@ def outgoing_part(A, v, side):
     return out
 
 
+def round_to_bf16(x):
+    """Nearest bfloat16 (8 significant bits, ties to even) of each FP64 value,
+    returned as FP64; normal range (no overflow or subnormal handling): with
+    x = m 2^e, 1/2 <= |m| < 1, the significand m 2^8 is rounded to an integer
+    (numpy rounds halves to even) and scaled back."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.round(m * 256.0), e - 8)
+
+
 class Sim:
     """One VKLB simulation on a uniform grid.
 
@@ -125,11 +140,12 @@ class Sim:
     omega    : relaxation parameter, 0 < omega <= 2 (Sec. 2.3)
     nu       : CFL number (Eq. 29);  dt > 0 fixes xi = dx / dt instead
     alpha_norm: "local" or "global", reading R1 of alpha's normaliser
+    storage  : "fp64", or "bf16" to round every stored f to bfloat16 (R20)
     """
 
     def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted",
                  c=0.05, k=2.0, omega=1.0, nu=0.9, dt=None, ch_factor=6.0, eta=None,
-                 alpha_norm="global"):
+                 alpha_norm="global", storage="fp64"):
         self.sys = system
         self.dim = system.dim
         self.n = tuple(int(v) for v in n)
@@ -165,6 +181,9 @@ class Sim:
         if alpha_norm not in ("local", "global"):
             raise ValueError(alpha_norm)
         self.alpha_norm = alpha_norm
+        if storage not in ("fp64", "bf16"):
+            raise ValueError(storage)
+        self.store = round_to_bf16 if storage == "bf16" else (lambda f: f)
         self.f = None
         self.t = 0.0
         self.steps = 0
@@ -289,7 +308,7 @@ class Sim:
         assert U0.shape == (self.sys.p,) + tuple(reversed(self.n)), U0.shape
         self.refresh_ch(U0)
         self.xi = self.cfl_xi(U0)
-        self.f = self.equilibrium(U0, self.xi)              # Eq. (2b)
+        self.f = self.store(self.equilibrium(U0, self.xi))  # Eq. (2b), R20
         self.t = 0.0
         self.steps = 0
 
@@ -310,7 +329,7 @@ class Sim:
         U = self.f.sum(axis=0)
         feq = self.equilibrium(U, xi)                         # Eqs. (22)-(24)/(41)
         fs = self.f - self.omega * (self.f - feq)             # Eq. (42)
-        fn = self.stream(fs)                                  # Eq. (43)
+        fn = self.store(self.stream(fs))                      # Eq. (43), R20
         Un = fn.sum(axis=0)                                   # Eq. (3)
         if self.bc == "characteristic" and self.dim == 1:
             ubl, ubr = self.char_bc(U, Un, xi)                # Eqs. (33)-(35)
@@ -329,7 +348,7 @@ class Sim:
         elif self.bc == "characteristic":
             fb = self.equilibrium(Un[:, mask], xin, self.max_lambda(Un))
             fn[:, :, mask] = fb                               # Eq. (36), R11, R19
-        self.f = fn
+        self.f = self.store(fn)                               # R20 (boundary nodes)
         self.t = self.t + self.dx / xi
         if t_end is not None and abs(self.t - t_end) <= 1e-13 * max(1.0, abs(t_end)):
             self.t = float(t_end)

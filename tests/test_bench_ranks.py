@@ -66,3 +66,20 @@ def test_single_rank_needs_no_process_group():
     import bench
     value, ms = bench.replica_throughput(torch, 10.0, cells=1000, steps=10, world=1, device="cpu")
     assert ms == 10.0 and value == pytest.approx(1000 * 10 / 0.01 / 1e6)
+
+
+def test_reference_arm_prints_the_workload_config():
+    """Both arms print the same workload config (the driver compares them); the
+    oracle's sample and the GPU launch shape sit in their own keys."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    args = bench.parse_args(["--steps", "1", "--warmup", "1"])
+    assert line["config"] == bench.workload_config(args, bench.WORKLOADS[args.workload], 1)
+    assert line["impl"] == "reference" and line["launch"]["precision"] == "fp64"
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
