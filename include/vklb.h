@@ -250,7 +250,9 @@ int vklb_info(const vklb_sim* sim, vklb_info_t* info);
  * row of bricks holds all components of 32 neighbouring cells contiguously).
  * In the moment form (vklb_set_form) the buffer holds U instead, field k of
  * cell (x, y) at f[((y * (pitch / 32) + x / 32) * p + k) * 32 + x % 32].
- * Borrowed; valid until the next vklb_step. */
+ * Borrowed and read-only (a step of MHD-GLM also keeps a copy of the tiles'
+ * edge columns, which writes through this pointer would leave stale); valid
+ * until the next vklb_step. */
 int vklb_device_state(const vklb_sim* sim, void** f_dev);
 
 /* Checking aid (no counterpart in the paper): fill the buffer that the next

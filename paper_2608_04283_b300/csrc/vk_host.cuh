@@ -63,6 +63,12 @@ struct vklb_sim {
   int variant, stages;     // step kernel: 0 plain, 1 bulk-copy row pipeline with `stages` rows in flight
   int form;                // 0 distributions f, 1 moments U (omega = 1, D2Q5)
   int QS;                  // stored components a field: Q (form 0) or 1 (form 1)
+  // halo of the long-split march (2D, p > 4): hl[b] holds the edge columns of
+  // the tiles of f[b] (halo_index), for tiles hl_tx wide; hl_ok: hl[cur] is
+  // the one of f[cur], written by the last step
+  void* hl[2];
+  size_t hl_bytes;
+  int hl_tx, hl_ok;
   bool ready;
   const Ops* ops;
 };
@@ -137,6 +143,10 @@ StepArgs<T> make_args(const vklb_sim* s, double t_end) {
   a.ctl = s->ctl;
   a.slot = (int)(s->launched % 3);
   a.sp = s->sp;
+  const bool hl = s->hl[0] && s->hl_tx == s->tile_x;
+  a.hl[0] = hl ? (T*)s->hl[0] : nullptr;
+  a.hl[1] = hl ? (T*)s->hl[1] : nullptr;
+  a.hl_ok = hl && s->hl_ok;
   return a;
 }
 
@@ -212,6 +222,9 @@ struct Impl {
       const size_t sm = smem_bytes_v(kv, TX, TY, D);
       set_attributes();
       dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
+      // the long-split march keeps the halo of its tiles' edge columns (p > 4,
+      // not the bulk-copy step)
+      const bool halo = P > 4 && kv != 1 && s->hl[0] && s->hl_tx == TX;
       for (int64_t i = 0; i < n; ++i) {
         StepArgs<T> a = make_args<T>(s, t_end);
         if (kv == 1)
@@ -236,6 +249,7 @@ struct Impl {
         }
         s->cur ^= 1;
         s->launched += 1;
+        s->hl_ok = halo;
       }
       g_launches += n;
       return cuda_status(cudaGetLastError());
@@ -421,7 +435,11 @@ struct BatchImpl {
       }
     }
     StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
-    for (size_t i = 0; i < b->sims.size(); ++i) h[i] = make_args<T>(b->sims[i], -1.0);
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+      h[i] = make_args<T>(b->sims[i], -1.0);
+      h[i].hl[0] = h[i].hl[1] = nullptr;   // batches keep no halo: the batch's tiles are its own
+      h[i].hl_ok = 0;
+    }
     // order after the work already queued on the simulations' streams
     int st = VKLB_OK;
     for (size_t i = 0; i < b->sims.size(); ++i) {
@@ -458,6 +476,7 @@ struct BatchImpl {
     for (vklb_sim* s : b->sims) {
       s->cur ^= (int)(n & 1);
       s->launched += n;
+      s->hl_ok = 0;
     }
     return VKLB_OK;
     }

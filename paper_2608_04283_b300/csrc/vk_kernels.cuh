@@ -68,8 +68,14 @@ struct StepArgs {
   Ctl* ctl;
   int slot;        // n % 3
   SysParams sp;
+  // Edge columns of the tiles (long-split march only; see halo_index): hl[b]
+  // holds those of f[b]; hl_ok says hl[parity] matches f^n for this tile width.
+  T* hl[2];
+  int hl_ok;
   VK_HD T* src() const { return parity ? f[1] : f[0]; }
   VK_HD T* dst() const { return parity ? f[0] : f[1]; }
+  VK_HD const T* halo_in() const { return hl_ok ? (parity ? hl[1] : hl[0]) : nullptr; }
+  VK_HD T* halo_out() const { return parity ? hl[0] : hl[1]; }
 };
 
 // 2D distribution layout: 32-cell bricks.  Component k = q p + i of cell (x, y)
@@ -89,6 +95,15 @@ VK_HD size_t cell_base(int Q, int P, int x, int y, int pitch) {
   return Q != 3 ? brick_base(x, y, pitch / kBrick, Q * P) : (size_t)y * pitch + x;
 }
 VK_HD size_t comp_stride(int Q, int pitch, int ny) { return Q != 3 ? (size_t)kBrick : (size_t)pitch * ny; }
+
+// Halo of the long-split march: the first (side 0) and last (side 1) column of
+// every tile TX wide, the npl stored components of a cell contiguous, rows in
+// order.  The step that writes f^{n+1} writes them too, so the next step reads
+// its x ring (the neighbouring tiles' edge columns) as whole contiguous runs
+// instead of one 4-byte value from each of npl brick lines a cell.
+VK_HD size_t halo_index(int tile, int side, int y, int ny, int npl) {
+  return (((size_t)tile * 2 + side) * ny + y) * npl;
+}
 
 // Which post-collision components a cell must produce (C_QX: f*_1 and f*_2).
 enum CollideMode { C_FULL = 0, C_Q1 = 1, C_Q2 = 2, C_Q4 = 3, C_Q5 = 4, C_QX = 5 };
@@ -284,23 +299,31 @@ struct StateForm {
   static constexpr int NS = FORM == 0 ? 5 * Sys::P : Sys::P;   // stored components a cell
 };
 
-// Post-collision components of cell (x, y) that MODE needs.
+// Post-collision components that MODE needs of the cell whose stored
+// component j sits at fin[b + j * plane].
 template <class Sys, class T, class R, int MODE, int FORM, bool KEEP = false>
-__device__ __forceinline__ void cell_post(const Sys& sys, const T* __restrict__ fin, int x, int y, int nxb, R xinv,
-                                          R c, R om, int set, R k, R ch, R (&o)[5][Sys::P]) {
+__device__ __forceinline__ void cell_post_at(const Sys& sys, const T* __restrict__ fin, size_t plane, size_t b,
+                                             R xinv, R c, R om, int set, R k, R ch, R (&o)[5][Sys::P]) {
   constexpr int P = Sys::P;
-  const size_t b = brick_base(x, y, nxb, StateForm<Sys, FORM>::NS);
   if constexpr (FORM == 0) {
-    collide_d2q5<Sys, T, R, MODE, KEEP>(sys, fin, kBrick, b, xinv, c, om, set, k, ch, o);
+    collide_d2q5<Sys, T, R, MODE, KEEP>(sys, fin, plane, b, xinv, c, om, set, k, ch, o);
   } else {
     R U[P];
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-      const T* ptr = fin + b + (size_t)i * kBrick;
+      const T* ptr = fin + b + (size_t)i * plane;
       U[i] = KEEP ? Store<T>::ld_keep(ptr) : Store<T>::ld(ptr);
     }
     equilibria_d2q5<Sys, R, MODE>(sys, U, xinv, c, set, k, ch, o);
   }
+}
+
+// Post-collision components of cell (x, y) that MODE needs.
+template <class Sys, class T, class R, int MODE, int FORM, bool KEEP = false>
+__device__ __forceinline__ void cell_post(const Sys& sys, const T* __restrict__ fin, int x, int y, int nxb, R xinv,
+                                          R c, R om, int set, R k, R ch, R (&o)[5][Sys::P]) {
+  cell_post_at<Sys, T, R, MODE, FORM, KEEP>(sys, fin, kBrick, brick_base(x, y, nxb, StateForm<Sys, FORM>::NS), xinv,
+                                            c, om, set, k, ch, o);
 }
 
 // A node on a characteristic (non-periodic) face: the step writes it from the
@@ -506,15 +529,29 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
   R* ringL = rb2 + 3 * P * TX;           // [P][TY]     f*_1 at x0 - 1, by tile row
   R* ringR = ringL + P * TY;             // [P][TY]     f*_2 at x0 + w
 
-  // x ring, read up front with the L2 keep policy (as in the march above);
-  // the loops stay rolled so that the split is not copied
+  // x ring, read up front with the L2 keep policy (as in the march above):
+  // from the halo of the neighbouring tiles when the last step wrote it (the
+  // left ring is the left neighbour's last column, the right ring the right
+  // neighbour's first), else from the bricks.  The loops stay rolled so that
+  // the split is not copied.
+  const T* __restrict__ hin = a.halo_in();
+  T* __restrict__ hout = a.halo_out();
+  const int nbx = (nx + TX - 1) / TX;
 #pragma unroll 1
   for (int t = tx; t < 2 * h; t += blockDim.x) {
     const int side = t >= h;
     const int r = side ? t - h : t;
-    const int xr = side ? (x0 + w) % nx : (x0 - 1 + nx) % nx;
+    const T* src = fin;
+    size_t plane = kBrick, b;
+    if (hin) {
+      src = hin;
+      plane = 1;
+      b = halo_index(side ? (bx + 1) % nbx : (bx - 1 + nbx) % nbx, side ? 0 : 1, y0 + r, ny, NS);
+    } else {
+      b = brick_base(side ? (x0 + w) % nx : (x0 - 1 + nx) % nx, y0 + r, nxb, NS);
+    }
     R o[5][P];
-    cell_post<Sys, T, R, C_QX, FORM, true>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
+    cell_post_at<Sys, T, R, C_QX, FORM, true>(sys, src, plane, b, xinv, c, om, set, kk, ch, o);
     R* dst = side ? ringR : ringL;
 #pragma unroll
     for (int i = 0; i < P; ++i) dst[i * TY + r] = side ? o[1][i] : o[0][i];
@@ -557,6 +594,9 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
         const size_t base = brick_base(x, j, nxb, NS);
         const int rt = j - y0;
         const R* bp = beh + (r & 1) * P * TX;          // behind component of R_{r-2}
+        // the tile's edge columns also go to the halo of f^{n+1}
+        T* const h0 = hout && tx == 0 ? hout + halo_index(bx, 0, j, ny, NS) : nullptr;
+        T* const h1 = hout && tx == w - 1 ? hout + halo_index(bx, 1, j, ny, NS) : nullptr;
         R U[P];
 #pragma unroll
         for (int i = 0; i < P; ++i) {
@@ -573,12 +613,16 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
               Store<T>::st(fout + (size_t)(q * P + i) * kBrick + base, g[q]);
+              if (h0) Store<T>::st(h0 + q * P + i, g[q]);
+              if (h1) Store<T>::st(h1 + q * P + i, g[q]);
               acc += round_store(g[q], tp);
             }
             U[i] = acc;
           } else {
             const R u = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];
             Store<T>::st(fout + (size_t)i * kBrick + base, u);
+            if (h0) Store<T>::st(h0 + i, u);
+            if (h1) Store<T>::st(h1 + i, u);
             U[i] = round_store(u, tp);
           }
         }
@@ -621,11 +665,15 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
     // t_end already reached: this launch is a no-op that keeps the ping-pong
     // consistent (f^{n+1} = f^n, same control words).
     const int w = min(TX, a.nx - x0), h = min(TY, a.ny - y0);
+    T* const hout = Sys::P > 4 ? a.halo_out() : nullptr;   // the long-split march's halo
     if (tx < w)
       for (int r = 0; r < h; ++r)
         for (int i = 0; i < NS; ++i) {
           const size_t o = brick_base(x0 + tx, y0 + r, a.pitch / kBrick, NS) + (size_t)i * kBrick;
-          a.dst()[o] = a.src()[o];
+          const T v = a.src()[o];
+          a.dst()[o] = v;
+          if (hout && tx == 0) hout[halo_index(bx, 0, y0 + r, a.ny, NS) + i] = v;
+          if (hout && tx == w - 1) hout[halo_index(bx, 1, y0 + r, a.ny, NS) + i] = v;
         }
     if (bx == 0 && by == 0 && tx == 0) {
       const int s1 = (a.slot + 1) % 3, s2 = (a.slot + 2) % 3;

@@ -69,7 +69,37 @@ void free_sim(vklb_sim* s) {
   free_on(s->dvec, s->stream);
   free_on(s->stage, s->stream);
   free_on(s->ub, s->stream);
+  free_on(s->hl[0], s->stream);
+  free_on(s->hl[1], s->stream);
   delete s;
+}
+
+// Halo of the long-split march (2D systems with p > 4): two buffers of the
+// tiles' first and last columns, sized for the current tile width; any change
+// of the tiling or the form invalidates it until the next step writes it.
+int halo_fit(vklb_sim* s) {
+  s->hl_ok = 0;
+  if (s->dim != 2 || s->P <= 4) return VKLB_OK;
+  const size_t nbx = (size_t)((s->nx + s->tile_x - 1) / s->tile_x);
+  const size_t need = nbx * 2 * (size_t)s->ny * (size_t)s->QS * s->P * s->store_bytes;
+  if (need > s->hl_bytes) {
+    free_on(s->hl[0], s->stream);
+    free_on(s->hl[1], s->stream);
+    s->hl[0] = s->hl[1] = nullptr;
+    s->hl_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&s->hl[0], need, s->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&s->hl[1], need, s->stream);
+    if (e != cudaSuccess) {
+      free_on(s->hl[0], s->stream);
+      free_on(s->hl[1], s->stream);
+      s->hl[0] = s->hl[1] = nullptr;
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? VKLB_ERR_NOMEM : VKLB_ERR_CUDA;
+    }
+    s->hl_bytes = need;
+  }
+  s->hl_tx = s->tile_x;
+  return VKLB_OK;
 }
 
 const uint32_t kMagic = 0x564b4c42u;  // "VKLB"
@@ -231,6 +261,10 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->cby = dim == 2 && bc->lo[1] == VKLB_BC_CHARACTERISTIC;
   s->nb = dim == 2 ? char_face_nodes((int)nx, (int)ny, s->cbx, s->cby) : 0;
   s->ub = nullptr;
+  s->hl[0] = s->hl[1] = nullptr;
+  s->hl_bytes = 0;
+  s->hl_tx = 0;
+  s->hl_ok = 0;
   s->stream = (cudaStream_t)cuda_stream;
   s->tile_x = 64;
   s->tile_y = 16;
@@ -268,6 +302,10 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
       s->tile_y = ty;
     }
   }
+  if (int hs = halo_fit(s)) {
+    free_sim(s);
+    return hs;
+  }
   *out = s;
   return VKLB_OK;
 }
@@ -289,6 +327,7 @@ int vklb_set_state(vklb_sim* s, const double* U, int32_t on_device) {
   if ((st = cuda_status(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), s->stream)))) return st;
   s->cur = 0;
   s->launched = 0;
+  s->hl_ok = 0;
   if ((st = s->ops->init(s, s->stage))) return st;
   if (!on_device) {
     // the caller may reuse U as soon as we return
@@ -308,8 +347,10 @@ int vklb_set_tiling(vklb_sim* s, int32_t tx, int32_t ty) {
   }
   if (tx < 32 || tx > 256 || (tx % 32) != 0 || ty < 1 || ty > 256) return VKLB_ERR_ARG;
   if (s->ops->smem(kernel_variant(s), s->P, tx, ty, s->stages) > 200 * 1024) return VKLB_ERR_ARG;
+  const int old_tx = s->tile_x;
   s->tile_x = tx;
   s->tile_y = ty;
+  if (tx != old_tx) return halo_fit(s);
   return VKLB_OK;
 }
 
@@ -323,6 +364,7 @@ int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
   if (s->ops->smem(variant, s->P, s->tile_x, s->tile_y, stages) > 200 * 1024) return VKLB_ERR_ARG;
   s->variant = variant;
   s->stages = stages;
+  s->hl_ok = 0;
   return VKLB_OK;
 }
 
@@ -362,7 +404,7 @@ int vklb_set_form(vklb_sim* s, int32_t form) {
     s->tile_x = 128;
     s->tile_y = ty;
   }
-  return VKLB_OK;
+  return halo_fit(s);
 }
 
 int vklb_step(vklb_sim* s, int64_t n) {
@@ -482,7 +524,10 @@ int vklb_device_state(const vklb_sim* s, void** f_dev) {
 int vklb_poison_next(vklb_sim* s) {
   if (!s) return VKLB_ERR_ARG;
   const size_t bytes = (size_t)s->QS * s->P * s->pitch * s->ny * s->store_bytes;
-  return cuda_status(cudaMemsetAsync(s->f[s->cur ^ 1], 0xFF, bytes, s->stream));
+  int st = cuda_status(cudaMemsetAsync(s->f[s->cur ^ 1], 0xFF, bytes, s->stream));
+  if (st == VKLB_OK && s->hl[s->cur ^ 1])   // and the halo the next step writes
+    st = cuda_status(cudaMemsetAsync(s->hl[s->cur ^ 1], 0xFF, s->hl_bytes, s->stream));
+  return st;
 }
 
 int vklb_state_bytes(const vklb_sim* s, size_t* bytes) {
@@ -522,6 +567,7 @@ int vklb_put_state(vklb_sim* s, const void* blob, size_t bytes) {
   if (st) return st;
   s->cur = 0;
   s->launched = hdr.launched;
+  s->hl_ok = 0;
   const size_t fb = (size_t)s->QS * s->P * s->pitch * s->ny * s->store_bytes;
   if ((st = cuda_status(cudaMemcpyAsync(s->f[0], p + sizeof(Ctl), fb, cudaMemcpyHostToDevice, s->stream)))) return st;
   if ((st = cuda_status(cudaStreamSynchronize(s->stream)))) return st;

@@ -37,14 +37,16 @@ FAMILY = {
 FIELDS = {"swe": 3, "euler": 4, "mhd_glm": 9}
 
 
-def device_bytes(system, n, precision="fp32", form="moments"):
+def device_bytes(system, n, precision="fp32", form="moments", tile_x=128):
     """Device memory one simulation holds: two state buffers (p or 5p values a
-    cell) plus the double staging array used by set_state / moments."""
+    cell), the double staging array used by set_state / moments, and for
+    MHD-GLM the two buffers of its tiles' edge columns (tiles tile_x wide)."""
     s = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
     pitch = ((n + 31) // 32) * 32
     p = FIELDS[system]
     q = 1 if form == "moments" else 5
-    return 2 * q * p * pitch * n * s + p * n * n * 8
+    halo = 2 * (-(-n // tile_x)) * 2 * n * q * p * s if system == "mhd_glm" else 0
+    return 2 * q * p * pitch * n * s + p * n * n * 8 + halo
 
 
 @dataclass

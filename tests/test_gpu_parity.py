@@ -89,8 +89,8 @@ def test_euler_vortex_bf16_storage(vk):
     L1) of the oracle with the same storage rounding after 100 steps (measured
     0.96 u), whatever the tiling, while the FP64 oracle without it drifts away
     linearly (measured 4.6e-2): the storage model explains at least 3/4 of the
-    departure (measured: 0.88 or more).  The residue is near-tie roundings that FP32 and
-    FP64 arithmetic decide differently."""
+    departure (measured: 0.88 or more).  The residue is near-tie roundings that
+    FP32 and FP64 arithmetic decide differently."""
     n = (48, 40)
     lo, hi = _box(n, 10.0)
     U0 = _vortex(*n)
@@ -452,3 +452,36 @@ def test_every_cell_written_each_step(vk, system, variant, tile, bc):
     ref.run(6)
     assert max_rel(sim.moments(), ref.moments()).max() <= 1e-11
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "bf16"])
+@pytest.mark.parametrize("form", ["distributions", "moments"])
+@pytest.mark.parametrize("tile", [(32, 8), (64, 5), (128, 16)])
+def test_mhd_ring_from_halo_equals_ring_from_bricks(vk, precision, form, tile):
+    """The long-split march (MHD-GLM) reads its x ring from the halo of tile
+    edge columns that the previous step wrote.  A run that invalidates the halo
+    before every step (set_variant, so the ring comes from the bricks) gives
+    the same bits: the halo holds exactly the stored f^n of those columns, for
+    ragged grids (100 = 3 x 32 + 4 columns, 37 rows) and tile widths, in both
+    state forms; with NaN in the buffers each step writes, every cell and
+    every halo entry the next step reads is written."""
+    n = (100, 37)
+    U0 = np.ascontiguousarray(inputs.orszag_tang(100)[:, :37, :])
+    lo, hi = _box(n, 2 * np.pi)
+    sims = []
+    for _ in range(2):
+        s = vk.Sim("mhd_glm", n, lo, hi, precision=precision, omega=1.0, cfl=0.3, gamma=5 / 3, form=form)
+        s.set_tiling(*tile)
+        s.set_state(U0)
+        sims.append(s)
+    a, b = sims
+    for k in range(12):
+        a.poison_next()
+        a.step(1)
+        b.set_variant(0, 4)
+        b.step(1)
+    ua, ub = a.moments(), b.moments()
+    assert np.all(np.isfinite(ua))
+    assert np.array_equal(ua, ub)
+    a.close()
+    b.close()
