@@ -88,17 +88,22 @@ typedef struct {
   double hi[2];
 } vklb_grid;
 
-/* Boundary kinds per side: periodic (Eq. 37) or characteristic /
- * non-reflecting (Eqs. 33-36).  1D: both ends alike.  2D (D2Q5): per axis,
- * lo[i] == hi[i]; a characteristic axis applies the 1D construction of
+/* Boundary kinds per side: periodic (Eq. 37), characteristic /
+ * non-reflecting (Eqs. 33-36), or transmissive (zero-order extrapolation, the
+ * textbook outflow condition: a boundary node takes U_b^{n+1} = U^{n+1} of the
+ * node one cell inwards along each non-periodic face it lies on, a 2D corner
+ * its diagonal neighbour, and f^eq(U_b^{n+1}) with xi_{n+1} as its
+ * distributions).  1D: both ends alike.  2D (D2Q5): per axis, lo[i] == hi[i],
+ * and the non-periodic axes all of one kind (VKLB_ERR_ARG otherwise); a
+ * characteristic axis applies the 1D construction of
  * Eqs. 33-35 along the normal of its two faces (the paper writes it for D1Q3
  * only): a boundary node takes U_b^{n+1} = U_b^n - (1/xi_n) P Lambda^out P^-1 D U^n
  * with the one-sided difference D towards the interior, a corner sums its two
  * faces, and its distributions become f^eq(U_b^{n+1}) with xi_{n+1} (Eq. 36).
- * 2D characteristic faces are built for shallow water, Euler and advection
- * (VKLB_ERR_UNSUPPORTED for MHD-GLM), with the plain step kernel in the
- * distribution form, outside batches; they need 3 or more cells across. */
-typedef enum { VKLB_BC_PERIODIC = 0, VKLB_BC_CHARACTERISTIC = 1 } vklb_bc_kind;
+ * Non-periodic 2D faces (either kind) are built for shallow water, Euler and
+ * advection (VKLB_ERR_UNSUPPORTED for MHD-GLM), with the plain step kernel in
+ * the distribution form, outside batches; they need 3 or more cells across. */
+typedef enum { VKLB_BC_PERIODIC = 0, VKLB_BC_CHARACTERISTIC = 1, VKLB_BC_TRANSMISSIVE = 2 } vklb_bc_kind;
 typedef struct {
   int32_t lo[2];
   int32_t hi[2];
@@ -174,6 +179,27 @@ typedef struct {
 int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid,
                 const vklb_bc* bc, const vklb_weight* weight, double dt,
                 int32_t precision, void* cuda_stream, vklb_sim** out);
+
+/* Like vklb_create, but the two distribution buffers are the caller's: device
+ * allocations (for example framework tensors) that the simulation borrows and
+ * never frees, f_buf[0] and f_buf[1], each of buf_bytes >= vklb_buffer_bytes
+ * bytes, 256-byte aligned, not overlapping, and alive until vklb_destroy
+ * returns.  The simulation writes zeros into both when it is created and then
+ * owns their contents (layout: vklb_device_state).  Everything else is
+ * allocated and owned as by vklb_create.  VKLB_ERR_ARG for a null, misaligned,
+ * overlapping or short buffer (checked before any device call);
+ * vklb_set_form then returns VKLB_ERR_UNSUPPORTED (the moment form needs
+ * buffers of another size). */
+int vklb_create_borrowed(const vklb_system* sys, int32_t lattice, const vklb_grid* grid,
+                         const vklb_bc* bc, const vklb_weight* weight, double dt,
+                         int32_t precision, void* cuda_stream, void* const f_buf[2],
+                         size_t buf_bytes, vklb_sim** out);
+
+/* Bytes of one distribution buffer of a simulation of this system kind,
+ * lattice, grid and precision: q * p values a cell of the padded grid
+ * (rows padded to whole 32-cell bricks in 2D) times the store size. */
+int vklb_buffer_bytes(int32_t system_kind, int32_t lattice, const vklb_grid* grid, int32_t precision,
+                      size_t* bytes);
 
 /* Set U(x, 0) (layout above; host pointer if on_device == 0, else device).
  * Initialises as Fig. 5: xi_0 from Eq. (29) over U (and c_h for MHD-GLM), then

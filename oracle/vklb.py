@@ -47,6 +47,13 @@ Readings of the paper taken here, where it is silent or ambiguous:
       distributions are f^eq(U_b^{n+1}) with xi_{n+1} (R11), and xi_{n+1}
       includes the boundary states.  Streaming wraps as on a periodic grid;
       what wraps lands only in boundary nodes, which are overwritten.
+  R21 transmissive boundaries (zero-order extrapolation, the textbook outflow
+      condition; the paper's own open boundary is the characteristic one):
+      after streaming, a boundary node takes U_b^{n+1} = U^{n+1} of the node
+      one cell inwards along every non-periodic face it lies on (a 2D corner
+      takes its diagonal neighbour), and its distributions are f^eq(U_b^{n+1})
+      with xi_{n+1} as in R11.  In 2D every non-periodic axis takes the same
+      kind (characteristic or transmissive).
   R20 storage="bf16" models distributions kept in bfloat16 (the precision form
       of the GPU path; the paper computes in FP64 throughout): every stored f
       (the initial f^eq, and after each step the streamed f including the
@@ -134,8 +141,8 @@ class Sim:
 
     system   : an ``oracle.systems`` object (its dim selects D1Q3 or D2Q5)
     n        : (nx,) or (nx, ny) cells;  lo, hi: domain corners
-    bc       : "periodic" or "characteristic" (all sides), or in 2D a pair
-               (x axis, y axis) of those
+    bc       : "periodic", "characteristic" or "transmissive" (all sides), or
+               in 2D a pair (x axis, y axis) of those (R19, R21)
     set_kind : "weighted" (c, k), "centered" (c = 1/Q, F/2), "discontinuous"
     omega    : relaxation parameter, 0 < omega <= 2 (Sec. 2.3)
     nu       : CFL number (Eq. 29);  dt > 0 fixes xi = dx / dt instead
@@ -158,10 +165,13 @@ class Sim:
         self.dx = float(dxs[0])
         self.lo, self.hi = lo, hi
         axes = (bc,) * self.dim if isinstance(bc, str) else tuple(bc)
-        if len(axes) != self.dim or any(b not in ("periodic", "characteristic") for b in axes):
+        if len(axes) != self.dim or any(b not in ("periodic", "characteristic", "transmissive") for b in axes):
             raise ValueError(bc)
+        open_kinds = {b for b in axes if b != "periodic"}
+        if len(open_kinds) > 1:
+            raise ValueError("the non-periodic axes take one kind (R21)")
         self.bc_axes = axes
-        self.bc = bc if isinstance(bc, str) else ("characteristic" if "characteristic" in axes else "periodic")
+        self.bc = open_kinds.pop() if open_kinds else "periodic"
         self.set_kind = set_kind
         if set_kind == "centered":
             c = 1.0 / 3.0 if self.dim == 1 else 1.0 / 5.0
@@ -276,11 +286,24 @@ class Sim:
         """2D: True at the nodes of the non-periodic faces ([ny, nx])."""
         ny, nx = self.n[1], self.n[0]
         m = np.zeros((ny, nx), dtype=bool)
-        if self.bc_axes[0] == "characteristic":
+        if self.bc_axes[0] != "periodic":
             m[:, 0] = m[:, -1] = True
-        if self.bc_axes[1] == "characteristic":
+        if self.bc_axes[1] != "periodic":
             m[0, :] = m[-1, :] = True
         return m
+
+    def transmissive_2d(self, Unew):
+        """R21: U_b^{n+1} = U^{n+1} of the node one cell inwards along every
+        non-periodic face the node lies on ([p, ny, nx]; interior nodes keep
+        their own value)."""
+        ny, nx = self.n[1], self.n[0]
+        xi = np.arange(nx)
+        yi = np.arange(ny)
+        if self.bc_axes[0] != "periodic":
+            xi[0], xi[-1] = 1, nx - 2
+        if self.bc_axes[1] != "periodic":
+            yi[0], yi[-1] = 1, ny - 2
+        return Unew[:, yi[:, None], xi[None, :]]
 
     def char_bc_2d(self, Uold, xi_n):
         """R19: Eqs. (33)-(35) along the normal of every non-periodic face, from
@@ -335,17 +358,23 @@ class Sim:
             ubl, ubr = self.char_bc(U, Un, xi)                # Eqs. (33)-(35)
             Un[:, 0] = ubl
             Un[:, -1] = ubr
+        elif self.bc == "transmissive" and self.dim == 1:
+            Un[:, 0] = Un[:, 1]                               # R21
+            Un[:, -1] = Un[:, -2]
         elif self.bc == "characteristic":
             mask = self.boundary_mask()
             Un[:, mask] = self.char_bc_2d(U, xi)[:, mask]     # R19
+        elif self.bc == "transmissive":
+            mask = self.boundary_mask()
+            Un[:, mask] = self.transmissive_2d(Un)[:, mask]   # R21
         self.refresh_ch(Un)
         xin = self.cfl_xi(Un)                                 # Eq. (29)
-        if self.bc == "characteristic" and self.dim == 1:
+        if self.bc != "periodic" and self.dim == 1:
             fb = self.equilibrium(np.stack([Un[:, 0], Un[:, -1]], axis=1), xin,
                                   self.max_lambda(Un))
             fn[:, :, 0] = fb[:, :, 0]                         # Eq. (36), R11
             fn[:, :, -1] = fb[:, :, 1]
-        elif self.bc == "characteristic":
+        elif self.bc != "periodic":
             fb = self.equilibrium(Un[:, mask], xin, self.max_lambda(Un))
             fn[:, :, mask] = fb                               # Eq. (36), R11, R19
         self.f = self.store(fn)                               # R20 (boundary nodes)

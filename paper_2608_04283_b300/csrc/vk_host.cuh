@@ -48,11 +48,13 @@ struct vklb_sim {
   double c, k, omega, cfl, fixed_xi;
   double inv_nu;   // xi = inv_nu max|lambda|: 1 / cfl, or sqrt(3/2) / eta
   int bc_lo, bc_hi;
-  int cbx, cby;            // 2D: characteristic faces normal to x / y (else periodic)
+  int cbx, cby;            // 2D: non-periodic faces normal to x / y
+  int btr;                 // 2D: those faces are transmissive (else characteristic)
   int nb;                  // 2D: boundary nodes of those faces (0: fully periodic)
   void* ub;                // 2D: [p][nb] boundary states U_b^{n+1} between the two boundary passes
   cudaStream_t stream;
   void* f[2];
+  bool f_borrowed;         // f[] belong to the caller (vklb_create_borrowed): never freed here
   int cur;                 // f[cur] holds the current state
   long long launched;      // step launches so far (slot = launched % 3)
   Ctl* ctl;
@@ -140,6 +142,7 @@ StepArgs<T> make_args(const vklb_sim* s, double t_end) {
   a.bc_hi = s->bc_hi;
   a.cbx = s->cbx;
   a.cby = s->cby;
+  a.btr = s->btr;
   a.ctl = s->ctl;
   a.slot = (int)(s->launched % 3);
   a.sp = s->sp;

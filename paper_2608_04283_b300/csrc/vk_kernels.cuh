@@ -63,8 +63,9 @@ struct StepArgs {
   double dx, c, omega, k, inv_nu, fixed_xi, t_end, ch_factor;
   int set;
   int anorm;       // alpha's normaliser: 0 per cell and direction, 1 grid-wide max |lambda| of the step
-  int bc_lo, bc_hi;  // 1D: 0 periodic, 1 characteristic
-  int cbx, cby;      // 2D: characteristic boundaries on the x (y) faces, else periodic
+  int bc_lo, bc_hi;  // 1D: 0 periodic, 1 characteristic, 2 transmissive
+  int cbx, cby;      // 2D: non-periodic boundaries on the x (y) faces
+  int btr;           // 2D: those faces are transmissive (else characteristic)
   Ctl* ctl;
   int slot;        // n % 3
   SysParams sp;
@@ -1093,7 +1094,19 @@ __global__ void char2d_state_kernel(StepArgs<T> a, R* __restrict__ Ub, int nb) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   R m1 = R(0), m2 = R(0);
   bool bad = false;
-  if (id < nb) {
+  if (id < nb && a.btr) {
+    // transmissive faces: U_b^{n+1} = U^{n+1} of the node one cell inwards along
+    // each face it lies on (a corner: the diagonal one), from f^{n+1}
+    int x, y;
+    char_face_node(id, nx, ny, a.cbx, a.cby, x, y);
+    const int xi = a.cbx && x == 0 ? 1 : (a.cbx && x == nx - 1 ? nx - 2 : x);
+    const int yi = a.cby && y == 0 ? 1 : (a.cby && y == ny - 1 ? ny - 2 : y);
+    R U[P];
+    load_U<Sys, T, R>(a.dst(), xi, yi, nxb, U);
+#pragma unroll
+    for (int i = 0; i < P; ++i) Ub[(size_t)i * nb + id] = U[i];
+    bad = !sys.epilogue(U, m1, m2);
+  } else if (id < nb) {
     int x, y;
     char_face_node(id, nx, ny, a.cbx, a.cby, x, y);
     R U[P], rhs[P];
@@ -1176,7 +1189,9 @@ __global__ void step1d_kernel(StepArgs<T> a, int nsteps) {
   Sys sys = make_sys<Sys>(a.sp);
   const int nx = a.nx;
   const size_t plane = (size_t)nx;
-  const bool cl = a.bc_lo == 1, chi = a.bc_hi == 1;
+  const bool cl = a.bc_lo != 0, chi = a.bc_hi != 0;        // non-periodic ends
+  const bool ccl = a.bc_lo == 1, cchi = a.bc_hi == 1;      // characteristic ones
+  const bool trans = (cl && !ccl) || (chi && !cchi);      // a transmissive end
   __shared__ R Ub[2][P];
   __shared__ double red[32];
   int par = a.parity, slot = a.slot;
@@ -1213,7 +1228,7 @@ __global__ void step1d_kernel(StepArgs<T> a, int nsteps) {
       }
     }
     // characteristic boundaries (Eqs. 33-35): U_b^{n+1} from U^n at x_b and its neighbour
-    if (threadIdx.x < 2 && ((threadIdx.x == 0 && cl) || (threadIdx.x == 1 && chi))) {
+    if (threadIdx.x < 2 && ((threadIdx.x == 0 && ccl) || (threadIdx.x == 1 && cchi))) {
       const int side = threadIdx.x;
       const int ib = side == 0 ? 0 : nx - 1, in = side == 0 ? 1 : nx - 2;
       R Ubv[P], Un[P], dU[P], rhs[P];
@@ -1232,6 +1247,19 @@ __global__ void step1d_kernel(StepArgs<T> a, int nsteps) {
       for (int s = 0; s < P; ++s) Ub[side][s] = Ubv[s] - rhs[s] * xinv;
     }
     __syncthreads();
+    // transmissive ends: U_b^{n+1} = U^{n+1} of the neighbour, now streamed
+    if (trans) {
+      if (threadIdx.x < 2 && ((threadIdx.x == 0 && cl && !ccl) || (threadIdx.x == 1 && chi && !cchi))) {
+        const int side = threadIdx.x;
+        const int in = side == 0 ? 1 : nx - 2;
+#pragma unroll
+        for (int s = 0; s < P; ++s)
+          Ub[side][s] = Store<T>::ld(fout + (size_t)(0 * P + s) * plane + in) +
+                        Store<T>::ld(fout + (size_t)(1 * P + s) * plane + in) +
+                        Store<T>::ld(fout + (size_t)(2 * P + s) * plane + in);
+      }
+      __syncthreads();
+    }
     // moments of f^{n+1} (Eq. 3) and the CFL max (Eq. 29)
     double m1 = 0.0;
     bool bad = false;

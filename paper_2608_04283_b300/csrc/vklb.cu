@@ -62,8 +62,10 @@ void free_on(void* p, cudaStream_t st) {
 }
 void free_sim(vklb_sim* s) {
   if (!s) return;
-  free_on(s->f[0], s->stream);
-  free_on(s->f[1], s->stream);
+  if (!s->f_borrowed) {
+    free_on(s->f[0], s->stream);
+    free_on(s->f[1], s->stream);
+  }
   free_on(s->ctl, s->stream);
   free_on(s->part, s->stream);
   free_on(s->dvec, s->stream);
@@ -180,8 +182,50 @@ static int wave_fit_rows(vklb_sim* s, int tx, int* ty_out) {
   return VKLB_OK;
 }
 
+// Bytes of one distribution buffer (q p values a cell on the padded grid).
+static int64_t buffer_bytes_of(int32_t kind, int32_t lattice, const vklb_grid* grid, int32_t precision) {
+  const int dim = grid->dim;
+  if (!((lattice == VKLB_D1Q3 && dim == 1) || (lattice == VKLB_D2Q5 && dim == 2))) return -1;
+  if (kind < VKLB_ADVECT || kind > VKLB_MHD_GLM || precision < VKLB_FP64 || precision > VKLB_BF16_STORE) return -1;
+  const int64_t nx = grid->n[0], ny = dim == 2 ? grid->n[1] : 1;
+  if (nx < 1 || ny < 1 || nx > (1 << 30) || ny > (1 << 30)) return -1;
+  const int64_t pitch = dim == 2 ? ((nx + 31) / 32) * 32 : nx;
+  const int64_t sb = precision == VKLB_FP64 ? 8 : (precision == VKLB_FP32 ? 4 : 2);
+  return (int64_t)(dim == 1 ? 3 : 5) * fields_of(kind, dim) * pitch * ny * sb;
+}
+
+int vklb_buffer_bytes(int32_t kind, int32_t lattice, const vklb_grid* grid, int32_t precision, size_t* bytes) {
+  if (!grid || !bytes) return VKLB_ERR_ARG;
+  const int64_t b = buffer_bytes_of(kind, lattice, grid, precision);
+  if (b < 0) return VKLB_ERR_ARG;
+  *bytes = (size_t)b;
+  return VKLB_OK;
+}
+
+static int create_impl(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, const vklb_bc* bc,
+                       const vklb_weight* weight, double dt, int32_t precision, void* cuda_stream,
+                       void* const* f_buf, size_t buf_bytes, vklb_sim** out);
+
 int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, const vklb_bc* bc,
                 const vklb_weight* weight, double dt, int32_t precision, void* cuda_stream, vklb_sim** out) {
+  return create_impl(sys, lattice, grid, bc, weight, dt, precision, cuda_stream, nullptr, 0, out);
+}
+
+int vklb_create_borrowed(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, const vklb_bc* bc,
+                         const vklb_weight* weight, double dt, int32_t precision, void* cuda_stream,
+                         void* const f_buf[2], size_t buf_bytes, vklb_sim** out) {
+  if (!f_buf || !f_buf[0] || !f_buf[1] || !grid || !sys || !out) return VKLB_ERR_ARG;
+  const int64_t need = buffer_bytes_of(sys->kind, lattice, grid, precision);
+  if (need < 0 || buf_bytes < (size_t)need) return VKLB_ERR_ARG;
+  const uintptr_t a = (uintptr_t)f_buf[0], b = (uintptr_t)f_buf[1];
+  if ((a % 256) != 0 || (b % 256) != 0) return VKLB_ERR_ARG;          // whole bricks on 256-byte lines
+  if ((a < b ? b - a : a - b) < (uintptr_t)need) return VKLB_ERR_ARG;   // the two must not overlap
+  return create_impl(sys, lattice, grid, bc, weight, dt, precision, cuda_stream, f_buf, buf_bytes, out);
+}
+
+static int create_impl(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, const vklb_bc* bc,
+                       const vklb_weight* weight, double dt, int32_t precision, void* cuda_stream,
+                       void* const* f_buf, size_t buf_bytes, vklb_sim** out) {
   if (!sys || !grid || !bc || !weight || !out) return VKLB_ERR_ARG;
   *out = nullptr;
   const int dim = grid->dim;
@@ -202,22 +246,22 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
     const double dy = (grid->hi[1] - grid->lo[1]) / (double)ny;
     if (!(fabs(dx - dy) <= 1e-12 * dx)) return VKLB_ERR_ARG;                  // Sec. 3.4
   }
-  for (int i = 0; i < dim; ++i)
-    if (bc->lo[i] != bc->hi[i] && dim == 2) return VKLB_ERR_ARG;
-  for (int i = 0; i < dim; ++i)
-    if (bc->lo[i] != VKLB_BC_PERIODIC && bc->lo[i] != VKLB_BC_CHARACTERISTIC) return VKLB_ERR_ARG;
-  // 2D characteristic faces: shallow water, Euler and advection (closed-form
-  // outgoing parts); at least 3 cells across a characteristic axis
-  const bool char2d = dim == 2 && (bc->lo[0] == VKLB_BC_CHARACTERISTIC || bc->lo[1] == VKLB_BC_CHARACTERISTIC);
-  if (char2d && sys->kind == VKLB_MHD_GLM) return VKLB_ERR_UNSUPPORTED;
-  if (dim == 1 && ((bc->lo[0] != VKLB_BC_PERIODIC && bc->lo[0] != VKLB_BC_CHARACTERISTIC) ||
-                   (bc->hi[0] != VKLB_BC_PERIODIC && bc->hi[0] != VKLB_BC_CHARACTERISTIC)))
+  // one kind per axis (both ends alike), each periodic, characteristic or
+  // transmissive; the non-periodic axes of a 2D grid all of one kind
+  for (int i = 0; i < dim; ++i) {
+    if (bc->lo[i] != bc->hi[i]) return VKLB_ERR_ARG;
+    if (bc->lo[i] < VKLB_BC_PERIODIC || bc->lo[i] > VKLB_BC_TRANSMISSIVE) return VKLB_ERR_ARG;
+  }
+  if (dim == 2 && bc->lo[0] != VKLB_BC_PERIODIC && bc->lo[1] != VKLB_BC_PERIODIC && bc->lo[0] != bc->lo[1])
     return VKLB_ERR_ARG;
-  if (dim == 1 && (bc->lo[0] == VKLB_BC_PERIODIC) != (bc->hi[0] == VKLB_BC_PERIODIC)) return VKLB_ERR_ARG;
+  // non-periodic 2D faces: shallow water, Euler and advection; at least 3
+  // cells across a non-periodic axis
+  const bool open2d = dim == 2 && (bc->lo[0] != VKLB_BC_PERIODIC || bc->lo[1] != VKLB_BC_PERIODIC);
+  if (open2d && sys->kind == VKLB_MHD_GLM) return VKLB_ERR_UNSUPPORTED;
   const Ops* ops = pick_ops(sys->kind, dim, precision);
   if (!ops) return VKLB_ERR_UNSUPPORTED;
-  if (char2d && ((bc->lo[0] == VKLB_BC_CHARACTERISTIC && grid->n[0] < 3) ||
-                 (bc->lo[1] == VKLB_BC_CHARACTERISTIC && grid->n[1] < 3)))
+  if (open2d && ((bc->lo[0] != VKLB_BC_PERIODIC && grid->n[0] < 3) ||
+                 (bc->lo[1] != VKLB_BC_PERIODIC && grid->n[1] < 3)))
     return VKLB_ERR_ARG;
   if ((sys->kind == VKLB_EULER || sys->kind == VKLB_MHD_GLM) && !(sys->gamma > 1.0)) return VKLB_ERR_ARG;
   if (sys->kind == VKLB_SWE && !(sys->g > 0.0)) return VKLB_ERR_ARG;
@@ -257,8 +301,9 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   s->fixed_xi = dt > 0.0 ? dx / dt : 0.0;
   s->bc_lo = bc->lo[0];
   s->bc_hi = bc->hi[0];
-  s->cbx = dim == 2 && bc->lo[0] == VKLB_BC_CHARACTERISTIC;
-  s->cby = dim == 2 && bc->lo[1] == VKLB_BC_CHARACTERISTIC;
+  s->cbx = dim == 2 && bc->lo[0] != VKLB_BC_PERIODIC;
+  s->cby = dim == 2 && bc->lo[1] != VKLB_BC_PERIODIC;
+  s->btr = dim == 2 && (bc->lo[0] == VKLB_BC_TRANSMISSIVE || bc->lo[1] == VKLB_BC_TRANSMISSIVE);
   s->nb = dim == 2 ? char_face_nodes((int)nx, (int)ny, s->cbx, s->cby) : 0;
   s->ub = nullptr;
   s->hl[0] = s->hl[1] = nullptr;
@@ -276,8 +321,14 @@ int vklb_create(const vklb_system* sys, int32_t lattice, const vklb_grid* grid, 
   const size_t fbytes = (size_t)s->Q * s->P * (size_t)s->pitch * s->ny * s->store_bytes;
   cudaError_t e = cudaSuccess;
   cudaStream_t st = s->stream;
-  if ((e = cudaMallocAsync(&s->f[0], fbytes, st)) != cudaSuccess ||
-      (e = cudaMallocAsync(&s->f[1], fbytes, st)) != cudaSuccess ||
+  s->f_borrowed = f_buf != nullptr;
+  if (s->f_borrowed) {
+    s->f[0] = f_buf[0];
+    s->f[1] = f_buf[1];
+  }
+  (void)buf_bytes;
+  if ((!s->f_borrowed && (e = cudaMallocAsync(&s->f[0], fbytes, st)) != cudaSuccess) ||
+      (!s->f_borrowed && (e = cudaMallocAsync(&s->f[1], fbytes, st)) != cudaSuccess) ||
       (e = cudaMallocAsync((void**)&s->ctl, sizeof(Ctl), st)) != cudaSuccess ||
       (e = cudaMallocAsync((void**)&s->part, sizeof(double) * s->P * kRedBlocks, st)) != cudaSuccess ||
       (e = cudaMallocAsync((void**)&s->dvec, sizeof(double) * s->P, st)) != cudaSuccess ||
@@ -371,6 +422,7 @@ int vklb_set_variant(vklb_sim* s, int32_t variant, int32_t stages) {
 int vklb_set_form(vklb_sim* s, int32_t form) {
   if (!s || (form != 0 && form != 1)) return VKLB_ERR_ARG;
   if (form == s->form) return VKLB_OK;
+  if (s->f_borrowed) return VKLB_ERR_UNSUPPORTED;   // the caller's buffers keep their size
   if (form == 1 && s->dim != 2) return VKLB_ERR_UNSUPPORTED;
   if (form == 1 && s->nb > 0) return VKLB_ERR_UNSUPPORTED;
   if (form == 1 && s->omega != 1.0) return VKLB_ERR_ARG;   // f* = f^eq(U) holds at omega = 1 only

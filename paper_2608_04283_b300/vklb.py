@@ -23,7 +23,8 @@ OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_NONPHYSICAL, ERR_CFL, ERR_TIMEOUT, ERR_STA
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 ADVECT, SWE, EULER, MHD_GLM = 0, 1, 2, 3
 D1Q3, D2Q5 = 13, 25
-BC_PERIODIC, BC_CHARACTERISTIC = 0, 1
+BC_PERIODIC, BC_CHARACTERISTIC, BC_TRANSMISSIVE = 0, 1, 2
+BC_KIND = {"periodic": BC_PERIODIC, "characteristic": BC_CHARACTERISTIC, "transmissive": BC_TRANSMISSIVE}
 SET_WEIGHTED, SET_CENTERED, SET_DISCONTINUOUS = 0, 1, 2
 FP64, FP32, BF16_STORE = 0, 1, 2
 
@@ -64,6 +65,10 @@ _D = C.POINTER(C.c_double)
 _SIGS = {
     "vklb_create": (C.c_int, [C.POINTER(System), C.c_int32, C.POINTER(Grid), C.POINTER(BC), C.POINTER(Weight),
                               C.c_double, C.c_int32, _P, C.POINTER(_P)]),
+    "vklb_create_borrowed": (C.c_int, [C.POINTER(System), C.c_int32, C.POINTER(Grid), C.POINTER(BC),
+                                       C.POINTER(Weight), C.c_double, C.c_int32, _P, C.POINTER(_P), C.c_size_t,
+                                       C.POINTER(_P)]),
+    "vklb_buffer_bytes": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(Grid), C.c_int32, C.POINTER(C.c_size_t)]),
     "vklb_set_state": (C.c_int, [_P, _P, C.c_int32]),
     "vklb_set_tiling": (C.c_int, [_P, C.c_int32, C.c_int32]),
     "vklb_set_variant": (C.c_int, [_P, C.c_int32, C.c_int32]),
@@ -93,6 +98,18 @@ for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
     _fn.restype = _res
     _fn.argtypes = _args
+
+
+def buffer_bytes(system, n, precision="fp32"):
+    """Bytes of one distribution buffer (vklb_buffer_bytes) for Sim(buffers=...)."""
+    n = tuple(int(v) for v in n)
+    dim = len(n)
+    grid = Grid(dim, (C.c_int64 * 2)(n[0], n[1] if dim == 2 else 1), (C.c_double * 2)(0.0, 0.0),
+                (C.c_double * 2)(1.0, 1.0))
+    out = C.c_size_t()
+    _check(_lib.vklb_buffer_bytes(SYSTEM_KIND[system], D1Q3 if dim == 1 else D2Q5, C.byref(grid),
+                                  PRECISION[precision], C.byref(out)), "vklb_buffer_bytes")
+    return out.value
 
 
 class VKLBError(RuntimeError):
@@ -130,16 +147,19 @@ def _stream_handle(stream):
 class Sim:
     """One simulation (see vklb_create).  ``system`` in advection / swe / euler /
     mhd_glm; ``n`` = (nx,) or (nx, ny); ``lo``/``hi`` domain corners; ``bc``
-    "periodic" or "characteristic", or per axis in 2D, e.g. ("characteristic",
-    "periodic") (vklb_bc); ``form``
+    "periodic", "characteristic" or "transmissive", or per axis in 2D, e.g.
+    ("characteristic", "periodic") (vklb_bc); ``form``
     "moments" keeps U instead of f as the state (D2Q5, omega = 1; vklb_set_form);
     ``eta`` > 0 takes the subcharacteristic lattice speed of the centered set
     instead of the CFL rule (vklb_weight.eta); ``alpha_norm`` "global" (default) or
-    "local" places the sigmoid weight's normaliser (vklb_weight.alpha_norm)."""
+    "local" places the sigmoid weight's normaliser (vklb_weight.alpha_norm);
+    ``buffers`` = two contiguous CUDA tensors of at least buffer_bytes() bytes
+    each holds the distributions in the caller's memory (vklb_create_borrowed;
+    the tensors are kept referenced for the simulation's lifetime)."""
 
     def __init__(self, system, n, lo, hi, bc="periodic", set_kind="weighted", c=0.05, k=2.0, omega=1.0,
                  cfl=0.9, dt=0.0, precision="fp32", gamma=1.4, g=9.81, ch_factor=6.0, adv_speed=(1.0, 0.0),
-                 stream=None, form="distributions", eta=0.0, alpha_norm="global"):
+                 stream=None, form="distributions", eta=0.0, alpha_norm="global", buffers=None):
         n = tuple(int(v) for v in n)
         dim = len(n)
         lo = tuple(float(v) for v in np.atleast_1d(lo))
@@ -150,7 +170,7 @@ class Sim:
                     (C.c_double * 2)(lo[0], lo[1] if dim == 2 else 0.0),
                     (C.c_double * 2)(hi[0], hi[1] if dim == 2 else 1.0))
         axes = (bc,) * 2 if isinstance(bc, str) else tuple(bc) + (bc[-1],) * (2 - len(bc))
-        kinds = [BC_PERIODIC if b_ == "periodic" else BC_CHARACTERISTIC for b_ in axes]
+        kinds = [BC_KIND[b_] for b_ in axes]
         b = BC((C.c_int32 * 2)(*kinds), (C.c_int32 * 2)(*kinds))
         w = Weight(SET_KIND[set_kind], float(c), float(k), float(omega), float(cfl), float(eta),
                    ALPHA_NORM[alpha_norm])
@@ -158,9 +178,24 @@ class Sim:
         self.system, self.n, self.dim = system, n, dim
         self.precision = precision
         self._stream = stream
-        _check(_lib.vklb_create(C.byref(s), D1Q3 if dim == 1 else D2Q5, C.byref(grid), C.byref(b), C.byref(w),
-                                float(dt), PRECISION[precision], _stream_handle(stream), C.byref(self._h)),
-               "vklb_create")
+        lat = D1Q3 if dim == 1 else D2Q5
+        if buffers is None:
+            _check(_lib.vklb_create(C.byref(s), lat, C.byref(grid), C.byref(b), C.byref(w), float(dt),
+                                    PRECISION[precision], _stream_handle(stream), C.byref(self._h)), "vklb_create")
+        else:
+            # two caller-owned device buffers (torch CUDA tensors), borrowed for
+            # the simulation's lifetime
+            need = buffer_bytes(system, n, precision)
+            for t in buffers:
+                if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+                    raise ValueError("buffers: need two contiguous CUDA tensors")
+                if t.numel() * t.element_size() < need:
+                    raise ValueError(f"buffers: need {need} bytes each")
+            self._buffers = tuple(buffers)
+            ptrs = (_P * 2)(buffers[0].data_ptr(), buffers[1].data_ptr())
+            _check(_lib.vklb_create_borrowed(C.byref(s), lat, C.byref(grid), C.byref(b), C.byref(w), float(dt),
+                                             PRECISION[precision], _stream_handle(stream), ptrs, need,
+                                             C.byref(self._h)), "vklb_create_borrowed")
         self.info = Info()
         _check(_lib.vklb_info(self._h, C.byref(self.info)), "vklb_info")
         self.p = self.info.p

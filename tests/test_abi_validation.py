@@ -107,3 +107,78 @@ def test_device_buffers_checked_before_the_library(vk, bad):
         vk.Sim.moments(stub, out=_FakeCuda(**bad))
     with pytest.raises(ValueError):
         vk.Sim.set_state(stub, _FakeCuda(**bad))
+
+
+class _FakeTensor:
+    """Stands in for a CUDA tensor: only a pointer and a size (the library
+    checks these before any device call)."""
+
+    is_cuda = True
+
+    def __init__(self, ptr, nbytes):
+        self._ptr, self._n = ptr, nbytes
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        return self._ptr
+
+    def numel(self):
+        return self._n
+
+    def element_size(self):
+        return 1
+
+
+def test_buffer_bytes(vk):
+    assert vk.buffer_bytes("euler", (100, 37), "fp32") == 5 * 4 * 128 * 37 * 4   # rows padded to bricks
+    assert vk.buffer_bytes("mhd_glm", (64, 64), "bf16") == 5 * 9 * 64 * 64 * 2
+    assert vk.buffer_bytes("swe", (400,), "fp64") == 3 * 2 * 400 * 8
+
+
+@pytest.mark.parametrize("case", ["misaligned", "overlap", "null"])
+def test_borrowed_buffers_rejected_before_device_calls(vk, case):
+    need = vk.buffer_bytes("euler", (64, 64), "fp32")
+    base = 1 << 40
+    bufs = {"misaligned": (_FakeTensor(base + 16, need), _FakeTensor(base + 2 * need, need)),
+            "overlap": (_FakeTensor(base, need), _FakeTensor(base + need // 2, need)),
+            "null": (_FakeTensor(0, need), _FakeTensor(base, need))}[case]
+    assert _status(vk, lambda: vk.Sim("euler", (64, 64), (0, 0), (1, 1), buffers=bufs)) == vk.ERR_ARG
+
+
+def test_borrowed_buffers_too_short(vk):
+    need = vk.buffer_bytes("euler", (64, 64), "fp32")
+    base = 1 << 40
+    with pytest.raises(ValueError):     # the binding's check
+        vk.Sim("euler", (64, 64), (0, 0), (1, 1), buffers=(_FakeTensor(base, need), _FakeTensor(base + need, 64)))
+    # and the library's own, called directly with a short size
+    s = vk.System(vk.EULER, 1.4, 9.81, 6.0, (C.c_double * 2)(1.0, 0.0))
+    grid = vk.Grid(2, (C.c_int64 * 2)(64, 64), (C.c_double * 2)(0, 0), (C.c_double * 2)(1, 1))
+    b = vk.BC((C.c_int32 * 2)(0, 0), (C.c_int32 * 2)(0, 0))
+    w = vk.Weight(0, 0.05, 2.0, 1.0, 0.9, 0.0, 0)
+    ptrs = (C.c_void_p * 2)(base, base + 2 * need)
+    h = C.c_void_p()
+    st = vk.lib().vklb_create_borrowed(C.byref(s), vk.D2Q5, C.byref(grid), C.byref(b), C.byref(w), 0.0, vk.FP32,
+                                        None, ptrs, need - 1, C.byref(h))
+    assert st == vk.ERR_ARG and not h.value
+
+
+@pytest.mark.parametrize("bc,status", [
+    (("transmissive", "characteristic"), "ERR_ARG"),        # the open axes take one kind
+    (("characteristic", "transmissive"), "ERR_ARG"),
+    ("nonsense", None),
+])
+def test_boundary_kinds(vk, bc, status):
+    if status is None:
+        with pytest.raises(KeyError):
+            vk.Sim("euler", (16, 16), (0, 0), (1, 1), bc=bc)
+        return
+    assert _status(vk, lambda: vk.Sim("euler", (16, 16), (0, 0), (1, 1), bc=bc)) == getattr(vk, status)
+
+
+def test_transmissive_refusals(vk):
+    assert _status(vk, lambda: vk.Sim("mhd_glm", (16, 16), (0, 0), (1, 1), bc="transmissive")) == \
+        vk.ERR_UNSUPPORTED
+    assert _status(vk, lambda: vk.Sim("euler", (2, 16), (0, 0), (1, 8), bc=("transmissive", "periodic"))) == \
+        vk.ERR_ARG

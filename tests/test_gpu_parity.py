@@ -419,6 +419,7 @@ def test_fixed_dt_cfl_violation_is_reported(vk):
 @pytest.mark.parametrize("system,variant,tile,bc", [("euler", (0, 0), (32, 8), "periodic"),
                                                     ("euler", (1, 4), (64, 5), "periodic"),
                                                     ("swe", (0, 0), (32, 6), "characteristic"),
+                                                    ("swe", (0, 0), (64, 5), "transmissive"),
                                                     ("mhd_glm", (0, 0), (64, 8), "periodic")])
 def test_every_cell_written_each_step(vk, system, variant, tile, bc):
     """Before every step the destination buffer is filled with NaN

@@ -1,7 +1,8 @@
 """The paper's 1D verification suite on the GPU (Secs. 5.1, 5.2): the shallow-water
 Riemann problems of Table 1 and the Euler problems of Table 2 with
-characteristic (transmissive, reading R12) boundaries, omega = 1, c = 0.05,
-k = 2, and the smooth hump of Eq. (53).
+characteristic boundaries (the paper's transmissive ones, reading R12; the
+parity tests also run the zero-order extrapolation of reading R21), omega = 1,
+c = 0.05, k = 2, and the smooth hump of Eq. (53).
 
 * Parity with the FP64 oracle at the paper's CFL number 0.9 over 30 steps (the
   weighted set at rest is ill-conditioned at CFL 0.9 over long runs: its
@@ -50,15 +51,16 @@ def _exact(table, name, x, T):
 PROBLEMS = [(1, "standard"), (1, "hydraulic"), (1, "compression"), (2, "sod"), (2, "sonic"), (2, "leblanc")]
 
 
+@pytest.mark.parametrize("bc", ["characteristic", "transmissive"])
 @pytest.mark.parametrize("table,name", PROBLEMS)
-def test_tables_parity_paper_cfl(vk, table, name):
+def test_tables_parity_paper_cfl(vk, table, name, bc):
     n = 128
     system, U0, meta, skw, sysm = _problem(table, name, n)
-    sim = vk.Sim(system, (n,), (meta["lo"],), (meta["hi"],), precision="fp64", cfl=0.9, **KW, **skw)
+    kw = dict(KW, bc=bc)
+    sim = vk.Sim(system, (n,), (meta["lo"],), (meta["hi"],), precision="fp64", cfl=0.9, **kw, **skw)
     sim.set_state(U0)
     sim.step(30)
-    ref = ovklb.Sim(sysm, (n,), (meta["lo"],), (meta["hi"],), bc="characteristic", c=0.05, k=2.0, omega=1.0,
-                    nu=0.9)
+    ref = ovklb.Sim(sysm, (n,), (meta["lo"],), (meta["hi"],), bc=bc, c=0.05, k=2.0, omega=1.0, nu=0.9)
     ref.set_state(U0)
     ref.run(30)
     assert max_rel(sim.moments(), ref.moments()).max() <= 1e-11
@@ -67,15 +69,16 @@ def test_tables_parity_paper_cfl(vk, table, name):
     sim.close()
 
 
+@pytest.mark.parametrize("bc", ["characteristic", "transmissive"])
 @pytest.mark.parametrize("table,name", [(1, "standard"), (1, "compression"), (2, "sod")])
-def test_tables_parity_to_final_time(vk, table, name):
+def test_tables_parity_to_final_time(vk, table, name, bc):
     n = 160
     system, U0, meta, skw, sysm = _problem(table, name, n)
-    sim = vk.Sim(system, (n,), (meta["lo"],), (meta["hi"],), precision="fp64", cfl=0.6, **KW, **skw)
+    kw = dict(KW, bc=bc)
+    sim = vk.Sim(system, (n,), (meta["lo"],), (meta["hi"],), precision="fp64", cfl=0.6, **kw, **skw)
     sim.set_state(U0)
     sim.step_to(meta["T"])
-    ref = ovklb.Sim(sysm, (n,), (meta["lo"],), (meta["hi"],), bc="characteristic", c=0.05, k=2.0, omega=1.0,
-                    nu=0.6)
+    ref = ovklb.Sim(sysm, (n,), (meta["lo"],), (meta["hi"],), bc=bc, c=0.05, k=2.0, omega=1.0, nu=0.6)
     ref.set_state(U0)
     ref.run_to(meta["T"])
     assert max_rel(sim.moments(), ref.moments()).max() <= 1e-10
