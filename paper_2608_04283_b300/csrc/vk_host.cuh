@@ -184,8 +184,11 @@ struct Impl {
 
   // rows f*_1 / f*_2 (3 each) and the x ring; the long-split march (P > 4)
   // also keeps its column state (3 rows of P) in shared memory
+  // row buffers [3][tx] x 2, the x ring [ty] x 2, and for the long-split march
+  // its column state [3][tx], each entry a cell of CellVec<R, P>::PP values
   static size_t smem_bytes(int tx, int ty) {
-    return (size_t)(((P > 4) ? 9 : 6) * P * tx + 2 * P * ty) * sizeof(R);
+    constexpr int PP = CellVec<R, P>::PP;
+    return (size_t)(((P > 4) ? 9 : 6) * PP * tx + 2 * PP * ty) * sizeof(R);
   }
   static size_t smem_bytes_v(int variant, int tx, int ty, int d) {
     if (variant == 1) return TmaLayout<T>::template make<R, P>(tx, ty, d).bytes;
@@ -233,14 +236,10 @@ struct Impl {
         if (kv == 1)
           step2d_tma_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY, D);
 
-        else if (kv == 2 && bounded(TX))
-          launch_lb<1>(grid, TX, sm, s->stream, a, TY);
-        else if (kv == 2)
-          step2d_u_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
-        else if (bounded(TX))
-          launch_lb<0>(grid, TX, sm, s->stream, a, TY);
+        else if (wide128(TX))
+          launch_plain<128>(kv, grid, TX, sm, s->stream, a, TY);
         else
-          step2d_kernel<Sys, T, R><<<grid, TX, sm, s->stream>>>(a, TX, TY);
+          launch_plain<0>(kv, grid, TX, sm, s->stream, a, TY);
         if constexpr (!Sys::MHD) {
           if (s->nb > 0) {
             // the characteristic faces (same step arguments: parity and slot of step n)
@@ -263,36 +262,70 @@ struct Impl {
   // and the block fits its 128-thread bound
   static constexpr bool kBounded = StepBound<Sys, R>::min_blocks > 0;
   // the bounded instantiations exist only where they are launched
-  template <int FORM>
+  template <int FORM, int TXC>
   static void launch_lb(dim3 grid, int TX, size_t sm, cudaStream_t st, const StepArgs<T>& a, int TY) {
-    if constexpr (kBounded) step2d_lb_kernel<Sys, T, R, kMinBlocks, FORM><<<grid, TX, sm, st>>>(a, TX, TY);
+    if constexpr (kBounded) step2d_lb_kernel<Sys, T, R, kMinBlocks, FORM, TXC><<<grid, TX, sm, st>>>(a, TX, TY);
   }
   static constexpr int kMinBlocks = kBounded ? StepBound<Sys, R>::min_blocks : 1;
   static bool bounded(int tx) { return kBounded && tx <= 128; }
+  // The long-split march (p > 4) has instantiations with the tile width 128
+  // (the default launch shape's and the server's) known at compile time:
+  // measured 9 % fewer instructions for MHD-GLM than with the width at run time.
+  static constexpr bool kWide128 = P > 4;
+  static bool wide128(int tx) { return kWide128 && tx == 128; }
+  // plain (kv 0) or moment-form (kv 2) step kernel, TXC as above
+  template <int TXC>
+  static void launch_plain(int kv, dim3 grid, int TX, size_t sm, cudaStream_t st, const StepArgs<T>& a, int TY) {
+    if constexpr (TXC == 0 || kWide128) {
+      if (kv == 2 && bounded(TX))
+        launch_lb<1, TXC>(grid, TX, sm, st, a, TY);
+      else if (kv == 2)
+        step2d_u_kernel<Sys, T, R, TXC><<<grid, TX, sm, st>>>(a, TX, TY);
+      else if (bounded(TX))
+        launch_lb<0, TXC>(grid, TX, sm, st, a, TY);
+      else
+        step2d_kernel<Sys, T, R, TXC><<<grid, TX, sm, st>>>(a, TX, TY);
+    }
+  }
 
   static void set_attributes() {
     if constexpr (DIM == 2) {
       static std::atomic<unsigned long long> done{0};
       if (!first_on_device(done)) return;
-      cudaFuncSetAttribute(step2d_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(step2d_tma_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute(step2d_u_kernel<Sys, T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-
-      if constexpr (kBounded) {
-        cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-      }
+      set_plain_attributes<0>();
+      if constexpr (kWide128) set_plain_attributes<128>();
+    }
+  }
+  template <int TXC>
+  static void set_plain_attributes() {
+    cudaFuncSetAttribute(step2d_kernel<Sys, T, R, TXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(step2d_u_kernel<Sys, T, R, TXC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if constexpr (kBounded) {
+      cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks, 0, TXC>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_lb_kernel<Sys, T, R, kMinBlocks, 1, TXC>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     }
   }
 
-  template <int FORM>
+  template <int FORM, int TXC>
   static cudaError_t occupancy_lb(int* nb, int tx, size_t sm) {
     if constexpr (kBounded)
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_lb_kernel<Sys, T, R, kMinBlocks, FORM>, tx, sm);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_lb_kernel<Sys, T, R, kMinBlocks, FORM, TXC>, tx,
+                                                           sm);
     else
       return cudaErrorInvalidValue;
+  }
+  template <int TXC>
+  static cudaError_t occupancy_plain(int* nb, int variant, int tx, size_t sm) {
+    if constexpr (TXC == 0 || kWide128) {
+      if (variant == 2 && bounded(tx)) return occupancy_lb<1, TXC>(nb, tx, sm);
+      if (variant == 2) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_u_kernel<Sys, T, R, TXC>, tx, sm);
+      if (bounded(tx)) return occupancy_lb<0, TXC>(nb, tx, sm);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_kernel<Sys, T, R, TXC>, tx, sm);
+    }
+    return cudaErrorInvalidValue;
   }
 
   // resident blocks per SM of the step kernel a sim with this launch shape runs
@@ -306,15 +339,10 @@ struct Impl {
       cudaError_t e;
       if (variant == 1)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_tma_kernel<Sys, T, R>, tx, sm);
-
-      else if (variant == 2 && bounded(tx))
-        e = occupancy_lb<1>(&nb, tx, sm);
-      else if (variant == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_u_kernel<Sys, T, R>, tx, sm);
-      else if (bounded(tx))
-        e = occupancy_lb<0>(&nb, tx, sm);
+      else if (wide128(tx))
+        e = occupancy_plain<128>(&nb, variant, tx, sm);
       else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_kernel<Sys, T, R>, tx, sm);
+        e = occupancy_plain<0>(&nb, variant, tx, sm);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -358,19 +386,69 @@ struct BatchImpl {
   static constexpr bool kBounded = Impl<Sys, T, R, DIM>::kBounded;
   static constexpr int kMinBlocks = Impl<Sys, T, R, DIM>::kMinBlocks;
   static bool bounded(int variant, int tx) { return variant != 1 && Impl<Sys, T, R, DIM>::bounded(tx); }
-  template <int V>
+  // tile width 128 at compile time for the long-split march (as Impl)
+  static constexpr bool kWide128 = Impl<Sys, T, R, DIM>::kWide128;
+  static bool wide128(int variant, int tx) { return variant != 1 && Impl<Sys, T, R, DIM>::wide128(tx); }
+  template <int V, int TXC>
   static void launch_lb(const vklb_batch* b, int i, int TX, int TY, int D, size_t sm) {
     if constexpr (kBounded)
-      step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks><<<b->nwork, TX, sm, b->own>>>(
+      step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks, TXC><<<b->nwork, TX, sm, b->own>>>(
           (const StepArgs<T>*)b->d_desc, b->d_work, i, TX, TY, D);
   }
-  template <int V>
+  template <int V, int TXC>
   static cudaError_t occupancy_lb(int* nb, int tx, size_t sm) {
     if constexpr (kBounded) {
-      cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks>,
+      cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks, TXC>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks>, tx,
-                                                           sm);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_batch_lb_kernel<Sys, T, R, V, kMinBlocks, TXC>,
+                                                           tx, sm);
+    }
+    return cudaErrorInvalidValue;
+  }
+  // plain (variant 0) or moment-form (variant 2) batched step, TXC as in Impl
+  template <int TXC>
+  static void launch_plain(vklb_batch* b, int i, int TX, int TY, int D, size_t sm) {
+    if constexpr (TXC == 0 || kWide128) {
+      const bool lb = bounded(b->variant, TX);
+      if (b->variant == 2 && lb)
+        launch_lb<2, TXC>(b, i, TX, TY, D, sm);
+      else if (b->variant == 2)
+        step2d_batch_kernel<Sys, T, R, 2, TXC><<<b->nwork, TX, sm, b->own>>>(
+            (const StepArgs<T>*)b->d_desc, b->d_work, i, TX, TY, D);
+      else if (lb)
+        launch_lb<0, TXC>(b, i, TX, TY, D, sm);
+      else
+        step2d_batch_kernel<Sys, T, R, 0, TXC><<<b->nwork, TX, sm, b->own>>>(
+            (const StepArgs<T>*)b->d_desc, b->d_work, i, TX, TY, D);
+    }
+  }
+  template <int TXC>
+  static void set_plain_attributes() {
+    cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0, TXC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2, TXC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    if constexpr (kBounded) {
+      cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, 0, kMinBlocks, TXC>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, 2, kMinBlocks, TXC>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }
+  }
+  static void set_attributes() {
+    cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    set_plain_attributes<0>();
+    if constexpr (kWide128) set_plain_attributes<128>();
+  }
+  template <int TXC>
+  static cudaError_t occupancy_plain(int* nb, int variant, int tx, size_t sm) {
+    if constexpr (TXC == 0 || kWide128) {
+      const bool lb = bounded(variant, tx);
+      if (variant == 2)
+        return lb ? occupancy_lb<2, TXC>(nb, tx, sm)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_batch_kernel<Sys, T, R, 2, TXC>, tx, sm);
+      return lb ? occupancy_lb<0, TXC>(nb, tx, sm)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step2d_batch_kernel<Sys, T, R, 0, TXC>, tx, sm);
     }
     return cudaErrorInvalidValue;
   }
@@ -378,21 +456,14 @@ struct BatchImpl {
     if constexpr (DIM == 2) {
     const int TX = b->tile_x, TY = b->tile_y, D = b->stages;
     const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(b->variant, TX, TY, D);
-    const bool lb = bounded(b->variant, TX);
     for (int64_t i = 0; i < n; ++i) {
       if (b->variant == 1)
         step2d_batch_kernel<Sys, T, R, 1><<<b->nwork, TX, sm, b->own>>>(
             (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
-      else if (b->variant == 2 && lb)
-        launch_lb<2>(b, (int)i, TX, TY, D, sm);
-      else if (b->variant == 2)
-        step2d_batch_kernel<Sys, T, R, 2><<<b->nwork, TX, sm, b->own>>>(
-            (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
-      else if (lb)
-        launch_lb<0>(b, (int)i, TX, TY, D, sm);
+      else if (wide128(b->variant, TX))
+        launch_plain<128>(b, (int)i, TX, TY, D, sm);
       else
-        step2d_batch_kernel<Sys, T, R, 0><<<b->nwork, TX, sm, b->own>>>(
-            (const StepArgs<T>*)b->d_desc, b->d_work, (int)i, TX, TY, D);
+        launch_plain<0>(b, (int)i, TX, TY, D, sm);
     }
     }
   }
@@ -402,18 +473,12 @@ struct BatchImpl {
       return 0;
     } else {
       const size_t sm = Impl<Sys, T, R, DIM>::smem_bytes_v(variant, tx, ty, d);
-      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      set_attributes();
       int nb = 0;
-      const bool lb = bounded(variant, tx);
       cudaError_t e =
-          variant == 1   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx, sm)
-          : variant == 2 ? (lb ? occupancy_lb<2>(&nb, tx, sm)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 2>,
-                                                                               tx, sm))
-          : lb ? occupancy_lb<0>(&nb, tx, sm)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 0>, tx, sm);
+          variant == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step2d_batch_kernel<Sys, T, R, 1>, tx, sm)
+          : wide128(variant, tx) ? occupancy_plain<128>(&nb, variant, tx, sm)
+                                 : occupancy_plain<0>(&nb, variant, tx, sm);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -426,17 +491,7 @@ struct BatchImpl {
       return VKLB_ERR_UNSUPPORTED;
     } else {
     static std::atomic<unsigned long long> attr_set{0};
-    if (first_on_device(attr_set)) {
-      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      cudaFuncSetAttribute(step2d_batch_kernel<Sys, T, R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if constexpr (kBounded) {
-        cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, 0, kMinBlocks>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(step2d_batch_lb_kernel<Sys, T, R, 2, kMinBlocks>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      }
-    }
+    if (first_on_device(attr_set)) set_attributes();
     StepArgs<T>* h = (StepArgs<T>*)b->h_desc.data();
     for (size_t i = 0; i < b->sims.size(); ++i) {
       h[i] = make_args<T>(b->sims[i], -1.0);

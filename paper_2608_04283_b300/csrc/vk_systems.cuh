@@ -422,28 +422,41 @@ struct MHDGLM {
 
   // Both directions through one copy of split_x (a loop the compiler keeps):
   // the split is several kilobytes of code, and a second inlined copy costs
-  // more in instruction-cache misses than the loop's register moves.
+  // more in instruction-cache misses than the loop's register moves.  The
+  // second pass keeps the first one's result and turns the state in place
+  // (swapping (m_x, m_y) and (B_x, B_y)), so that no value is chosen by the
+  // pass index at run time (a select per value and pass, measured 5 % of the
+  // MHD-GLM step's instructions).
   VK_HD void split2(const R* U, int set, R k, R ch, R* Fp1, R* F1, R* Fp2, R* F2) const {
+    R V[9], a[9], b[9], ax[9], bx[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) V[i] = U[i];
 #pragma unroll 1
     for (int d = 0; d < 2; ++d) {
-      const bool y = d == 1;
-      const R V[9] = {U[0], y ? U[2] : U[1], y ? U[1] : U[2], U[3], U[4],
-                      y ? U[6] : U[5], y ? U[5] : U[6], U[7], U[8]};
-      R a[9], b[9];
-      split_x(V, set, k, ch, a, b);
-      if (!y) {
+      if (d == 1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-          Fp1[i] = a[i];
-          F1[i] = b[i];
+          ax[i] = a[i];
+          bx[i] = b[i];
         }
-      } else {
-        Fp2[0] = a[0]; Fp2[1] = a[2]; Fp2[2] = a[1]; Fp2[3] = a[3]; Fp2[4] = a[4];
-        Fp2[5] = a[6]; Fp2[6] = a[5]; Fp2[7] = a[7]; Fp2[8] = a[8];
-        F2[0] = b[0]; F2[1] = b[2]; F2[2] = b[1]; F2[3] = b[3]; F2[4] = b[4];
-        F2[5] = b[6]; F2[6] = b[5]; F2[7] = b[7]; F2[8] = b[8];
+        R t = V[1];
+        V[1] = V[2];
+        V[2] = t;
+        t = V[5];
+        V[5] = V[6];
+        V[6] = t;
       }
+      split_x(V, set, k, ch, a, b);
     }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      Fp1[i] = ax[i];
+      F1[i] = bx[i];
+    }
+    Fp2[0] = a[0]; Fp2[1] = a[2]; Fp2[2] = a[1]; Fp2[3] = a[3]; Fp2[4] = a[4];
+    Fp2[5] = a[6]; Fp2[6] = a[5]; Fp2[7] = a[7]; Fp2[8] = a[8];
+    F2[0] = b[0]; F2[1] = b[2]; F2[2] = b[1]; F2[3] = b[3]; F2[4] = b[4];
+    F2[5] = b[6]; F2[6] = b[5]; F2[7] = b[7]; F2[8] = b[8];
   }
 
   // m1 = max_d (|u_d| + c_f,d), m2 = max_d c_f,d, physical test of U^{n+1}
