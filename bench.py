@@ -109,13 +109,19 @@ def configure(sim, shape):
     sim.set_tiling(*tile)          # the wave-fit height depends on the variant
 
 
+# systems whose FP32-compute step kernel has a register-bounded instantiation
+# (taken for blocks of at most 128 threads)
+BOUNDED_STEP = ("mhd_glm", "euler")
+
+
 def step_kernel_name(system, prec, tile_x, variant, form=0):
     """The step kernel the library launches: the bulk-copy variant, or the plain
-    one (moment form: step2d_u_kernel), which FP32-compute MHD-GLM with blocks
-    of at most 128 threads takes in its register-bounded instantiation."""
+    one (moment form: step2d_u_kernel), which FP32-compute MHD-GLM and Euler
+    with blocks of at most 128 threads take in their register-bounded
+    instantiation."""
     if variant == 1:
         return "step2d_tma_kernel"
-    if system == "mhd_glm" and prec != "fp64" and tile_x <= 128:
+    if system in BOUNDED_STEP and prec != "fp64" and tile_x <= 128:
         return "step2d_lb_kernel"
     return "step2d_u_kernel" if form == 1 else "step2d_kernel"
 

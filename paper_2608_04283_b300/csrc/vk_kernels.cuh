@@ -525,7 +525,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
           U[i] = round_store(u, tp);
         }
       }
-      if (!on_char_face(a, x, j)) {
+      if (!(a.cbx | a.cby) || !on_char_face(a, x, j)) {   // periodic grids skip the face test
         R e1, e2;
         bad |= !sys.epilogue(U, e1, e2);
         m1 = vmax(m1, e1);
