@@ -1063,8 +1063,8 @@ __global__ void step2d_u_kernel(StepArgs<T> a, int TX, int TY) {
 
 // Register bound of the plain step: blocks of at most 128 threads with at least
 // `min_blocks` of them resident per SM (0 = no bound).  FP32 MHD-GLM needs about
-// 157 registers a thread unbounded (3 blocks of 4 warps per SM); capped at 128
-// (4 blocks) it spills a few hundred bytes to L1 and still runs faster.
+// 170 registers a thread unbounded (3 blocks of 4 warps per SM); capped at 128
+// (4 blocks) it fits without spills and runs faster.
 template <class Sys, class R>
 struct StepBound {
   static constexpr int min_blocks = 0;
