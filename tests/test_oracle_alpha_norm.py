@@ -257,3 +257,74 @@ def test_rest_state_growth_by_reading():
     xi = Lam / 0.9
     gl, gg = _rest_growth(1.0, 3.0, xi, None), _rest_growth(1.0, 3.0, xi, Lam)
     assert 1.15 < gl < 1.25 and 1.0 < gg < 1.05
+
+
+def _mode_amplification(M, tx, ty, omega=2.0):
+    """|largest eigenvalue| of the linearised D2Q5 step for one wave vector,
+    with M the equilibrium Jacobians of _amplification."""
+    p = M.shape[1]
+    G = np.zeros((5 * p, 5 * p), complex)
+    for q in range(5):
+        blk = np.tile(omega * M[q], (1, 5)).astype(complex)
+        blk[:, q * p:(q + 1) * p] += (1 - omega) * np.eye(p)
+        G[q * p:(q + 1) * p] = np.exp(-1j * (tx * V2[q][0] + ty * V2[q][1])) * blk
+    return float(np.abs(np.linalg.eigvals(G)).max())
+
+
+def _eq_jacobians(s, U0, xi, lam_norm, c=0.05, k=2.0):
+    p = len(U0)
+
+    def feq(U):
+        Uc = U.reshape(-1, 1)
+        parts = []
+        for d in range(2):
+            Fp, Fm = splitting.split_weighted(s, Uc, d, k, lam_norm=lam_norm)
+            parts += [Fp, Fm]
+        return vklb.equilibrium_2d(Uc, *parts, xi, c)[:, :, 0]
+    M = np.zeros((5, p, p))
+    for j in range(p):
+        e = np.zeros(p)
+        e[j] = 1e-6 * max(1.0, abs(U0[j]))
+        M[:, :, j] = (feq(U0 + e) - feq(U0 - e)) / (2 * e[j])
+    return M
+
+
+def test_entropy_wave_unstable_mode():
+    """A finding: the entropy wave's background flow (Sec. 5.2, Eq. 55: rho = 1,
+    u = v = 1, p = 1; CFL 0.3, omega = 2, c = 0.05, k = 2, grid-wide normaliser
+    2.247 = max |u| + c over the wave) is linearly unstable through one family
+    of modes along the flow's diagonal, theta_x = theta_y near 0.68 pi (about
+    three cells a wavelength), which grows about 1.7 % a step: x 1e14 over the
+    1,918 steps of the paper's N = 256, T = 1.  The same state moving along x
+    (v = 0) and the fluid at rest are neutral, as are the diagonal modes far
+    from that band.  With d F+/dU taken as alpha(A) A (the weights'
+    derivatives dropped) the same equilibria are neutral on the whole
+    diagonal, so the growth comes from the derivative of the weighted split
+    itself, not from a reading of the lattice speed or of c."""
+    s = systems.Euler(1.4, 2)
+    lam = 2.247
+    diag = inputs.euler_conserved(np.array(1.0), np.array(1.0), np.array(1.0), np.array(1.0), 1.4)
+    along = inputs.euler_conserved(np.array(1.0), np.array(1.0), np.array(0.0), np.array(1.0), 1.4)
+    M = _eq_jacobians(s, diag, lam / 0.3, lam)
+    th = np.linspace(0.0, np.pi, 91)
+    a = np.array([_mode_amplification(M, t, t) for t in th])
+    i = int(np.argmax(a))
+    assert 1.012 < a[i] < 1.025, a[i]
+    assert 0.6 < th[i] / np.pi < 0.75, th[i]
+    assert a[th < 0.4 * np.pi].max() < 1 + 1e-8                 # long waves: neutral
+    Ma = _eq_jacobians(s, along, lam / 0.3, lam)
+    assert max(_mode_amplification(Ma, t, t) for t in th[::5]) < 1 + 1e-8
+    assert max(_mode_amplification(Ma, t, 0.0) for t in th[::5]) < 1 + 1e-8
+    # the same equilibria with d F+/dU taken as alpha(A) A (Eq. 41 with the
+    # weights frozen): neutral on the whole diagonal
+    import scipy.linalg as sla
+    xi, c, I = lam / 0.3, 0.05, np.eye(4)
+    Mf = np.zeros((5, 4, 4))
+    for d in range(2):
+        A = splitting.jacobian(s, diag.reshape(4, 1), d)[0]
+        E = sla.expm(2.0 * A / lam)
+        alA = np.linalg.solve((E + I).T, E.T).T @ A           # alpha(A) A, alpha = E (E + I)^-1
+        Mf[3 * d] = c * I + alA / xi
+        Mf[3 * d + 1] = c * I - (A - alA) / xi
+    Mf[2] = I - Mf[0] - Mf[1] - Mf[3] - Mf[4]
+    assert max(_mode_amplification(Mf, t, t) for t in th) < 1 + 1e-8
