@@ -139,34 +139,37 @@ extern "C" int vklb_hc_split2(int kind, int precision, int set, double k, double
 // (the construction of Eqs. 33-35 applied per face), at n states; U, dU, out: [p][n].
 namespace {
 template <class Sys, class R>
-void run_bc2(const Sys& sys, const double* U, const double* dU, int d, int side, int64_t n, double* out) {
+void run_bc2(const Sys& sys, const double* U, const double* dU, int d, int side, double ch, int64_t n,
+             double* out) {
   const int P = Sys::P;
   for (int64_t i = 0; i < n; ++i) {
-    R u[4], du[4], o[4];
+    R u[9], du[9], o[9];
     for (int c = 0; c < P; ++c) {
       u[c] = (R)U[c * n + i];
       du[c] = (R)dU[c * n + i];
     }
-    sys.char_rhs_d(u, du, d, side, o);
+    sys.char_rhs_d(u, du, d, side, (R)ch, o);
     for (int c = 0; c < P; ++c) out[c * n + i] = (double)o[c];
   }
 }
 template <class R>
-int bc2_dispatch(int kind, int d, int side, double gamma, double g, double ax, double ay, const double* U,
-                 const double* dU, int64_t n, double* out) {
+int bc2_dispatch(int kind, int d, int side, double gamma, double g, double ax, double ay, double ch,
+                 const double* U, const double* dU, int64_t n, double* out) {
   const double lg = 0.0;
-  if (kind == 0) { vk::Advect<R, 2> s; s.lg = (R)lg; s.a[0] = (R)ax; s.a[1] = (R)ay; run_bc2<vk::Advect<R, 2>, R>(s, U, dU, d, side, n, out); }
-  else if (kind == 1) { vk::SWE<R, 2> s; s.lg = (R)lg; s.g = (R)g; run_bc2<vk::SWE<R, 2>, R>(s, U, dU, d, side, n, out); }
-  else if (kind == 2) { vk::Euler<R, 2> s; s.lg = (R)lg; s.gamma = (R)gamma; run_bc2<vk::Euler<R, 2>, R>(s, U, dU, d, side, n, out); }
+  if (kind == 0) { vk::Advect<R, 2> s; s.lg = (R)lg; s.a[0] = (R)ax; s.a[1] = (R)ay; run_bc2<vk::Advect<R, 2>, R>(s, U, dU, d, side, ch, n, out); }
+  else if (kind == 1) { vk::SWE<R, 2> s; s.lg = (R)lg; s.g = (R)g; run_bc2<vk::SWE<R, 2>, R>(s, U, dU, d, side, ch, n, out); }
+  else if (kind == 2) { vk::Euler<R, 2> s; s.lg = (R)lg; s.gamma = (R)gamma; run_bc2<vk::Euler<R, 2>, R>(s, U, dU, d, side, ch, n, out); }
+  else if (kind == 3) { vk::MHDGLM<R> s; s.lg = (R)lg; s.gamma = (R)gamma; run_bc2<vk::MHDGLM<R>, R>(s, U, dU, d, side, ch, n, out); }
   else return -8;
   return 0;
 }
 }  // namespace
 
+// ch: the cleaning speed c_h (MHD-GLM only)
 extern "C" int vklb_hc_char_rhs2d(int kind, int precision, int d, int side, double gamma, double g, double ax,
-                                  double ay, const double* U, const double* dU, int64_t n, double* out) {
-  if (precision == 0) return bc2_dispatch<double>(kind, d, side, gamma, g, ax, ay, U, dU, n, out);
-  return bc2_dispatch<float>(kind, d, side, gamma, g, ax, ay, U, dU, n, out);
+                                  double ay, double ch, const double* U, const double* dU, int64_t n, double* out) {
+  if (precision == 0) return bc2_dispatch<double>(kind, d, side, gamma, g, ax, ay, ch, U, dU, n, out);
+  return bc2_dispatch<float>(kind, d, side, gamma, g, ax, ay, ch, U, dU, n, out);
 }
 
 // The enumeration of the characteristic faces' nodes that the boundary passes

@@ -1199,7 +1199,7 @@ __global__ void char2d_state_kernel(StepArgs<T> a, R* __restrict__ Ub, int nb) {
       load_U<Sys, T, R>(fin, xn, yn, nxb, Un);
 #pragma unroll
       for (int i = 0; i < P; ++i) dU[i] = side == 0 ? Un[i] - U[i] : U[i] - Un[i];
-      sys.char_rhs_d(U, dU, d, side, t);
+      sys.char_rhs_d(U, dU, d, side, (R)sc.ch, t);
 #pragma unroll
       for (int i = 0; i < P; ++i) rhs[i] += t[i];
     }

@@ -63,7 +63,7 @@ struct Advect {
     out[0] = out_going ? l * dU[0] : R(0);
   }
   // The same along direction d of a 2D grid (a face normal to d).
-  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R* out) const {
+  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R /*ch*/, R* out) const {
     R l = a[d];
     bool out_going = side == 0 ? l < R(0) : l > R(0);
     out[0] = out_going ? l * dU[0] : R(0);
@@ -173,7 +173,7 @@ struct SWE {
   // 2D, along direction d (normal momentum n = 1 + d, tangential t = 2 - d):
   // r = (1, u_n - c, u_t), (0, 0, 1) (shear, lambda = u_n), (1, u_n + c, u_t);
   // dual rows ((u_n + c), -1, 0)/(2c), (-u_t, 0, 1), ((c - u_n), 1, 0)/(2c).
-  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R* out) const {
+  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R /*ch*/, R* out) const {
     const int in = 1 + d, it = 2 - d;
     const R h = U[0], un = U[in] / h, ut = U[it] / h, c = vsqrt(g * h);
     const R i2c = R(0.5) / c;
@@ -331,7 +331,7 @@ struct Euler {
   // b2 = b1 q^2/2 the dual rows are
   // ((b2 + u_n/a), -(b1 u_n + 1/a), -b1 u_t, b1)/2, (1 - b2, b1 u_n, b1 u_t, -b1),
   // (-u_t, 0, 1, 0), ((b2 - u_n/a), -(b1 u_n - 1/a), -b1 u_t, b1)/2.
-  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R* out) const {
+  VK_HD void char_rhs_d(const R* U, const R* dU, int d, int side, R /*ch*/, R* out) const {
     const int in = 1 + d, it = 2 - d;
     const R rho = U[0], un = U[in] / rho, ut = U[it] / rho, E = U[3];
     const R q2 = un * un + ut * ut;
@@ -487,6 +487,130 @@ struct MHDGLM {
     Fp[5] = a[6]; Fp[6] = a[5]; Fp[7] = a[7]; Fp[8] = a[8];
     F[0] = b[0]; F[1] = b[2]; F[2] = b[1]; F[3] = b[3]; F[4] = b[4];
     F[5] = b[6]; F[6] = b[5]; F[7] = b[7]; F[8] = b[8];
+  }
+
+  // Characteristic boundary along direction d (Eqs. 33-35 on a face normal
+  // to d): out = P Lambda^out P^-1 dU of the 9 x 9 Jacobian, the waves leaving
+  // through a low face (side 0: lambda < 0) or a high face (side 1: lambda > 0).
+  // The same eigen-structure as split_x with the weight alpha(lambda) replaced by
+  // g(lambda) = lambda on outgoing waves, 0 on incoming ones, and the flux by
+  // dU: for the block-triangular Jacobian g(A) dU = (sum_j c_j r_j,
+  // sum_+- g(+-c_h) phi_+- (1, +-c_h)) with phi_+- = dB_n / 2 +- dpsi / (2 c_h)
+  // and c_j = g_j l_j.dU_7 + l_j.ga sum_+- phi_+- (g_j - g_+-) / (lambda_j - lambda_+-).
+  VK_HD void char_rhs_d(const R* Uin, const R* dUin, int d, int side, R ch, R* out) const {
+    if (d == 0) {
+      char_rhs_x(Uin, dUin, side, ch, out);
+      return;
+    }
+    const R U[9] = {Uin[0], Uin[2], Uin[1], Uin[3], Uin[4], Uin[6], Uin[5], Uin[7], Uin[8]};
+    const R dU[9] = {dUin[0], dUin[2], dUin[1], dUin[3], dUin[4], dUin[6], dUin[5], dUin[7], dUin[8]};
+    R o[9];
+    char_rhs_x(U, dU, side, ch, o);
+    out[0] = o[0]; out[1] = o[2]; out[2] = o[1]; out[3] = o[3]; out[4] = o[4];
+    out[5] = o[6]; out[6] = o[5]; out[7] = o[7]; out[8] = o[8];
+  }
+
+  VK_HD void char_rhs_x(const R* U, const R* dU, int side, R ch, R* out) const {
+    const R rho = U[0];
+    const R ir = R(1) / rho;
+    const R u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+    const R bx = U[5], by = U[6], bz = U[7];
+    const R bt2 = by * by + bz * bz;
+    const R q2 = u * u + v * v + w * w;
+    const R gm1 = gamma - R(1);
+    const R p = gm1 * (U[4] - R(0.5) * rho * q2 - R(0.5) * (bx * bx + bt2));
+    const R a2 = gamma * p * ir, bx2 = bx * bx * ir, btt = bt2 * ir;
+    R af, as, dcs;
+    mhd_norm<R>(a2, bx2, btt, af, as, dcs);
+    if (sizeof(R) == 4 && !(dcs > R(1e-3) * (a2 + bx2 + btt))) {
+      double af64, as64, d64;
+      mhd_norm<double>((double)a2, (double)bx2, (double)btt, af64, as64, d64);
+      af = (R)af64;
+      as = (R)as64;
+    }
+    const R cf2 = R(0.5) * (a2 + bx2 + btt + dcs);
+    const R cf = vsqrt(cf2);
+    const R cs = cf2 > R(0) ? vsqrt(a2 * bx2 / cf2) : R(0);
+    const R ca = vsqrt(bx2), a = vsqrt(a2), sr = vsqrt(rho);
+    R bty, btz;
+    const R bt = vsqrt(bt2);
+    if (bt > R(1e-30) * (vabs(bx) + R(1e-30))) {
+      bty = by / bt;
+      btz = bz / bt;
+    } else {
+      bty = btz = R(0.70710678118654752440);
+    }
+    const R s = bx >= R(0) ? R(1) : R(-1);
+    auto og = [&](R l) -> bool { return side == 0 ? l < R(0) : l > R(0); };
+    auto g = [&](R l) -> R { return og(l) ? l : R(0); };
+    // divided difference (g(l1) - g(l2)) / (l1 - l2): exactly 1 when both waves
+    // leave, 0 when both enter (g is l or 0 there), else the plain quotient
+    // (one of the two is 0 and the speeds lie on either side of 0)
+    auto gdd = [&](R l1, R g1, R l2, R g2) -> R {
+      if (og(l1) == og(l2)) return og(l1) ? R(1) : R(0);
+      return (g1 - g2) / (l1 - l2);
+    };
+    const R lam[7] = {u - cf, u - ca, u - cs, u, u + cs, u + ca, u + cf};
+    R gl[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) gl[j] = g(lam[j]);
+    const R gp = g(ch), gm = g(-ch);
+    const R php = R(0.5) * (dU[5] + dU[8] / ch), phm = R(0.5) * (dU[5] - dU[8] / ch);
+    // primitive increments of the MHD block of dU (B_n held), and of d F7 / d B_n
+    const R ia2 = R(1) / a2;
+    const R Gr = dU[0];
+    const R Gu = (dU[1] - u * dU[0]) * ir, Gv = (dU[2] - v * dU[0]) * ir, Gw = (dU[3] - w * dU[0]) * ir;
+    const R Gp = gm1 * (dU[4] + R(0.5) * q2 * dU[0] - (u * dU[1] + v * dU[2] + w * dU[3]) - (by * dU[6] + bz * dU[7]));
+    const R Gy = dU[6], Gz = dU[7];
+    const R hu = -gamma * bx * ir, hv = -by * ir, hw = -bz * ir;
+    const R hp = gm1 * (v * by + w * bz), hy = -v, hz = -w;
+    const R isr_a = R(1) / (sr * a), isr = R(1) / sr;
+    const R Tu = R(0.5) * Gu * ia2, Tt = R(0.5) * s * (bty * Gv + btz * Gw) * ia2;
+    const R Tp = R(0.5) * Gp * ia2 * ir, TB = R(0.5) * (bty * Gy + btz * Gz) * isr_a;
+    const R Tq = R(0.5) * (-btz * Gv + bty * Gw), TQ = R(0.5) * s * (btz * Gy - bty * Gz) * isr;
+    const R Hu = R(0.5) * hu * ia2, Ht = R(0.5) * s * (bty * hv + btz * hw) * ia2;
+    const R Hp = R(0.5) * hp * ia2 * ir, HB = R(0.5) * (bty * hy + btz * hz) * isr_a;
+    const R Hq = R(0.5) * (-btz * hv + bty * hw), HQ = R(0.5) * s * (btz * hy - bty * hz) * isr;
+    R lG[7], lH[7];
+    lG[0] = -(af * cf * Tu - as * cs * Tt) + af * Tp + as * TB;
+    lG[6] = +(af * cf * Tu - as * cs * Tt) + af * Tp + as * TB;
+    lG[2] = -(as * cs * Tu + af * cf * Tt) + as * Tp - af * TB;
+    lG[4] = +(as * cs * Tu + af * cf * Tt) + as * Tp - af * TB;
+    lG[1] = Tq - TQ;
+    lG[5] = Tq + TQ;
+    lG[3] = Gr - Gp * ia2;
+    lH[0] = -(af * cf * Hu - as * cs * Ht) + af * Hp + as * HB;
+    lH[6] = +(af * cf * Hu - as * cs * Ht) + af * Hp + as * HB;
+    lH[2] = -(as * cs * Hu + af * cf * Ht) + as * Hp - af * HB;
+    lH[4] = +(as * cs * Hu + af * cf * Ht) + as * Hp - af * HB;
+    lH[1] = Hq - HQ;
+    lH[5] = Hq + HQ;
+    lH[3] = -hp * ia2;
+    R cc[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j)
+      cc[j] = gl[j] * lG[j] + lH[j] * (php * gdd(lam[j], gl[j], ch, gp) + phm * gdd(lam[j], gl[j], -ch, gm));
+    const R fs = cc[6] + cc[0], fd = cc[6] - cc[0];
+    const R ss = cc[4] + cc[2], sd = cc[4] - cc[2];
+    const R as_ = cc[5] + cc[1], ad = cc[5] - cc[1];
+    const R Sr = rho * (af * fs + as * ss) + cc[3];
+    const R Su = af * cf * fd + as * cs * sd;
+    const R tr = s * (-as * cs * fd + af * cf * sd);
+    const R Sv = bty * tr - btz * as_;
+    const R Sw = btz * tr + bty * as_;
+    const R Sp = rho * a2 * (af * fs + as * ss);
+    const R tb = sr * a * (as * fs - af * ss);
+    const R Sy = bty * tb + s * sr * btz * ad;
+    const R Sz = btz * tb - s * sr * bty * ad;
+    out[0] = Sr;
+    out[1] = u * Sr + rho * Su;
+    out[2] = v * Sr + rho * Sv;
+    out[3] = w * Sr + rho * Sw;
+    out[4] = Sp / gm1 + R(0.5) * q2 * Sr + rho * (u * Su + v * Sv + w * Sw) + by * Sy + bz * Sz;
+    out[6] = Sy;
+    out[7] = Sz;
+    out[5] = gp * php + gm * phm;
+    out[8] = ch * (gp * php - gm * phm);
   }
 
   VK_HD void split_x(const R* U, int set, R k, R ch, R* Fp, R* F) const {

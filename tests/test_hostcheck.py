@@ -175,28 +175,35 @@ def test_split2_and_epilogue_match_oracle(name, kw, prec, tol, set_kind):
     assert np.all(ok == 1)
 
 
-@pytest.mark.parametrize("name,kw", [("swe", {"g": 9.81}), ("euler", {"gamma": 1.4}), ("advection", {})])
+@pytest.mark.parametrize("name,kw", [("swe", {"g": 9.81}), ("euler", {"gamma": 1.4}), ("advection", {}),
+                                     ("mhd_glm", {"gamma": 5.0 / 3.0})])
 @pytest.mark.parametrize("d,side", [(0, 0), (0, 1), (1, 0), (1, 1)])
 def test_char_rhs_2d_matches_oracle(name, kw, d, side):
     """The 2D characteristic boundary's outgoing part along either face normal
     (closed-form eigenvectors, vk_systems.cuh) against the oracle's basis-free
-    spectral projection (Sylvester's formula over the complex-step Jacobian)."""
+    spectral projection (Sylvester's formula over the complex-step Jacobian).
+    MHD-GLM: the 9-wave Jacobian with c_h = 6 max c_f of the states (R4)."""
     from oracle import vklb as ovklb
     s = systems.make(name, 2, a=(0.7, -0.4), **kw)
     U = np.ascontiguousarray(inputs.random_states(name, 150, seed=37 + 2 * d + side, dim=2,
                                                   gamma=kw.get("gamma", 1.4)))
+    ch = 0.0
+    if name == "mhd_glm":
+        ch = 6.0 * float(max(s.fast_speed(U, 0).max(), s.fast_speed(U, 1).max()))
+        s.ch = ch
     rng = np.random.default_rng(5)
     dU = np.ascontiguousarray(0.1 * rng.standard_normal(U.shape))
     out = np.zeros_like(U)
     st = _lib.vklb_hc_char_rhs2d(KIND[name], 0, d, side, C.c_double(kw.get("gamma", 1.4)),
-                                 C.c_double(kw.get("g", 9.81)), C.c_double(0.7), C.c_double(-0.4),
+                                 C.c_double(kw.get("g", 9.81)), C.c_double(0.7), C.c_double(-0.4), C.c_double(ch),
                                  U.ctypes.data_as(_PD), dU.ctypes.data_as(_PD), C.c_int64(U.shape[1]),
                                  out.ctypes.data_as(_PD))
     assert st == 0
     A = splitting.jacobian(s, U, d)
     for i in range(U.shape[1]):
         want = ovklb.outgoing_part(A[i], dU[:, i], side)
-        assert np.allclose(out[:, i], want, rtol=1e-10, atol=1e-12), i
+        scale = 1.0 if name != "mhd_glm" else max(1.0, float(np.abs(want).max()))
+        assert np.allclose(out[:, i], want, rtol=1e-10, atol=1e-12 * scale), i
 
 
 @pytest.mark.parametrize("nx,ny", [(3, 3), (4, 7), (37, 5), (64, 64)])
