@@ -100,9 +100,10 @@ typedef struct {
  * only): a boundary node takes U_b^{n+1} = U_b^n - (1/xi_n) P Lambda^out P^-1 D U^n
  * with the one-sided difference D towards the interior, a corner sums its two
  * faces, and its distributions become f^eq(U_b^{n+1}) with xi_{n+1} (Eq. 36).
- * Non-periodic 2D faces (either kind) are built for shallow water, Euler and
- * advection (VKLB_ERR_UNSUPPORTED for MHD-GLM), with the plain step kernel in
- * the distribution form, outside batches; they need 3 or more cells across. */
+ * Non-periodic 2D faces (either kind) are built for every system (MHD-GLM:
+ * the nine waves of its Jacobian, c_h of step n; the paper itself runs MHD-GLM
+ * on periodic grids only), with the plain step kernel in the distribution
+ * form, outside batches; they need 3 or more cells across. */
 typedef enum { VKLB_BC_PERIODIC = 0, VKLB_BC_CHARACTERISTIC = 1, VKLB_BC_TRANSMISSIVE = 2 } vklb_bc_kind;
 typedef struct {
   int32_t lo[2];

@@ -229,8 +229,10 @@ struct Impl {
       set_attributes();
       dim3 grid((unsigned)((s->nx + TX - 1) / TX), (unsigned)((s->ny + TY - 1) / TY));
       // the long-split march keeps the halo of its tiles' edge columns (p > 4,
-      // not the bulk-copy step)
-      const bool halo = P > 4 && kv != 1 && s->hl[0] && s->hl_tx == TX;
+      // not the bulk-copy step); with non-periodic faces the boundary passes
+      // rewrite face nodes after the halo was written, so the next step reads
+      // its x ring from the bricks
+      const bool halo = P > 4 && kv != 1 && s->hl[0] && s->hl_tx == TX && s->nb == 0;
       for (int64_t i = 0; i < n; ++i) {
         StepArgs<T> a = make_args<T>(s, t_end);
         if (kv == 1)
@@ -240,14 +242,12 @@ struct Impl {
           launch_plain<128>(kv, grid, TX, sm, s->stream, a, TY);
         else
           launch_plain<0>(kv, grid, TX, sm, s->stream, a, TY);
-        if constexpr (!Sys::MHD) {
-          if (s->nb > 0) {
-            // the characteristic faces (same step arguments: parity and slot of step n)
-            const int bb = 128, gb = (s->nb + bb - 1) / bb;
-            char2d_state_kernel<Sys, T, R><<<gb, bb, 0, s->stream>>>(a, (R*)s->ub, s->nb);
-            char2d_feq_kernel<Sys, T, R><<<gb, bb, 0, s->stream>>>(a, (const R*)s->ub, s->nb);
-            g_launches += 2;
-          }
+        if (s->nb > 0) {
+          // the non-periodic faces (same step arguments: parity and slot of step n)
+          const int bb = 128, gb = (s->nb + bb - 1) / bb;
+          char2d_state_kernel<Sys, T, R><<<gb, bb, 0, s->stream>>>(a, (R*)s->ub, s->nb);
+          char2d_feq_kernel<Sys, T, R><<<gb, bb, 0, s->stream>>>(a, (const R*)s->ub, s->nb);
+          g_launches += 2;
         }
         s->cur ^= 1;
         s->launched += 1;

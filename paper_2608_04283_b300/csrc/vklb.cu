@@ -254,10 +254,8 @@ static int create_impl(const vklb_system* sys, int32_t lattice, const vklb_grid*
   }
   if (dim == 2 && bc->lo[0] != VKLB_BC_PERIODIC && bc->lo[1] != VKLB_BC_PERIODIC && bc->lo[0] != bc->lo[1])
     return VKLB_ERR_ARG;
-  // non-periodic 2D faces: shallow water, Euler and advection; at least 3
-  // cells across a non-periodic axis
+  // non-periodic 2D faces: at least 3 cells across a non-periodic axis
   const bool open2d = dim == 2 && (bc->lo[0] != VKLB_BC_PERIODIC || bc->lo[1] != VKLB_BC_PERIODIC);
-  if (open2d && sys->kind == VKLB_MHD_GLM) return VKLB_ERR_UNSUPPORTED;
   const Ops* ops = pick_ops(sys->kind, dim, precision);
   if (!ops) return VKLB_ERR_UNSUPPORTED;
   if (open2d && ((bc->lo[0] != VKLB_BC_PERIODIC && grid->n[0] < 3) ||

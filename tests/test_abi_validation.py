@@ -46,9 +46,8 @@ def test_create_rejects_system_parameters(vk):
     assert _status(vk, lambda: vk.Sim("swe", (32, 32), (0, 0), (1, 1), g=0.0)) == vk.ERR_ARG
     assert _status(vk, lambda: vk.Sim("mhd_glm", (32, 32), (0, 0), (1, 1), ch_factor=0.0)) == vk.ERR_ARG
     assert _status(vk, lambda: vk.Sim("mhd_glm", (32,), (0.0,), (1.0,))) == vk.ERR_UNSUPPORTED   # MHD-GLM is 2D
-    # 2D characteristic faces are built for shallow water, Euler and advection
-    assert _status(vk, lambda: vk.Sim("mhd_glm", (32, 32), (0, 0), (1, 1), bc="characteristic")) == \
-        vk.ERR_UNSUPPORTED
+    # non-periodic 2D faces need 3 or more cells across (checked before any device call)
+    assert _status(vk, lambda: vk.Sim("mhd_glm", (2, 32), (0, 0), (2 / 32, 1), bc="characteristic")) == vk.ERR_ARG
 
 
 def test_null_handles(vk):
@@ -178,7 +177,6 @@ def test_boundary_kinds(vk, bc, status):
 
 
 def test_transmissive_refusals(vk):
-    assert _status(vk, lambda: vk.Sim("mhd_glm", (16, 16), (0, 0), (1, 1), bc="transmissive")) == \
-        vk.ERR_UNSUPPORTED
+    assert _status(vk, lambda: vk.Sim("mhd_glm", (16, 2), (0, 0), (1, 2 / 16), bc="transmissive")) == vk.ERR_ARG
     assert _status(vk, lambda: vk.Sim("euler", (2, 16), (0, 0), (1, 8), bc=("transmissive", "periodic"))) == \
         vk.ERR_ARG

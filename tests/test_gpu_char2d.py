@@ -4,8 +4,9 @@ corners summing both faces) and transmissive (reading R21: the state of the
 node one cell inwards); <= 1e-11 max relative per field in FP64, <= 1e-5
 relative L1 in FP32, on ragged grids with all four faces open or one axis
 periodic, several tilings; a uniform state is a fixed point; the smooth hump
-leaves the box with small reflections at a size the oracle cannot reach; and
-the combinations not built are refused."""
+leaves the box with small reflections at a size the oracle cannot reach;
+MHD-GLM's nine-wave faces against the oracle in both precisions; and the
+combinations not built are refused."""
 import numpy as np
 import pytest
 
@@ -125,6 +126,66 @@ def test_hump_leaves_the_box(vk, kind, frac, ratio):
     refl = np.abs(out[kind][0] - ref[0]).max()
     wrap = np.abs(out["periodic"][0] - ref[0]).max()
     assert refl < frac * 0.3 and refl < ratio * wrap, (refl, wrap)
+
+
+def _mhd_pulse(nx, ny, L):
+    dx = 2 * L / nx
+    x = -L + (np.arange(nx) + 0.5) * dx
+    y = -L + (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    r = np.sqrt((X - 2.4) ** 2 + (Y + 2.4) ** 2)
+    b = np.where(r <= 1.4, ((1.0 + np.cos(np.pi * r / 1.4)) / 2.0) ** 2, 0.0)
+    z = np.zeros_like(b)
+    return inputs.mhd_conserved(1.0 + 0.2 * b, z + 0.3, z - 0.2, z, 1.0 + 0.3 * b, z + 0.5, z + 0.3, z, z, 5.0 / 3.0)
+
+
+@pytest.mark.parametrize("bc", ["characteristic", ("characteristic", "periodic"), ("periodic", "characteristic"),
+                                "transmissive"])
+@pytest.mark.parametrize("tile", [(64, 5), None])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mhd_pulse_against_oracle(vk, bc, tile, precision):
+    """MHD-GLM with non-periodic faces (the nine waves of the Jacobian along each
+    face normal, c_h of step n): a pressure pulse in a uniform field over the
+    x = hi / y = lo corner, on a ragged 44 x 34 grid, 30 steps; the default
+    launch shape takes the 128-wide long-split march."""
+    from parity_util import rel_l1_mhd
+    nx, ny = 44, 34
+    L = 3.0
+    U0 = np.ascontiguousarray(_mhd_pulse(nx, ny, L))
+    lo, hi = (-L, -L), (L, -L + ny * 2 * L / nx)
+    sim = vk.Sim("mhd_glm", (nx, ny), lo, hi, precision=precision, omega=1.0, cfl=0.3, bc=bc, gamma=5.0 / 3.0)
+    if tile:
+        sim.set_tiling(*tile)
+    sim.set_state(U0)
+    sim.step(30)
+    ref = ovklb.Sim(systems.MHDGLM(5.0 / 3.0), (nx, ny), lo, hi, bc=bc, omega=1.0, nu=0.3)
+    ref.set_state(U0)
+    ref.run(30)
+    got, want = sim.moments(), ref.moments()
+    if precision == "fp64":
+        err = max_rel(got, want)
+        assert err.max() <= 1e-11, err
+        t, steps, xi = sim.time()
+        assert steps == 30 and abs(xi - ref.xi) <= 1e-11 * ref.xi and abs(t - ref.t) <= 1e-12 * ref.t
+    else:
+        err = rel_l1_mhd(got, want)
+        assert err.max() <= 1e-5, err
+    if bc != "transmissive":
+        assert np.abs(want[8]).max() > 1e-6     # the faces made a cleaning field: psi is compared, not zero
+    sim.close()
+
+
+@pytest.mark.parametrize("kind", ["characteristic", "transmissive"])
+def test_uniform_mhd_state_fixed(vk, kind):
+    u0 = inputs.mhd_conserved(np.array(1.3), np.array(0.2), np.array(-0.1), np.array(0.05), np.array(0.8),
+                              np.array(0.6), np.array(-0.4), np.array(0.2), np.array(0.0), 5.0 / 3.0)
+    U = np.broadcast_to(u0[:, None, None], (9, 30, 52)).copy()
+    sim = vk.Sim("mhd_glm", (52, 30), (0, 0), (52 / 30, 1.0), precision="fp64", omega=1.0, cfl=0.3, bc=kind,
+                 gamma=5.0 / 3.0)
+    sim.set_state(U)
+    sim.step(20)
+    assert np.abs(sim.moments() - U).max() <= 1e-13 * np.abs(U).max()
+    sim.close()
 
 
 def test_refused_combinations(vk):
