@@ -316,6 +316,55 @@ __device__ __forceinline__ void cell_post(const Sys& sys, const T* __restrict__ 
                                             c, om, set, k, ch, o);
 }
 
+// The stored values of the cell at b (FORM 0: its 5p distributions; FORM 1:
+// U in v[0]), loaded ahead of the arithmetic that uses them.
+template <class Sys, class T, class R, int FORM>
+__device__ __forceinline__ void load_stored(const T* __restrict__ fin, size_t b, R (&v)[5][Sys::P]) {
+  constexpr int P = Sys::P;
+  if constexpr (FORM == 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int i = 0; i < P; ++i) v[q][i] = Store<T>::ld(fin + b + (size_t)(q * P + i) * kBrick);
+  } else {
+#pragma unroll
+    for (int i = 0; i < P; ++i) v[0][i] = Store<T>::ld(fin + b + (size_t)i * kBrick);
+  }
+}
+
+// Post-collision components MODE needs from loaded stored values, the same
+// arithmetic as cell_post_at (short splits: f held in registers).
+template <class Sys, class R, int MODE, int FORM>
+__device__ __forceinline__ void post_loaded(const Sys& sys, const R (&f)[5][Sys::P], R xinv, R c, R om, int set, R k,
+                                            R ch, R (&o)[5][Sys::P]) {
+  constexpr int P = Sys::P;
+  static_assert(P <= 4, "long splits reload f");
+  if constexpr (FORM == 0) {
+    R U[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) U[i] = f[0][i] + f[1][i] + f[2][i] + f[3][i] + f[4][i];
+    R e[5][P];
+    equilibria_d2q5<Sys, R, MODE>(sys, U, xinv, c, set, k, ch, e);
+    if (om == R(1)) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int i = 0; i < P; ++i) o[q][i] = e[q][i];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        constexpr bool qx = MODE == C_Q1 || MODE == C_Q2 || MODE == C_QX, qy = MODE == C_Q4 || MODE == C_Q5;
+        const bool need = MODE == C_FULL || ((q == 0 || q == 1) && qx) || ((q == 3 || q == 4) && qy);
+        if (!need) continue;
+#pragma unroll
+        for (int i = 0; i < P; ++i) o[q][i] = f[q][i] + om * (e[q][i] - f[q][i]);
+      }
+    }
+  } else {
+    equilibria_d2q5<Sys, R, MODE>(sys, f[0], xinv, c, set, k, ch, o);
+  }
+}
+
 // A node on a characteristic (non-periodic) face: the step writes it from the
 // periodic pull, the boundary pass overwrites it, and the CFL maximum of the
 // step leaves it to that pass.
@@ -461,13 +510,76 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   R m1 = R(0), m2 = R(0);
   bool bad = false;
   int nb = 1, cb = 0;   // row buffers of rows r + 1 and r: (r + 1) mod 3, r mod 3
+  // Software-pipelined rows: iteration r loads the stored values of row r + 1
+  // first, and while they arrive finishes row r - 1 (the component streaming
+  // from row r, its sum and the CFL epilogue) and as much of row r as does not
+  // need row r + 1 (stores and partial sums of the other four components);
+  // then row r + 1's collision.  Row r's f*_1 / f*_2 were published by the
+  // barrier ending iteration r - 1.
+  __syncthreads();
+  constexpr int QB = up ? 3 : 4;   // component streaming from the row behind
+  constexpr int QA = up ? 4 : 3;   // component streaming from the row ahead
+  const T* tp = nullptr;
+  R acc[P], held[P], fan[P];       // row r - 1's partial sums and its missing component
+  auto finish_late = [&](int jr) {
+    const size_t base = brick_base(x, jr, nxb, NS);
+    R U[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      if constexpr (FORM == 0) {
+        Store<T>::st(fout + (size_t)(QA * P + i) * kBrick + base, fan[i]);
+        U[i] = up ? acc[i] + round_store(fan[i], tp) : (acc[i] + round_store(fan[i], tp)) + held[i];
+      } else {
+        const R u = up ? acc[i] + fan[i] : (acc[i] + fan[i]) + held[i];
+        Store<T>::st(fout + (size_t)i * kBrick + base, u);
+        U[i] = round_store(u, tp);
+      }
+    }
+    if (!(a.cbx | a.cby) || !on_char_face(a, x, jr)) {   // periodic grids skip the face test
+      R e1, e2;
+      bad |= !sys.epilogue(U, e1, e2);
+      m1 = vmax(m1, e1);
+      m2 = vmax(m2, e2);
+    }
+  };
   for (int r = 0; r < h; ++r) {
     const int j = row_of(r);
-    R fan[P], f3n[P], fbn[P];
+    const bool nxt = r + 1 < h;
+    R f3n[P], fbn[P];
+    R fl[5][P];
     if (act) {
+      const int jn = nxt ? row_of(r + 1) : (up ? wrap1(y0 + h, ny) : wrap1(y0 - 1, ny));
+      load_stored<Sys, T, R, FORM>(fin, brick_base(x, jn, nxb, NS), fl);
+      if (r > 0) finish_late(row_of(r - 1));
+      const size_t base = brick_base(x, j, nxb, NS);
+      const int rt = j - y0;
+      // the x neighbours' components, picked by offset from one shared base (a
+      // select between two pointers would lose their state space)
+      R* const sm = rb1;
+      R g0[P], g1[P];
+      CV::get(sm + (tx == 0 ? (int)(ringL - sm) + rt * PP : (cb * TX + tx - 1) * PP), g0);
+      CV::get(sm + (tx == w - 1 ? (int)(ringR - sm) + rt * PP : (int)(rb2 - sm) + (cb * TX + tx + 1) * PP), g1);
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        if constexpr (FORM == 0) {
+          Store<T>::st(fout + (size_t)(0 * P + i) * kBrick + base, g0[i]);
+          Store<T>::st(fout + (size_t)(1 * P + i) * kBrick + base, g1[i]);
+          Store<T>::st(fout + (size_t)(2 * P + i) * kBrick + base, f3c[i]);
+          Store<T>::st(fout + (size_t)(QB * P + i) * kBrick + base, fbp[i]);
+          R sum = ((R(0) + round_store(g0[i], tp)) + round_store(g1[i], tp)) + round_store(f3c[i], tp);
+          if (up) sum += round_store(fbp[i], tp);
+          acc[i] = sum;
+          held[i] = round_store(fbp[i], tp);
+        } else {
+          R sum = (g0[i] + g1[i]) + f3c[i];
+          if (up) sum = sum + fbp[i];
+          acc[i] = sum;
+          held[i] = fbp[i];
+        }
+      }
       R o[5][P];
-      if (r + 1 < h) {
-        cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, row_of(r + 1), nxb, xinv, c, om, set, kk, ch, o);
+      if (nxt) {
+        post_loaded<Sys, R, C_FULL, FORM>(sys, fl, xinv, c, om, set, kk, ch, o);
         CV::put(rb1 + (nb * TX + tx) * PP, o[0]);
         CV::put(rb2 + (nb * TX + tx) * PP, o[1]);
 #pragma unroll
@@ -478,11 +590,11 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
         }
       } else {
         if (up) {
-          cell_post<Sys, T, R, C_Q5, FORM>(sys, fin, x, wrap1(y0 + h, ny), nxb, xinv, c, om, set, kk, ch, o);
+          post_loaded<Sys, R, C_Q5, FORM>(sys, fl, xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[4][i];
         } else {
-          cell_post<Sys, T, R, C_Q4, FORM>(sys, fin, x, wrap1(y0 - 1, ny), nxb, xinv, c, om, set, kk, ch, o);
+          post_loaded<Sys, R, C_Q4, FORM>(sys, fl, xinv, c, om, set, kk, ch, o);
 #pragma unroll
           for (int i = 0; i < P; ++i) fan[i] = o[3][i];
         }
@@ -491,47 +603,6 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
       }
     }
     __syncthreads();
-    if (act) {
-      const size_t base = brick_base(x, j, nxb, NS);
-      const int rt = j - y0;
-      // the x neighbours' components, picked by offset from one shared base (a
-      // select between two pointers would lose their state space)
-      R* const sm = rb1;
-      R g0[P], g1[P];
-      CV::get(sm + (tx == 0 ? (int)(ringL - sm) + rt * PP : (cb * TX + tx - 1) * PP), g0);
-      CV::get(sm + (tx == w - 1 ? (int)(ringR - sm) + rt * PP : (int)(rb2 - sm) + (cb * TX + tx + 1) * PP), g1);
-      R U[P];
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        R g[5];
-        g[0] = g0[i];
-        g[1] = g1[i];
-        g[2] = f3c[i];
-        g[3] = up ? fbp[i] : fan[i];
-        g[4] = up ? fan[i] : fbp[i];
-        const T* tp = nullptr;
-        if constexpr (FORM == 0) {
-          R acc = R(0);
-#pragma unroll
-          for (int q = 0; q < 5; ++q) {
-            Store<T>::st(fout + (size_t)(q * P + i) * kBrick + base, g[q]);
-            acc += round_store(g[q], tp);
-          }
-          U[i] = acc;
-        } else {
-          // Eq. (3), summed in the order of the distribution form's next collision
-          const R u = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];
-          Store<T>::st(fout + (size_t)i * kBrick + base, u);
-          U[i] = round_store(u, tp);
-        }
-      }
-      if (!(a.cbx | a.cby) || !on_char_face(a, x, j)) {   // periodic grids skip the face test
-        R e1, e2;
-        bad |= !sys.epilogue(U, e1, e2);
-        m1 = vmax(m1, e1);
-        m2 = vmax(m2, e2);
-      }
-    }
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       fbp[i] = fbc[i];
@@ -541,6 +612,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     nb = next3(nb);
     cb = next3(cb);
   }
+  if (act && h > 0) finish_late(row_of(h - 1));
   commit_max<R>(m1, m2, bad, a.ctl, s1);
 }
 
