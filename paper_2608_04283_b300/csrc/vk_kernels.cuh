@@ -465,10 +465,38 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   R* ringL = rb2 + 3 * PP * TX;          // [TY][PP]     f*_1 at x0 - 1, by tile row
   R* ringR = ringL + PP * TY;            // [TY][PP]     f*_2 at x0 + w
 
-  // x ring: only the component that streams into the tile, from the x split.
-  // Read up front for all rows, long before the neighbouring tile reaches the
-  // later rows; the step streams more bytes than L2 holds, so these loads ask
-  // L2 to keep their lines (else they are fetched from DRAM twice).
+  // The prologue: the ring row behind and the first row of this thread's
+  // column are loaded together and collided; then the x ring (only the
+  // component that streams into the tile, from the x split), read for all rows
+  // long before the neighbouring tile reaches the later rows: the step streams
+  // more bytes than L2 holds, so these loads ask L2 to keep their lines (else
+  // they are fetched from DRAM twice).
+  R fbp[P], f3c[P], fbc[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
+  if (act) {
+    R fb0[5][P], fr0[5][P];
+    load_stored<Sys, T, R, FORM>(fin, brick_base(x, up ? wrap1(y0 - 1, ny) : wrap1(y0 + h, ny), nxb, NS), fb0);
+    load_stored<Sys, T, R, FORM>(fin, brick_base(x, row_of(0), nxb, NS), fr0);
+    R o[5][P];
+    if (up) {
+      post_loaded<Sys, R, C_Q4, FORM>(sys, fb0, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+      for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
+    } else {
+      post_loaded<Sys, R, C_Q5, FORM>(sys, fb0, xinv, c, om, set, kk, ch, o);
+#pragma unroll
+      for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
+    }
+    post_loaded<Sys, R, C_FULL, FORM>(sys, fr0, xinv, c, om, set, kk, ch, o);
+    CV::put(rb1 + tx * PP, o[0]);
+    CV::put(rb2 + tx * PP, o[1]);
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      f3c[i] = o[2][i];
+      fbc[i] = up ? o[3][i] : o[4][i];
+    }
+  }
   for (int t = tx; t < 2 * h; t += blockDim.x) {
     const int side = t >= h;
     const int r = side ? t - h : t;
@@ -480,30 +508,6 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
     } else {
       cell_post<Sys, T, R, C_Q2, FORM, true>(sys, fin, xr, y0 + r, nxb, xinv, c, om, set, kk, ch, o);
       CV::put(ringR + r * PP, o[1]);
-    }
-  }
-
-  R fbp[P], f3c[P], fbc[P];
-#pragma unroll
-  for (int i = 0; i < P; ++i) fbp[i] = f3c[i] = fbc[i] = R(0);
-  if (act) {
-    R o[5][P];
-    if (up) {
-      cell_post<Sys, T, R, C_Q4, FORM>(sys, fin, x, wrap1(y0 - 1, ny), nxb, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-      for (int i = 0; i < P; ++i) fbp[i] = o[3][i];
-    } else {
-      cell_post<Sys, T, R, C_Q5, FORM>(sys, fin, x, wrap1(y0 + h, ny), nxb, xinv, c, om, set, kk, ch, o);
-#pragma unroll
-      for (int i = 0; i < P; ++i) fbp[i] = o[4][i];
-    }
-    cell_post<Sys, T, R, C_FULL, FORM>(sys, fin, x, row_of(0), nxb, xinv, c, om, set, kk, ch, o);
-    CV::put(rb1 + tx * PP, o[0]);
-    CV::put(rb2 + tx * PP, o[1]);
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-      f3c[i] = o[2][i];
-      fbc[i] = up ? o[3][i] : o[4][i];
     }
   }
 
