@@ -428,6 +428,43 @@ __device__ __forceinline__ int next3(int i) { return i == 2 ? 0 : i + 1; }
 // A row or column index one step outside [0, n) wrapped periodically (Eq. 37).
 __device__ __forceinline__ int wrap1(int j, int n) { return j < 0 ? j + n : (j >= n ? j - n : j); }
 
+// Row barrier of the plain march as an mbarrier: every thread arrives once its
+// row's f*_1 / f*_2 are in shared memory and waits only where it next reads
+// them, so a thread that is ahead issues the next row's loads and finishes the
+// previous row first.  The wait is bounded (%globaltimer): giving up latches
+// ERR_TIMEOUT and the march goes on without further waits, so it cannot hang.
+__device__ __forceinline__ void rowbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void rowbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+__device__ __forceinline__ bool rowbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool rowbar_wait(uint64_t* bar, uint32_t parity) {
+  if (rowbar_test(bar, parity)) return true;
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (uint32_t i = 1;; ++i) {
+    if (rowbar_test(bar, parity)) return true;
+    if ((i & 63u) == 0) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > 2000000000ull) return false;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ D2Q5 step
 // March over the rows of one tile, up or down.  Tiles of
 // even row index march up and odd ones down, so the two tiles that share a
@@ -465,6 +502,11 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   R* ringL = rb2 + 3 * PP * TX;          // [TY][PP]     f*_1 at x0 - 1, by tile row
   R* ringR = ringL + PP * TY;            // [TY][PP]     f*_2 at x0 + w
 
+  __shared__ __align__(8) uint64_t rowbar;
+  if (tx == 0) {
+    rowbar_init(&rowbar, blockDim.x);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   // The prologue: the ring row behind and the first row of this thread's
   // column are loaded together and collided; then the x ring (only the
   // component that streams into the tile, from the x split), read for all rows
@@ -519,7 +561,11 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
   // from row r, its sum and the CFL epilogue) and as much of row r as does not
   // need row r + 1 (stores and partial sums of the other four components);
   // then row r + 1's collision.  Row r's f*_1 / f*_2 were published by the
-  // barrier ending iteration r - 1.
+  // row barrier's arrivals ending iteration r - 1; a thread waits on them only
+  // after the loads and row r - 1's finish, which touch no shared memory.  The
+  // three row buffers make one phase of slack safe: a thread past the wait of
+  // iteration r writes buffer (r + 1) mod 3, while the slowest is still in
+  // iteration r, reading buffer r mod 3.
   __syncthreads();
   constexpr int QB = up ? 3 : 4;   // component streaming from the row behind
   constexpr int QA = up ? 4 : 3;   // component streaming from the row ahead
@@ -546,6 +592,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
       m2 = vmax(m2, e2);
     }
   };
+  bool waiting = true;
   for (int r = 0; r < h; ++r) {
     const int j = row_of(r);
     const bool nxt = r + 1 < h;
@@ -555,6 +602,14 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
       const int jn = nxt ? row_of(r + 1) : (up ? wrap1(y0 + h, ny) : wrap1(y0 - 1, ny));
       load_stored<Sys, T, R, FORM>(fin, brick_base(x, jn, nxb, NS), fl);
       if (r > 0) finish_late(row_of(r - 1));
+    }
+    // row r's f*_1 / f*_2, written in iteration r - 1; every thread waits
+    // (including those without a column), so that none arrives twice in a phase
+    if (r > 0 && waiting && !rowbar_wait(&rowbar, (uint32_t)((r - 1) & 1))) {
+      atomicOr(&a.ctl->err, ERR_TIMEOUT);
+      waiting = false;
+    }
+    if (act) {
       const size_t base = brick_base(x, j, nxb, NS);
       const int rt = j - y0;
       // the x neighbours' components, picked by offset from one shared base (a
@@ -606,7 +661,7 @@ __device__ __forceinline__ void step2d_tile_dir(const StepArgs<T>& a, const Bloc
         for (int i = 0; i < P; ++i) f3n[i] = fbn[i] = R(0);
       }
     }
-    __syncthreads();
+    rowbar_arrive(&rowbar);
 #pragma unroll
     for (int i = 0; i < P; ++i) {
       fbp[i] = fbc[i];
