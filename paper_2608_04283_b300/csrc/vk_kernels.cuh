@@ -718,6 +718,13 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
   R* ringL = rb2 + 3 * P * TX;           // [TY][P]     f*_1 at x0 - 1, by tile row
   R* ringR = ringL + P * TY;             // [TY][P]     f*_2 at x0 + w
 
+  __shared__ __align__(8) uint64_t rowbar;
+  if (tx == 0) {
+    rowbar_init(&rowbar, blockDim.x);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool waiting = true;
   // x ring, read up front with the L2 keep policy (as in the march above):
   // from the halo of the neighbouring tiles when the last step wrote it (the
   // left ring is the left neighbour's last column, the right ring the right
@@ -776,8 +783,18 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
       }
     }
     if (r >= 1) {
-      // finish row r - 1 of the march
-      __syncthreads();
+      // finish row r - 1 of the march, once every thread is done with iteration
+      // r - 1 (phase r - 1: a thread arrives from iteration 0 on, and waits
+      // between any two of its arrivals, so none runs two phases ahead).  Row
+      // r - 1's f*_1 / f*_2 were written in that iteration; the buffer this
+      // iteration wrote before the wait, (r mod 3), was last read in iteration
+      // r - 2, which the wait of iteration r - 1 saw finished.  Unlike a
+      // barrier after the split, a thread whose split ran long no longer holds
+      // up the others' finish.
+      if (waiting && !rowbar_wait(&rowbar, (uint32_t)((r - 1) & 1))) {
+        atomicOr(&a.ctl->err, ERR_TIMEOUT);
+        waiting = false;
+      }
       if (act) {
         const int rr = r - 1;
         const int j = up ? y0 + rr : y0 + h - 1 - rr;
@@ -833,6 +850,7 @@ __device__ __forceinline__ void step2d_tile_one(const StepArgs<T>& a, const Bloc
         f3s[i * TX + tx] = f3n[i];
       }
     }
+    if (r >= 0) rowbar_arrive(&rowbar);
     nbr = nbr == 2 ? 0 : nbr + 1;
     cbr = cbr == 2 ? 0 : cbr + 1;
   }
