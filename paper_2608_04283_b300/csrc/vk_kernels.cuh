@@ -15,7 +15,7 @@
 // equilibria (Eq. 41), collides (Eq. 42) and streams by pull (Eq. 43):
 //     f^{n+1}_q(x) = f*_q(x - v_q).
 // The x neighbours' f*_1, f*_2 go through shared memory (three row buffers, one
-// barrier per row); f*_4 of the row below and f*_5 of the row above stay in
+// mbarrier phase per row); f*_4 of the row below and f*_5 of the row above stay in
 // registers.  The 1-cell ring around the tile is recomputed for just the one
 // component that streams inward (x ring: f*_1 / f*_2 from the x split only;
 // y ring: f*_4 / f*_5 from the y split only).  Knowing every f^{n+1} of its tile,
@@ -428,11 +428,14 @@ __device__ __forceinline__ int next3(int i) { return i == 2 ? 0 : i + 1; }
 // A row or column index one step outside [0, n) wrapped periodically (Eq. 37).
 __device__ __forceinline__ int wrap1(int j, int n) { return j < 0 ? j + n : (j >= n ? j - n : j); }
 
-// Row barrier of the plain march as an mbarrier: every thread arrives once its
-// row's f*_1 / f*_2 are in shared memory and waits only where it next reads
-// them, so a thread that is ahead issues the next row's loads and finishes the
-// previous row first.  The wait is bounded (%globaltimer): giving up latches
-// ERR_TIMEOUT and the march goes on without further waits, so it cannot hang.
+// Row barrier of both marches as an mbarrier: every thread arrives once a row
+// iteration is done (its f*_1 / f*_2 written, the rows it read finished) and
+// waits only where it next reads the others' values, so a thread that is ahead
+// keeps working instead of idling at a block barrier.  A thread waits between
+// any two of its arrivals, so it is never two phases ahead and the parity of
+// the phase it waits on is unambiguous.  The wait is bounded (%globaltimer):
+// giving up latches ERR_TIMEOUT and the march goes on without further waits,
+// so it cannot hang.
 __device__ __forceinline__ void rowbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count)
                : "memory");
@@ -904,9 +907,10 @@ __device__ __forceinline__ void step2d_tile(const StepArgs<T>& a, int bx, int by
       step2d_tile_dir<Sys, T, R, +1, FORM>(a, s_bc, bx, by, TX, TY, smem);
   } else {
     // The weighted set (Eq. 41) gets its own copy of the march, compiled under
-    // the test that selects it.  Measured for MHD-GLM (FP32 2048^2): 321 us with
-    // this form, 327 us passing the set as a literal in that copy, 336 us with
-    // one copy; the short splits gain nothing.
+    // the test that selects it.  Measured for MHD-GLM (FP32 2048^2, with a block
+    // barrier per row at the time): 321 us with this form, 327 us passing the
+    // set as a literal in that copy, 336 us with one copy; the short splits
+    // gain nothing.
     if (a.set == SET_WEIGHTED)
       step2d_tile_one<Sys, T, R, FORM, TXC>(a, s_bc, bx, by, TX, TY, smem, a.set);
     else
