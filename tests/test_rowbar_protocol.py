@@ -14,10 +14,11 @@ decrements the pending count, the phase completes when it reaches zero, and
 
 Every read of a neighbour's buffer slot must see the row the reader expects
 (so no writer overwrote it early and no reader ran before the write), and every
-schedule must finish (no thread waits on a phase that has aliased).  A variant
-of the long-split march that also arrives after the ring row behind the tile
-(two arrivals before the first wait) is the negative control: the model must
-find schedules where it breaks.
+schedule must finish (no thread waits on a phase that has aliased).  Two
+variants are negative controls, which the model must find schedules to break:
+the long-split march also arriving after the ring row behind the tile (two
+arrivals before the first wait), and the plain march with the wait skipped by
+threads without a column.
 """
 import random
 
