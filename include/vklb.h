@@ -56,8 +56,9 @@ typedef enum {
   VKLB_ERR_CUDA = -3,         /* a CUDA runtime call failed (no device, launch error) */
   VKLB_ERR_NONPHYSICAL = -4,  /* NaN or non-positive h / rho / p produced on the device */
   VKLB_ERR_CFL = -5,          /* fixed lattice speed below max |lambda| (Eq. 28 violated) */
-  VKLB_ERR_TIMEOUT = -6,      /* a bounded device wait gave up (bulk-copy step variant; see
-                                 vklb_selftest_wait_timeout) */
+  VKLB_ERR_TIMEOUT = -6,      /* a bounded device wait gave up: a row stage of the bulk-copy
+                                 step variant, or the row barrier of a tile march (2 s);
+                                 see vklb_selftest_wait_timeout */
   VKLB_ERR_STATE = -7,        /* call out of order (e.g. stepping before vklb_set_state) */
   VKLB_ERR_UNSUPPORTED = -8,  /* combination not built (e.g. D1Q3 with MHD-GLM) */
   VKLB_ERR_LIMIT = -9         /* beyond the fixed scratch of vklb_conservation_totals_noalloc */
